@@ -1,0 +1,146 @@
+"""Pins of the split-precision oracle (no GPU): exact reconstruction of the
+digits, digit and exponent ranges, special cases that reduce to exact results
+(small integers, identity and permutation right factors), and accuracy within
+the 2 K u bound against the compensated reference."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import native, split
+
+
+@pytest.mark.parametrize("kind", ["int8", "bf16"])
+@pytest.mark.parametrize("dist", ["uniform", "wide", "smallint"])
+def test_digits_reconstruct_exactly(kind, dist):
+    w = split.SLICE_BITS[kind]
+    A = workloads.matrix(6, 11, 3, dist)
+    A[2, :] = 0.0                          # an all-zero row
+    A[3, 4] = 2.0 ** -1060                 # a subnormal next to normal values
+    e = split.row_exponents(A)
+    S = 9
+    D = split.split_rows(A, e, S, w)
+    # rebuild the remainder of the last step and check
+    # A_ik = 2^e_i (sum_s t_s 2^-ws + r_S 2^-wS) with |r_S| <= 1/2 exactly
+    for i in range(A.shape[0]):
+        for k in range(A.shape[1]):
+            x = Fraction(float(A[i, k])) / Fraction(2) ** int(e[i])
+            approx = sum(Fraction(int(D[s, i, k])) / Fraction(2) ** (w * (s + 1)) for s in range(S))
+            rem = (x - approx) * Fraction(2) ** (w * S)
+            assert abs(rem) <= Fraction(1, 2)
+            assert all(abs(D[s, i, k]) <= 2 ** (w - 1) for s in range(S))
+    assert np.all(D[:, 2, :] == 0)
+
+
+def test_exponent_range():
+    A = workloads.matrix(40, 30, 8, "wide")
+    A[5] = 0.0
+    e = split.row_exponents(A)
+    mu = np.abs(A).max(axis=1)
+    nz = mu > 0
+    s = mu[nz] * 2.0 ** (-e[nz].astype(float))
+    assert np.all(s >= 0.25) and np.all(s < 0.5)
+    assert e[5] == 0
+    assert np.array_equal(split.col_exponents(A.T), e)
+
+
+def test_tie_rounds_to_even():
+    # row max 0.25 = 2^-2 -> e = ilogb + 2 = 0, so r = A.  With w = 8:
+    #   0.25 * 256 = 64 exactly;  (2.5/256) * 256 = 2.5 -> 2 (even), remainder
+    #   +0.5 -> next digit 128;  (3.5/256) * 256 = 3.5 -> 4 (even), remainder
+    #   -0.5 -> next digit -128
+    A = np.array([[0.25, 2.5 / 256.0, 3.5 / 256.0]])
+    e = split.row_exponents(A)
+    assert e[0] == 0
+    D = split.split_rows(A, e, 3, 8)
+    assert D[:, 0, 0].tolist() == [64, 0, 0]
+    assert D[:, 0, 1].tolist() == [2, 128, 0]
+    assert D[:, 0, 2].tolist() == [4, -128, 0]
+
+
+@pytest.mark.parametrize("kind,S", [("int8", 1), ("int8", 3), ("bf16", 1), ("bf16", 4)])
+def test_small_integers_exact_for_any_S(kind, S):
+    A = workloads.matrix(13, 21, 51, "smallint")
+    B = workloads.matrix(21, 9, 52, "smallint")
+    C = split.split_gemm(A, B, S, kind)
+    assert np.array_equal(C, native.dgemm(A, B))
+
+
+@pytest.mark.parametrize("kind,S", [("bf16", 7), ("int8", 8)])
+def test_identity_right_factor_returns_A(kind, S):
+    # B = I: f_j = 2, the only nonzero digit of column j is 2^(w-2) at row j, so
+    # C^ = 2^e_i sum_s t_s 2^-ws, the first S digits of A; w S >= 56 > 53 bits
+    # relative to the row maximum captures A exactly
+    A = workloads.matrix(17, 12, 61, "uniform")
+    C = split.split_gemm(A, np.eye(12), S, kind)
+    assert np.array_equal(C, A)
+
+
+def test_permutation_right_factor():
+    A = workloads.matrix(9, 14, 62, "uniform")
+    perm = np.array(workloads.splitmix64(3, 0, 14).argsort())
+    Pm = np.eye(14)[:, perm]
+    C = split.split_gemm(A, Pm, 7, "bf16")
+    assert np.array_equal(C, A[:, perm])
+
+
+def test_truncation_changes_with_S():
+    # with fewer slices the identity product keeps only the top w S bits of each
+    # row (relative to the row maximum), within half a unit of the last digit
+    A = workloads.matrix(5, 8, 63, "uniform")
+    e = split.row_exponents(A)
+    for S in (2, 3, 4):
+        C = split.split_gemm(A, np.eye(8), S, "bf16")
+        bound = 0.5 * 2.0 ** (e[:, None].astype(float) - 8 * S)
+        assert np.all(np.abs(C - A) <= bound * (1 + 2.0 ** -50) + np.abs(A) * 2.0 ** -53)
+
+
+def test_pairs_triangle():
+    assert split.kept_pairs(3) == [(1, 1), (1, 2), (2, 1), (1, 3), (2, 2), (3, 1)]
+    assert len(split.kept_pairs(6)) == 21
+
+
+@pytest.mark.parametrize("kind,S", [("bf16", 5), ("bf16", 6), ("int8", 6), ("int8", 7)])
+def test_accuracy_bound_uniform(kind, S):
+    # FP64-accurate: max |C - C^| / (|A||B|) <= 2 K u on uniform[-1, 1] inputs.
+    # The slicing error relative to |A||B| hardly depends on K while the bound
+    # grows with K, so the smallest passing S depends on K; K = 4096 here.
+    M, N, K = 16, 16, 4096
+    A = workloads.matrix(M, K, 1002, "uniform")
+    B = workloads.matrix(K, N, 2002, "uniform")
+    C = split.split_gemm(A, B, S, kind)
+    ref, absab = native.dot2_full(A, B)
+    assert split.max_rel_error(C, ref, absab) <= split.tolerance(K)
+
+
+def test_accuracy_improves_with_S():
+    M, N, K = 16, 16, 128
+    A = workloads.matrix(M, K, 1002, "wide")
+    B = workloads.matrix(K, N, 2002, "wide")
+    ref, absab = native.dot2_full(A, B)
+    errs = [split.max_rel_error(split.split_gemm(A, B, S, "bf16"), ref, absab) for S in (2, 3, 4, 5)]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_entries_match_full():
+    A = workloads.matrix(10, 40, 71, "wide")
+    B = workloads.matrix(40, 12, 72, "uniform")
+    C = split.split_gemm(A, B, 4, "int8")
+    rows, cols = np.array([0, 9, 3, 3]), np.array([11, 0, 5, 6])
+    assert np.array_equal(split.split_entries(A, B, rows, cols, 4, "int8"), C[rows, cols])
+
+
+def test_round_scaled_is_correctly_rounded():
+    # ties to even, subnormal results and overflow
+    assert split.round_scaled(2 ** 53 + 1, 0) == 2.0 ** 53
+    assert split.round_scaled(2 ** 53 + 3, 0) == 2.0 ** 53 + 4
+    assert split.round_scaled(3, -1075) == 2.0 ** -1074 * 2      # 1.5 ulp -> 2 ulp
+    assert split.round_scaled(1, -1075) == 0.0                    # half ulp -> even 0
+    assert split.round_scaled(3, 1023) == float("inf")
+    assert split.round_scaled(-3, 1023) == float("-inf")
+
+
+def test_metric_zero_denominator():
+    assert split.max_rel_error(np.zeros(2), np.zeros(2), np.zeros(2)) == 0.0
+    assert split.max_rel_error(np.array([1e-300]), np.zeros(1), np.zeros(1)) == float("inf")
