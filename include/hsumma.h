@@ -1,0 +1,229 @@
+/*
+ * hsumma.h -- C ABI of the single-GPU (sm_103a) Hierarchical SUMMA library.
+ *
+ * The library computes C = A x B (Section II-A: "C = A x B over a
+ * two-dimensional p = s x t processor grid"; Section III, Algorithm 1) on one
+ * GPU.  The paper's virtual processor grid becomes a grid of P x Q thread
+ * blocks, one per virtual processor; its two broadcast levels become
+ *   - the outer, between-group level (Section III, Figure 3): B-wide panels of
+ *     A and B staged from HBM into L2 by the owner of each outer block, and
+ *   - the inner, in-group level (Figure 4): b-wide panels multicast by the
+ *     Tensor Memory Accelerator to every thread block of a group, the group
+ *     being one thread-block cluster;
+ * and the local update c_ij += a_ik b_kj runs on the tensor cores.
+ *
+ * Conventions for every entry point:
+ *   - matrices are row-major binary64; A is M x K with leading dimension
+ *     lda >= K, B is K x N (ldb >= N), C is M x N (ldc >= N); leading
+ *     dimensions are counted in elements and must be multiples of 2 (the
+ *     Tensor Memory Accelerator needs 16-byte row strides); base pointers must
+ *     be 16-byte aligned;
+ *   - pointers named d_* are device pointers owned by the caller; h_* are host
+ *     pointers owned by the caller; the library never frees caller memory;
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); work is
+ *     enqueued asynchronously, in stream order;
+ *   - every call returns an hsumma_status; nothing aborts or traps.  Errors
+ *     found on the device (a bounded wait that ran out, a non-finite input of
+ *     the split path) are recorded in a device word and returned by the next
+ *     hsumma_sync();  hsumma_last_error() gives a message for the last failure
+ *     of the calling thread.
+ */
+#ifndef HSUMMA_H
+#define HSUMMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HSUMMA_OK = 0,
+  HSUMMA_ERR_ARG = -1,          /* invalid argument (message says which) */
+  HSUMMA_ERR_UNSUPPORTED = -2,  /* valid but outside what this build handles */
+  HSUMMA_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+  HSUMMA_ERR_TIMEOUT = -4,      /* a device-side bounded wait ran out */
+  HSUMMA_ERR_NOT_INIT = -5,     /* hsumma_init() has not been called */
+  HSUMMA_ERR_NONFINITE = -6     /* split path given an Inf or NaN input */
+} hsumma_status;
+
+/* Arithmetic of the local update.  The mode argument of hsumma_gemm carries
+ * the kind in bits 0..7 and, for the split kinds, the slice count S in bits
+ * 8..15: use HSUMMA_MODE(kind, S). */
+typedef enum {
+  HSUMMA_FP64 = 0,        /* binary64 DGEMM update (Section II-A, Algorithm 1) */
+  HSUMMA_INT8_SLICES = 1, /* S int8 slices, 7 bits each, exact int32 sums, S in 1..8 */
+  HSUMMA_BF16_SLICES = 2  /* S bf16 slices, 8 bits each, exact fp32 sums, S in 1..7 */
+} hsumma_mode;
+
+#define HSUMMA_MODE(kind, slices) ((int)(kind) | ((int)(slices) << 8))
+
+/* Panel-load counters of the last hsumma_gemm launch, in matrix elements
+ * (slice elements for the split kinds, counted once per slice pair).  They
+ * are the GPU counterparts of the broadcast volumes of Section IV-B: with one
+ * sub-tile per thread block and the group realised as one cluster,
+ *   a_loaded = M K + (J-1) M K          (owner copy + outer volume),
+ *   a_delivered - a_loaded = (Q-J) M K  (inner volume saved by multicast),
+ * and symmetrically for B.  l2_prefetch counts outer-panel prefetches (one per
+ * processor row for A and per processor column for B, per sub-tile and outer
+ * step); tma_loads counts tensor-copy instructions issued. */
+typedef struct {
+  uint64_t a_loaded, a_delivered, b_loaded, b_delivered, l2_prefetch, tma_loads;
+} hsumma_counters;
+
+/* Bind the library to a CUDA device: queries the SM count and the largest
+ * cluster size, allocates the counters and the device error word.  Must be
+ * called (once per process, or again after hsumma_finalize) before any other
+ * call except hsumma_group_shape, hsumma_workspace_size and
+ * hsumma_last_error.  Returns HSUMMA_ERR_UNSUPPORTED on a device that is not
+ * compute capability 10.3. */
+int hsumma_init(int device);
+
+/* Free everything the library allocated.  Safe to call twice. */
+void hsumma_finalize(void);
+
+/* Group resolution (Section III: the s x t grid is arranged into I x J groups
+ * of (s/I) x (t/J) processors; Section IV-B uses sqrt(G) x sqrt(G)).  Writes
+ * the factorisation G = I J with I | P and J | Q whose in-group grid is most
+ * square (ties: smaller I), and the realised cluster shape: (P/I) x (Q/J) when
+ * that many thread blocks fit one cluster of the device, else 1 x 1 (the group
+ * is then served flat from L2).  Before hsumma_init a cluster limit of 16 is
+ * assumed.  HSUMMA_ERR_ARG if no factorisation exists. */
+int hsumma_group_shape(int P, int Q, int G, int *I, int *J, int *cluster_m,
+                       int *cluster_n);
+
+/* Device workspace the library will hold for a call with these sizes and
+ * mode (slices and exact pair sums of the split path; 0 for FP64).  The
+ * library allocates and grows it itself on first use. */
+int hsumma_workspace_size(int64_t M, int64_t N, int64_t K, int mode,
+                          size_t *bytes);
+
+/* C = A x B by HSUMMA on a virtual P x Q grid (Algorithm 1): G groups, inner
+ * block b, outer block Bouter (b <= Bouter, b | Bouter; Section III: "the
+ * block size inside a group should be less than or equal to the block size
+ * between groups").  Blocks are ceil(M/P) x ceil(N/Q) and the last ones may
+ * be short (the paper assumes divisibility; short blocks are allowed here);
+ * 1 <= P, Q <= 65535; G must factor as above; b a multiple of 16 in 16..256
+ * for FP64 and of 64 in 64..256 for the split kinds; Bouter a multiple of b.  P = Q = G = b = Bouter = 0 asks the library to choose them
+ * (the learned cost model if one is loaded, else exhaustive timing of the
+ * candidate set).  C is overwritten (beta = 0).  M, N or K = 0 is allowed
+ * (K = 0 writes zeros).  The split kinds (Ozaki-style) need
+ * finite inputs and K small enough for exact integer sums. */
+int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *d_A, int64_t lda,
+                const double *d_B, int64_t ldb, double *d_C, int64_t ldc, int P,
+                int Q, int G, int b, int Bouter, int mode, void *stream);
+
+/* The same product from host buffers: copies A and B to library-owned device
+ * buffers, runs hsumma_gemm, copies C back and synchronises the stream.
+ * Pinned host memory gives full copy bandwidth; pageable memory works. */
+int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *h_A,
+                     int64_t lda, const double *h_B, int64_t ldb, double *h_C,
+                     int64_t ldc, int P, int Q, int G, int b, int Bouter,
+                     int mode, void *stream);
+
+/* Counters of the last hsumma_gemm launch (call after hsumma_sync). */
+int hsumma_get_counters(hsumma_counters *out);
+
+/* Synchronise `stream` and report device-side errors recorded since the last
+ * call (HSUMMA_ERR_TIMEOUT, HSUMMA_ERR_NONFINITE) or a CUDA error. */
+int hsumma_sync(void *stream);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *hsumma_last_error(void);
+
+/* ---- Split path, step by step (the steps hsumma_gemm runs for the split
+ * kinds; exposed so that each step can be checked on its own) ---- */
+
+/* Step 1, exponent scan: e[i] = ilogb(max_k |A_ik|) + 2 (0 for a zero row),
+ * f[j] likewise over the columns of B, so that every scaled entry is < 1/2 in
+ * magnitude.  d_e: M int32, d_f: N int32. */
+int hsumma_split_exponents(int64_t M, int64_t N, int64_t K, const double *d_A,
+                           int64_t lda, const double *d_B, int64_t ldb,
+                           int32_t *d_e, int32_t *d_f, void *stream);
+
+/* Step 2, slicing: digit s (s = 1..S) of every entry, t_s = rint(r 2^(w s)) -
+ * 2^w rint(r 2^(w (s-1))), r = A_ik 2^-e_i (round half to even), written as
+ * int8 (kind INT8, w = 7) or bf16 (kind BF16, w = 8).  Layout: d_As is
+ * S x M x Kp (row-major, Kp = K rounded up to a multiple of 64, zero padded),
+ * d_Bs is S x N x Kp (B transposed: row j of slice t holds column j of B). */
+int hsumma_split_slices(int64_t M, int64_t N, int64_t K, const double *d_A,
+                        int64_t lda, const double *d_B, int64_t ldb,
+                        const int32_t *d_e, const int32_t *d_f, int kind, int S,
+                        void *d_As, void *d_Bs, void *stream);
+
+/* Number of int32 planes per diagonal that step 3 writes for this K: a
+ * diagonal's exact sum is split into segments whose partial sums stay below
+ * 2^31 in magnitude.  Returns the count (>= 1) or HSUMMA_ERR_ARG. */
+int hsumma_split_planes(int64_t K, int kind, int S);
+
+/* Step 3, the kept pair products (pairs s + t <= S + 1) multiplied on the
+ * tensor cores with HSUMMA's data movement (arguments P..Bouter as in
+ * hsumma_gemm), summed exactly per diagonal d = s + t:
+ * D_d[i][j] = sum_{s+t=d} sum_k a_s[i,k] b_t[k,j] = sum_g d_D[d-2][g][i][j]
+ * over the g = 0..hsumma_split_planes(K, kind, S)-1 int32 planes of d_D
+ * (layout S x planes x M x N).  d_As and d_Bs as written by step 2. */
+int hsumma_split_diagonals(int64_t M, int64_t N, int64_t K, int kind, int S,
+                           const void *d_As, const void *d_Bs, int32_t *d_D,
+                           int P, int Q, int G, int b, int Bouter, void *stream);
+
+/* Step 4, recombination: C_ij = RN(2^(e_i + f_j) sum_d D_d,ij 2^(-w d)), the
+ * exact sum (128-bit integers) rounded once to binary64, ties to even,
+ * subnormal and overflowing results included. */
+int hsumma_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S,
+                           const int32_t *d_D, const int32_t *d_e,
+                           const int32_t *d_f, double *d_C, int64_t ldc,
+                           void *stream);
+
+/* ---- Learned cost model (not in the paper: the paper picks G by sampling a
+ * few runs, Section V-A-1 and Section VI) ---- */
+
+/* MLP 10 -> 64 -> 64 -> 64 -> 1 with exact GELU; parameter vector layout
+ * W1[64][10] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[1][64] b4[1]
+ * (9089 floats).  Forward in fp32: d_X batch x 10, d_y batch predictions;
+ * d_cache (batch x 192 floats of pre-activations) may be NULL. */
+int hsumma_mlp_forward(int batch, const float *d_theta, const float *d_X,
+                       float *d_y, float *d_cache, void *stream);
+
+/* Gradient of mean_i (f(x_i) - t_i)^2 with respect to the parameters (fp32),
+ * and the loss: d_grad 9089 floats, d_loss 1 float. */
+int hsumma_mlp_backward(int batch, const float *d_theta, const float *d_X,
+                        const float *d_target, float *d_grad, float *d_loss,
+                        void *stream);
+
+/* One Adam step (fp32), step number t >= 1, on n parameters. */
+int hsumma_mlp_adam(int n, float *d_theta, const float *d_grad, float *d_m,
+                    float *d_v, int t, float lr, float beta1, float beta2,
+                    float eps, void *stream);
+
+/* Score candidates with the model in bf16 and return the index of the
+ * smallest prediction: d_X n x 10 features (already normalised). */
+int hsumma_mlp_pick(int n, const float *d_theta, const float *d_X,
+                    float *d_pred, int32_t *d_best, void *stream);
+
+/* Load a trained model into the library (host arrays: 9089 parameters, the
+ * 10 feature means and 10 standard deviations) for hsumma_gemm's automatic
+ * choice; NULL theta unloads it. */
+int hsumma_mlp_load(const float *h_theta, const float *h_mean,
+                    const float *h_std);
+
+/* ---- Peak microbenchmarks (roofline denominators) ---- */
+
+typedef enum {
+  HSUMMA_PEAK_DFMA = 0,      /* binary64 FMA on the CUDA cores */
+  HSUMMA_PEAK_DMMA = 1,      /* binary64 mma.sync m16n8k4 */
+  HSUMMA_PEAK_IMMA = 2,      /* int8 mma.sync m16n8k32, int32 accumulate */
+  HSUMMA_PEAK_HMMA_BF16 = 3, /* bf16 mma.sync m16n8k16, fp32 accumulate */
+  HSUMMA_PEAK_TC05_BF16 = 4, /* bf16 tcgen05.mma 128x256x16, fp32 in TMEM */
+  HSUMMA_PEAK_COPY = 5       /* device memory copy (bytes read + written) */
+} hsumma_peak_kind;
+
+/* Run one microbenchmark on every SM and return the rate: flops/s (2 per
+ * multiply-add) or bytes/s for the copy.  `work` scales the run length. */
+int hsumma_peak(int kind, int64_t work, double *rate);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSUMMA_H */

@@ -1,0 +1,272 @@
+"""Python binding of libhsumma (single-GPU Hierarchical SUMMA for sm_103a).
+
+Argument marshalling only: every step of C = A x B runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  The library must have
+been built (paper_1306_4161_gb300._build.build(), or __graft_entry__.build());
+importing works without it, but every call raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "_build", "libhsumma.so")
+HEADER = os.path.join(ROOT, "include", "hsumma.h")
+
+FP64, INT8_SLICES, BF16_SLICES = 0, 1, 2
+KINDS = {"fp64": FP64, "int8": INT8_SLICES, "bf16": BF16_SLICES}
+PEAKS = {"dfma": 0, "dmma": 1, "imma": 2, "hmma_bf16": 3, "tc05_bf16": 4, "copy": 5}
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSUPPORTED", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
+          -5: "ERR_NOT_INIT", -6: "ERR_NONFINITE"}
+N_MLP_PARAMS = 9089
+
+
+class HsummaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("a_loaded", "a_delivered", "b_loaded", "b_delivered", "l2_prefetch",
+                 "tma_loads")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+_i64, _i32, _vp, _dp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p
+
+_SIGS = {
+    "hsumma_init": ([_i32], _i32),
+    "hsumma_finalize": ([], None),
+    "hsumma_group_shape": ([_i32, _i32, _i32] + [ctypes.POINTER(ctypes.c_int)] * 4, _i32),
+    "hsumma_workspace_size": ([_i64, _i64, _i64, _i32, ctypes.POINTER(ctypes.c_size_t)], _i32),
+    "hsumma_gemm": ([_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64] + [_i32] * 6 + [_vp],
+                    _i32),
+    "hsumma_gemm_host": ([_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64] + [_i32] * 6
+                         + [_vp], _i32),
+    "hsumma_get_counters": ([ctypes.POINTER(Counters)], _i32),
+    "hsumma_sync": ([_vp], _i32),
+    "hsumma_last_error": ([], ctypes.c_char_p),
+    "hsumma_split_exponents": ([_i64, _i64, _i64, _dp, _i64, _dp, _i64, _vp, _vp, _vp], _i32),
+    "hsumma_split_slices": ([_i64, _i64, _i64, _dp, _i64, _dp, _i64, _vp, _vp, _i32, _i32,
+                             _vp, _vp, _vp], _i32),
+    "hsumma_split_planes": ([_i64, _i32, _i32], _i32),
+    "hsumma_split_diagonals": ([_i64, _i64, _i64, _i32, _i32, _vp, _vp, _vp] + [_i32] * 5
+                               + [_vp], _i32),
+    "hsumma_split_recombine": ([_i64, _i64, _i64, _i32, _i32, _vp, _vp, _vp, _vp, _i64, _vp],
+                               _i32),
+    "hsumma_mlp_forward": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
+    "hsumma_mlp_backward": ([_i32, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "hsumma_mlp_adam": ([_i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float,
+                         ctypes.c_float, ctypes.c_float, _vp], _i32),
+    "hsumma_mlp_pick": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
+    "hsumma_mlp_load": ([_vp, _vp, _vp], _i32),
+    "hsumma_peak": ([_i32, _i64, ctypes.POINTER(ctypes.c_double)], _i32),
+}
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/hsumma.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hsumma_\w+)\s*\(", text)))
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libhsumma is not built ({LIB_PATH} missing); run "
+                                   "paper_1306_4161_gb300._build.build()")
+            l = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(l, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = l
+    return _lib
+
+
+def last_error() -> str:
+    return lib().hsumma_last_error().decode()
+
+
+def _check(status: int):
+    if status != 0:
+        raise HsummaError(status, last_error())
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+_inited = None
+
+
+def init(device: int = 0):
+    global _inited
+    _check(lib().hsumma_init(device))
+    _inited = device
+
+
+def _ensure_init(t=None):
+    if _inited is None:
+        dev = t.device.index if (t is not None and t.device.index is not None) else 0
+        init(dev)
+
+
+def finalize():
+    global _inited
+    lib().hsumma_finalize()
+    _inited = None
+
+
+def mode_code(kind: str | int, slices: int = 0) -> int:
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    return k | (int(slices) << 8)
+
+
+def group_shape(P: int, Q: int, G: int):
+    """(I, J, cluster_m, cluster_n) for a P x Q grid with G groups."""
+    out = [ctypes.c_int() for _ in range(4)]
+    _check(lib().hsumma_group_shape(P, Q, G, *[ctypes.byref(o) for o in out]))
+    return tuple(o.value for o in out)
+
+
+def workspace_size(M, N, K, kind="fp64", slices=0) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().hsumma_workspace_size(M, N, K, mode_code(kind, slices), ctypes.byref(b)))
+    return b.value
+
+
+def _check_f64(t, name):
+    import torch
+    if t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be 2-D with unit column stride")
+
+
+def gemm(A, B, *, P, Q, G, b, Bouter, kind="fp64", slices=0, out=None, stream=None):
+    """C = A x B by HSUMMA on a virtual P x Q grid with G groups (torch tensors on
+    the GPU, float64, row-major)."""
+    import torch
+    _check_f64(A, "A")
+    _check_f64(B, "B")
+    M, K = A.shape
+    K2, N = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    _ensure_init(A)
+    C = out if out is not None else torch.empty((M, N), dtype=torch.float64, device=A.device)
+    _check_f64(C, "C")
+    _check(lib().hsumma_gemm(M, N, K, A.data_ptr(), A.stride(0) if M else max(K, 2),
+                             B.data_ptr(), B.stride(0) if K else max(N, 2), C.data_ptr(),
+                             C.stride(0) if M else max(N, 2), P, Q, G, b, Bouter,
+                             mode_code(kind, slices), _stream_ptr(stream)))
+    return C
+
+
+def gemm_host(A, B, C, *, P, Q, G, b, Bouter, kind="fp64", slices=0, stream=None):
+    """The same product from host memory (numpy or CPU torch float64 arrays,
+    row-major); C is written in place."""
+    def ptr_ld(x):
+        if hasattr(x, "data_ptr"):
+            return x.data_ptr(), x.stride(0)
+        return x.ctypes.data, x.strides[0] // 8
+    (pa, la), (pb, lb), (pc, lc) = ptr_ld(A), ptr_ld(B), ptr_ld(C)
+    M, K = A.shape
+    N = B.shape[1]
+    _ensure_init()
+    _check(lib().hsumma_gemm_host(M, N, K, pa, la, pb, lb, pc, lc, P, Q, G, b, Bouter,
+                                  mode_code(kind, slices), _stream_ptr(stream)))
+    return C
+
+
+def sync(stream=None):
+    _check(lib().hsumma_sync(_stream_ptr(stream)))
+
+
+def counters() -> dict:
+    c = Counters()
+    _check(lib().hsumma_get_counters(ctypes.byref(c)))
+    return c.as_dict()
+
+
+# ---- split path, step by step ----
+def split_exponents(A, B, stream=None):
+    import torch
+    _check_f64(A, "A")
+    _check_f64(B, "B")
+    _ensure_init(A)
+    M, K = A.shape
+    N = B.shape[1]
+    e = torch.empty(M, dtype=torch.int32, device=A.device)
+    f = torch.empty(N, dtype=torch.int32, device=A.device)
+    _check(lib().hsumma_split_exponents(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(),
+                                        B.stride(0), e.data_ptr(), f.data_ptr(),
+                                        _stream_ptr(stream)))
+    return e, f
+
+
+def split_slices(A, B, e, f, kind, S, stream=None):
+    import torch
+    _ensure_init(A)
+    M, K = A.shape
+    N = B.shape[1]
+    Kp = (K + 63) // 64 * 64
+    dt = torch.int8 if kind == "int8" else torch.bfloat16
+    As = torch.empty((S, M, Kp), dtype=dt, device=A.device)
+    Bs = torch.empty((S, N, Kp), dtype=dt, device=A.device)
+    _check(lib().hsumma_split_slices(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(),
+                                     B.stride(0), e.data_ptr(), f.data_ptr(), KINDS[kind], S,
+                                     As.data_ptr(), Bs.data_ptr(), _stream_ptr(stream)))
+    return As, Bs
+
+
+def split_planes(K, kind, S) -> int:
+    n = lib().hsumma_split_planes(K, KINDS[kind], S)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def split_diagonals(As, Bs, M, N, K, kind, S, *, P, Q, G, b, Bouter, stream=None):
+    import torch
+    _ensure_init(As)
+    g = split_planes(K, kind, S)
+    D = torch.empty((S, g, M, N), dtype=torch.int32, device=As.device)
+    _check(lib().hsumma_split_diagonals(M, N, K, KINDS[kind], S, As.data_ptr(), Bs.data_ptr(),
+                                        D.data_ptr(), P, Q, G, b, Bouter,
+                                        _stream_ptr(stream)))
+    return D
+
+
+def split_recombine(D, e, f, M, N, K, kind, S, stream=None):
+    import torch
+    _ensure_init(D)
+    C = torch.empty((M, N), dtype=torch.float64, device=D.device)
+    _check(lib().hsumma_split_recombine(M, N, K, KINDS[kind], S, D.data_ptr(), e.data_ptr(),
+                                        f.data_ptr(), C.data_ptr(), max(N, 2),
+                                        _stream_ptr(stream)))
+    return C
+
+
+def peak(kind: str, work: int) -> float:
+    _ensure_init()
+    r = ctypes.c_double()
+    _check(lib().hsumma_peak(PEAKS[kind], work, ctypes.byref(r)))
+    return r.value

@@ -1,0 +1,620 @@
+// C ABI of libhsumma: argument checks, group resolution (Section III), the
+// choice of kernels, the device error word, counters and workspace.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/hsumma.h"
+#include "internal.h"
+
+namespace hs {
+
+namespace {
+thread_local char g_err[512] = "";
+std::mutex g_mu;
+DeviceState g_state;
+bool g_init = false;
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+}  // namespace
+
+DeviceState &state() { return g_state; }
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return HSUMMA_ERR_CUDA;
+}
+
+bool encode_tmap_2d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
+                    const void *base, uint64_t inner, uint64_t outer,
+                    uint64_t row_stride_elems, uint32_t box_inner, uint32_t box_outer,
+                    CUtensorMapSwizzle swizzle) {
+  if (!g_encode) {
+    set_error("tensor-map encoder unavailable (hsumma_init not called?)");
+    return false;
+  }
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_stride_elems * (uint64_t)elem_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(out, dtype, 2, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d): dims %llu x %llu, stride %llu B, box %u x %u",
+              (int)r, (unsigned long long)inner, (unsigned long long)outer,
+              (unsigned long long)strides[0], box_inner, box_outer);
+    return false;
+  }
+  return true;
+}
+
+bool encode_tmap_3d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
+                    const void *base, uint64_t inner, uint64_t rows, uint64_t planes,
+                    uint32_t box_inner, uint32_t box_rows, CUtensorMapSwizzle swizzle) {
+  if (!g_encode) {
+    set_error("tensor-map encoder unavailable (hsumma_init not called?)");
+    return false;
+  }
+  cuuint64_t dims[3] = {inner, rows, planes};
+  cuuint64_t strides[2] = {inner * (uint64_t)elem_bytes, inner * rows * (uint64_t)elem_bytes};
+  cuuint32_t box[3] = {box_inner, box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(out, dtype, 3, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (3-D) failed (%d): %llu x %llu x %llu, box %u x %u",
+              (int)r, (unsigned long long)inner, (unsigned long long)rows,
+              (unsigned long long)planes, box_inner, box_rows);
+    return false;
+  }
+  return true;
+}
+
+static int launch_split_diagonals(const GridPlan &g, int kind, int S, const void *As,
+                                  const void *Bs, int32_t *D, cudaStream_t s) {
+  if (kind == HSUMMA_BF16_SLICES) return launch_split_bf16(g, S, As, Bs, D, s);
+  return launch_split_int8(g, S, As, Bs, D, s);
+}
+
+// Section III: I x J groups, I | P and J | Q; the most square in-group grid,
+// ties to the smaller I.  Realised as one cluster when the group has 2..limit
+// CTAs, otherwise flat.
+static int resolve_groups(int P, int Q, int G, int limit, int *I, int *J, int *cm, int *cn) {
+  if (P < 1 || Q < 1 || G < 1) {
+    set_error("P, Q and G must be positive (got %d, %d, %d)", P, Q, G);
+    return HSUMMA_ERR_ARG;
+  }
+  double best = -1.0;
+  int bi = 0, bj = 0;
+  for (int i = 1; i <= G; ++i) {
+    if (G % i) continue;
+    const int j = G / i;
+    if (P % i || Q % j) continue;
+    const double ratio = ((double)P / i) / ((double)Q / j);
+    const double key = ratio >= 1.0 ? ratio : 1.0 / ratio;
+    if (best < 0.0 || key < best * (1.0 - 1e-12)) {
+      best = key;
+      bi = i;
+      bj = j;
+    }
+  }
+  if (!bi) {
+    set_error("G = %d has no factorisation I x J with I | P = %d and J | Q = %d", G, P, Q);
+    return HSUMMA_ERR_ARG;
+  }
+  *I = bi;
+  *J = bj;
+  const int pi = P / bi, qj = Q / bj;
+  if (pi * qj > 1 && pi * qj <= limit) {
+    *cm = pi;
+    *cn = qj;
+  } else {
+    *cm = 1;
+    *cn = 1;
+  }
+  return HSUMMA_OK;
+}
+
+static int check_matrix_args(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda,
+                             const void *B, int64_t ldb, const void *C, int64_t ldc) {
+  if (M < 0 || N < 0 || K < 0) {
+    set_error("negative size (M=%lld N=%lld K=%lld)", (long long)M, (long long)N,
+              (long long)K);
+    return HSUMMA_ERR_ARG;
+  }
+  if (M > (1ll << 31) || N > (1ll << 31) || K > (1ll << 31)) {
+    set_error("sizes above 2^31 are not supported");
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  if (lda < (K > 0 ? K : 1) || ldb < (N > 0 ? N : 1) || ldc < (N > 0 ? N : 1)) {
+    set_error("leading dimensions too small (lda=%lld ldb=%lld ldc=%lld)", (long long)lda,
+              (long long)ldb, (long long)ldc);
+    return HSUMMA_ERR_ARG;
+  }
+  if ((lda | ldb | ldc) & 1) {
+    set_error("leading dimensions must be even (16-byte row strides)");
+    return HSUMMA_ERR_ARG;
+  }
+  if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15) {
+    set_error("matrix base pointers must be 16-byte aligned");
+    return HSUMMA_ERR_ARG;
+  }
+  if ((M && K && !A) || (K && N && !B) || (M && N && !C)) {
+    set_error("null matrix pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  return HSUMMA_OK;
+}
+
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" {
+
+int hsumma_init(int device) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_init && g_state.device == device) return HSUMMA_OK;
+  if (g_init) {
+    set_error("already initialised on device %d", g_state.device);
+    return HSUMMA_ERR_ARG;
+  }
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3) {
+    set_error("device %d is sm_%d%d; this build targets sm_103a", device, prop.major,
+              prop.minor);
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  cudaDriverEntryPointQueryResult q;
+  void *fn = nullptr;
+  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                       cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    set_error("cuTensorMapEncodeTiled entry point not found");
+    return HSUMMA_ERR_CUDA;
+  }
+  g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  g_state = DeviceState();
+  g_state.device = device;
+  g_state.sm_count = prop.multiProcessorCount;
+  e = cudaMalloc(&g_state.d_counters, 8 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(counters)");
+  e = cudaMalloc(&g_state.d_status, 4 * sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
+  cudaMemset(g_state.d_counters, 0, 8 * sizeof(unsigned long long));
+  cudaMemset(g_state.d_status, 0, 4 * sizeof(int));
+  int lim = 16, l2 = 16;
+  int st = fp64_cluster_limit(&lim);
+  if (st != HSUMMA_OK) return st;
+  st = bf16_cluster_limit(&l2);
+  if (st != HSUMMA_OK) return st;
+  if (l2 < lim) lim = l2;
+  st = int8_cluster_limit(&l2);
+  if (st != HSUMMA_OK) return st;
+  if (l2 < lim) lim = l2;
+  g_state.cluster_limit = lim;
+  if (g_state.cluster_limit > 16) g_state.cluster_limit = 16;
+  if (g_state.cluster_limit < 1) g_state.cluster_limit = 1;
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  g_init = true;
+  return HSUMMA_OK;
+}
+
+void hsumma_finalize(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_init) return;
+  cudaDeviceSynchronize();
+  cudaFree(g_state.d_counters);
+  cudaFree(g_state.d_status);
+  if (g_state.workspace) cudaFree(g_state.workspace);
+  if (g_state.host_staging) cudaFree(g_state.host_staging);
+  g_state = DeviceState();
+  g_init = false;
+}
+
+const char *hsumma_last_error(void) { return g_err; }
+
+int hsumma_group_shape(int P, int Q, int G, int *I, int *J, int *cluster_m, int *cluster_n) {
+  if (!I || !J || !cluster_m || !cluster_n) {
+    set_error("null output pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  const int limit = g_init ? g_state.cluster_limit : 16;
+  return resolve_groups(P, Q, G, limit, I, J, cluster_m, cluster_n);
+}
+
+static int split_kind_and_S(int mode, int *kind, int *S) {
+  *kind = mode & 0xff;
+  *S = (mode >> 8) & 0xff;
+  if (*kind == HSUMMA_FP64) return HSUMMA_OK;
+  if (*kind == HSUMMA_INT8_SLICES) {
+    if (*S < 1 || *S > 8) {
+      set_error("INT8 slices: S must be in 1..8 (got %d)", *S);
+      return HSUMMA_ERR_ARG;
+    }
+    return HSUMMA_OK;
+  }
+  if (*kind == HSUMMA_BF16_SLICES) {
+    if (*S < 1 || *S > 7) {
+      set_error("BF16 slices: S must be in 1..7 (got %d)", *S);
+      return HSUMMA_ERR_ARG;
+    }
+    return HSUMMA_OK;
+  }
+  set_error("unknown mode kind %d", *kind);
+  return HSUMMA_ERR_ARG;
+}
+
+// Split-path workspace: e (M int32), f (N int32), A slices S x M x Kp,
+// B slices S x N x Kp (1 or 2 bytes), exact diagonal sums S x nseg x M x N int32.
+static size_t split_ws_bytes(int64_t M, int64_t N, int64_t K, int kind, int S) {
+  const int64_t Kp = ceil_div(K, 64) * 64;
+  const size_t eb = kind == HSUMMA_INT8_SLICES ? 1 : 2;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  return al(M * 4) + al(N * 4) + al(S * M * Kp * eb) + al(S * N * Kp * eb) +
+         al((size_t)S * split_planes(K, S, kind) * M * N * 4);
+}
+
+int hsumma_workspace_size(int64_t M, int64_t N, int64_t K, int mode, size_t *bytes) {
+  if (!bytes) {
+    set_error("null output pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  int kind, S;
+  int st = split_kind_and_S(mode, &kind, &S);
+  if (st != HSUMMA_OK) return st;
+  if (M < 0 || N < 0 || K < 0) {
+    set_error("negative size");
+    return HSUMMA_ERR_ARG;
+  }
+  *bytes = kind == HSUMMA_FP64 ? 0 : split_ws_bytes(M, N, K, kind, S);
+  return HSUMMA_OK;
+}
+
+static int ensure_workspace(size_t bytes) {
+  if (g_state.workspace_bytes >= bytes) return HSUMMA_OK;
+  if (g_state.workspace) {
+    cudaDeviceSynchronize();
+    cudaFree(g_state.workspace);
+    g_state.workspace = nullptr;
+    g_state.workspace_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&g_state.workspace, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+  g_state.workspace_bytes = bytes;
+  return HSUMMA_OK;
+}
+
+static int make_plan(int64_t M, int64_t N, int64_t K, int P, int Q, int G, int b, int Bo,
+                     int kind, GridPlan *g) {
+  if (P > 65535 || Q > 65535) {
+    set_error("P and Q must be at most 65535");
+    return HSUMMA_ERR_ARG;
+  }
+  int I, J, cm, cn;
+  int st = resolve_groups(P, Q, G, g_state.cluster_limit, &I, &J, &cm, &cn);
+  if (st != HSUMMA_OK) return st;
+  const int bmul = kind == HSUMMA_FP64 ? 16 : 64;
+  if (b < bmul || b > 256 || b % bmul) {
+    set_error("inner block b = %d must be a multiple of %d in %d..256", b, bmul, bmul);
+    return HSUMMA_ERR_ARG;
+  }
+  if (Bo < b || Bo % b) {
+    set_error("outer block B = %d must be a multiple of b = %d (b <= B)", Bo, b);
+    return HSUMMA_ERR_ARG;
+  }
+  g->M = M;
+  g->N = N;
+  g->K = K;
+  g->P = P;
+  g->Q = Q;
+  g->G = G;
+  g->I = I;
+  g->J = J;
+  g->cm = cm;
+  g->cn = cn;
+  g->Mt = ceil_div(M, P);
+  // block width rounded up so that every block starts at a column whose byte
+  // offset the Tensor Memory Accelerator accepts (binary64: even columns) and
+  // the split path's vector stores stay aligned (multiples of 8); the number of
+  // sub-tiles per block is unchanged (tile widths are multiples of 8)
+  const int64_t nal = kind == HSUMMA_FP64 ? 2 : 8;
+  g->Nt = ceil_div(ceil_div(N, Q), nal) * nal;
+  g->Kq = K > 0 ? ceil_div(K, Q) : 1;
+  g->Kp = K > 0 ? ceil_div(K, P) : 1;
+  g->nsub_m = 0;
+  g->nsub_n = 0;
+  g->b = b;
+  g->Bo = Bo;
+  if (g->Kq < 1) g->Kq = 1;
+  if (g->Kp < 1) g->Kp = 1;
+  return HSUMMA_OK;
+}
+
+int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                const double *B, int64_t ldb, double *C, int64_t ldc, int P, int Q, int G,
+                int b, int Bouter, int mode, void *stream) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  int st = check_matrix_args(M, N, K, A, lda, B, ldb, C, ldc);
+  if (st != HSUMMA_OK) return st;
+  int kind, S;
+  st = split_kind_and_S(mode, &kind, &S);
+  if (st != HSUMMA_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (P == 0 && Q == 0 && G == 0 && b == 0 && Bouter == 0) {
+    set_error("automatic configuration needs a loaded cost model (not built yet)");
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  GridPlan g;
+  st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, &g);
+  if (st != HSUMMA_OK) return st;
+  cudaError_t e = cudaMemsetAsync(g_state.d_counters, 0, 8 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+  if (M == 0 || N == 0) return HSUMMA_OK;
+  if (K == 0) {
+    e = cudaMemset2DAsync(C, ldc * 8, 0, N * 8, M, s);
+    return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "cudaMemset2DAsync");
+  }
+  if (kind == HSUMMA_FP64) return launch_fp64_hsumma(g, A, lda, B, ldb, C, ldc, s);
+
+  // split path: exponents, slices, exact diagonal sums, recombination
+  // exactness of the recombination: a diagonal's planes sum to at most
+  // S K 2^14 in magnitude, which must fit 63 bits
+  if ((double)S * (double)K * 16384.0 >= 9.0e18) {
+    set_error("K = %lld too large for exact slice sums with S = %d", (long long)K, S);
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  const size_t need = split_ws_bytes(M, N, K, kind, S);
+  st = ensure_workspace(need);
+  if (st != HSUMMA_OK) return st;
+  const int64_t Kp = ceil_div(K, 64) * 64;
+  const size_t eb = kind == HSUMMA_INT8_SLICES ? 1 : 2;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  uint8_t *ws = reinterpret_cast<uint8_t *>(g_state.workspace);
+  int32_t *e_rows = reinterpret_cast<int32_t *>(ws);
+  ws += al(M * 4);
+  int32_t *f_cols = reinterpret_cast<int32_t *>(ws);
+  ws += al(N * 4);
+  void *As = ws;
+  ws += al(S * M * Kp * eb);
+  void *Bs = ws;
+  ws += al(S * N * Kp * eb);
+  int32_t *D = reinterpret_cast<int32_t *>(ws);
+  st = launch_split_exponents(M, N, K, A, lda, B, ldb, e_rows, f_cols, s);
+  if (st != HSUMMA_OK) return st;
+  st = launch_split_slices(M, N, K, A, lda, B, ldb, e_rows, f_cols, kind, S, As, Bs, s);
+  if (st != HSUMMA_OK) return st;
+  st = launch_split_diagonals(g, kind, S, As, Bs, D, s);
+  if (st != HSUMMA_OK) return st;
+  return launch_split_recombine(M, N, K, kind, S, D, e_rows, f_cols, C, ldc, s);
+}
+
+int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t lda,
+                     const double *hB, int64_t ldb, double *hC, int64_t ldc, int P, int Q,
+                     int G, int b, int Bouter, int mode, void *stream) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  int st = check_matrix_args(M, N, K, hA, lda, hB, ldb, hC, ldc);
+  if (st != HSUMMA_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t bA = al((size_t)M * lda * 8), bB = al((size_t)K * ldb * 8),
+               bC = al((size_t)M * ldc * 8);
+  if (g_state.host_staging_bytes < bA + bB + bC) {
+    if (g_state.host_staging) {
+      cudaDeviceSynchronize();
+      cudaFree(g_state.host_staging);
+      g_state.host_staging = nullptr;
+      g_state.host_staging_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&g_state.host_staging, bA + bB + bC);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(host staging)");
+    g_state.host_staging_bytes = bA + bB + bC;
+  }
+  uint8_t *base = reinterpret_cast<uint8_t *>(g_state.host_staging);
+  double *dA = reinterpret_cast<double *>(base);
+  double *dB = reinterpret_cast<double *>(base + bA);
+  double *dC = reinterpret_cast<double *>(base + bA + bB);
+  cudaError_t e;
+  if (M && K) {
+    e = cudaMemcpyAsync(dA, hA, (size_t)M * lda * 8, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(A)");
+  }
+  if (K && N) {
+    e = cudaMemcpyAsync(dB, hB, (size_t)K * ldb * 8, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(B)");
+  }
+  st = hsumma_gemm(M, N, K, dA, lda, dB, ldb, dC, ldc, P, Q, G, b, Bouter, mode, stream);
+  if (st != HSUMMA_OK) return st;
+  if (M && N) {
+    e = cudaMemcpyAsync(hC, dC, (size_t)M * ldc * 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(C)");
+  }
+  return hsumma_sync(stream);
+}
+
+int hsumma_get_counters(hsumma_counters *out) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  if (!out) {
+    set_error("null output pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  unsigned long long h[8];
+  cudaError_t e = cudaMemcpy(h, g_state.d_counters, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(counters)");
+  out->a_loaded = h[0];
+  out->a_delivered = h[1];
+  out->b_loaded = h[2];
+  out->b_delivered = h[3];
+  out->l2_prefetch = h[4];
+  out->tma_loads = h[5];
+  return HSUMMA_OK;
+}
+
+int hsumma_sync(void *stream) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "kernel execution");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  int h[4];
+  e = cudaMemcpy(h, g_state.d_status, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+  if (h[0] != 0) {
+    cudaMemset(g_state.d_status, 0, sizeof(h));
+    static const char *sites[] = {"?", "stage fill", "stage release", "accumulator fill",
+                                  "accumulator drain", "non-finite input"};
+    set_error("device error %d at %s (block %d)", h[0],
+              (h[1] >= 0 && h[1] <= 5) ? sites[h[1]] : "?", h[2]);
+    return h[0];
+  }
+  return HSUMMA_OK;
+}
+
+int hsumma_split_exponents(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                           const double *B, int64_t ldb, int32_t *e, int32_t *f,
+                           void *stream) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  int st = check_matrix_args(M, N, K, A, lda, B, ldb, A, lda);
+  if (st != HSUMMA_OK) return st;
+  if ((M && !e) || (N && !f)) {
+    set_error("null exponent pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  return launch_split_exponents(M, N, K, A, lda, B, ldb, e, f,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+int hsumma_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                        const double *B, int64_t ldb, const int32_t *e, const int32_t *f,
+                        int kind, int S, void *As, void *Bs, void *stream) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  int st = check_matrix_args(M, N, K, A, lda, B, ldb, A, lda);
+  if (st != HSUMMA_OK) return st;
+  int k2, s2;
+  st = split_kind_and_S(HSUMMA_MODE(kind, S), &k2, &s2);
+  if (st != HSUMMA_OK) return st;
+  if (kind == HSUMMA_FP64) {
+    set_error("slices need a split kind");
+    return HSUMMA_ERR_ARG;
+  }
+  if ((((uintptr_t)As) | ((uintptr_t)Bs)) & 15) {
+    set_error("slice buffers must be 16-byte aligned");
+    return HSUMMA_ERR_ARG;
+  }
+  return launch_split_slices(M, N, K, A, lda, B, ldb, e, f, kind, S, As, Bs,
+                             reinterpret_cast<cudaStream_t>(stream));
+}
+
+int hsumma_split_planes(int64_t K, int kind, int S) {
+  if (K < 0 || S < 1 || S > 8 || (kind != HSUMMA_INT8_SLICES && kind != HSUMMA_BF16_SLICES)) {
+    set_error("bad arguments");
+    return HSUMMA_ERR_ARG;
+  }
+  return split_planes(K, S, kind);
+}
+
+int hsumma_split_diagonals(int64_t M, int64_t N, int64_t K, int kind, int S, const void *As,
+                           const void *Bs, int32_t *D, int P, int Q, int G, int b,
+                           int Bouter, void *stream) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  int k2, s2;
+  int st = split_kind_and_S(HSUMMA_MODE(kind, S), &k2, &s2);
+  if (st != HSUMMA_OK) return st;
+  if (kind == HSUMMA_FP64) {
+    set_error("diagonal sums need a split kind");
+    return HSUMMA_ERR_ARG;
+  }
+  if (M < 0 || N < 0 || K < 0 || (M && N && !D)) {
+    set_error("bad sizes or null output");
+    return HSUMMA_ERR_ARG;
+  }
+  GridPlan g;
+  st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, &g);
+  if (st != HSUMMA_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(g_state.d_counters, 0, 8 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+  if (M == 0 || N == 0) return HSUMMA_OK;
+  return launch_split_diagonals(g, kind, S, As, Bs, D, s);
+}
+
+int hsumma_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, const int32_t *D,
+                           const int32_t *e, const int32_t *f, double *C, int64_t ldc,
+                           void *stream) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  int k2, s2;
+  int st = split_kind_and_S(HSUMMA_MODE(kind, S), &k2, &s2);
+  if (st != HSUMMA_OK) return st;
+  if (M < 0 || N < 0 || ldc < N) {
+    set_error("bad sizes");
+    return HSUMMA_ERR_ARG;
+  }
+  if (M == 0 || N == 0) return HSUMMA_OK;
+  if (K == 0) {
+    cudaError_t e2 = cudaMemset2DAsync(C, ldc * 8, 0, N * 8, M,
+                                       reinterpret_cast<cudaStream_t>(stream));
+    return e2 == cudaSuccess ? HSUMMA_OK : cuda_fail(e2, "cudaMemset2DAsync");
+  }
+  return launch_split_recombine(M, N, K, kind, S, D, e, f, C, ldc,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+int hsumma_peak(int kind, int64_t work, double *rate) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  if (!rate || work <= 0) {
+    set_error("bad arguments");
+    return HSUMMA_ERR_ARG;
+  }
+  return run_peak(kind, work, rate);
+}
+
+}  // extern "C"

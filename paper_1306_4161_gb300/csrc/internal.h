@@ -1,0 +1,87 @@
+// Host-side declarations shared by the translation units of libhsumma.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+namespace hs {
+
+// Result of the host-side group resolution (Section III) and its realisation.
+struct GridPlan {
+  int64_t M, N, K;
+  int P, Q, G, I, J;
+  int cm, cn;            // realised cluster: rows x cols of CTAs (1 x 1 = flat)
+  int64_t Mt, Nt;        // block sizes ceil(M/P), ceil(N/Q)
+  int64_t Kq, Kp;        // ceil(K/Q), ceil(K/P): owner ranges of outer panels
+  int nsub_m, nsub_n;    // sub-tiles per block
+  int b, Bo;             // inner / outer panel widths
+};
+
+struct DeviceState {
+  int device = -1;
+  int sm_count = 0;
+  int cluster_limit = 16;
+  unsigned long long *d_counters = nullptr;  // 8 x u64
+  int *d_status = nullptr;                   // 4 x int
+  void *workspace = nullptr;
+  size_t workspace_bytes = 0;
+  void *host_staging = nullptr;              // device buffers of hsumma_gemm_host
+  size_t host_staging_bytes = 0;
+};
+
+DeviceState &state();
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+// Tensor-map encoding through the driver entry point (no link to libcuda).
+bool encode_tmap_2d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
+                    const void *base, uint64_t inner, uint64_t outer,
+                    uint64_t row_stride_elems, uint32_t box_inner, uint32_t box_outer,
+                    CUtensorMapSwizzle swizzle);
+
+// 3-D view {inner, rows, planes} of a planes x rows x inner array (row-major).
+bool encode_tmap_3d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
+                    const void *base, uint64_t inner, uint64_t rows, uint64_t planes,
+                    uint32_t box_inner, uint32_t box_rows, CUtensorMapSwizzle swizzle);
+
+// Launchers (return an hsumma_status).
+int launch_fp64_hsumma(const GridPlan &g, const double *A, int64_t lda, const double *B,
+                       int64_t ldb, double *C, int64_t ldc, cudaStream_t s);
+int fp64_cluster_limit(int *limit);
+
+int launch_split_exponents(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                           const double *B, int64_t ldb, int32_t *e, int32_t *f,
+                           cudaStream_t s);
+int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                        const double *B, int64_t ldb, const int32_t *e,
+                        const int32_t *f, int kind, int S, void *As, void *Bs,
+                        cudaStream_t s);
+// Exact diagonal sums are stored as int32 planes D[d-2][seg][M][N]: a diagonal's
+// sum over its (d-1) K products is cut into segments whose partial sums stay
+// below 2^31 (bf16: 127 chunks of 1024 products of magnitude <= 2^14; int8:
+// 2^17 products of magnitude <= 2^12 per segment).
+constexpr int kSegChunks = 127;
+inline int split_planes(int64_t K, int S, int kind = 2) {
+  const int64_t Kp = (K + 63) / 64 * 64;
+  const int64_t prods = (int64_t)S * Kp;     // longest diagonal: S pairs
+  const int64_t per_seg = kind == 1 ? (int64_t)1 << 18 : (int64_t)kSegChunks * 1024;
+  const int64_t n = (prods + per_seg - 1) / per_seg;
+  return n < 1 ? 1 : (int)n;
+}
+int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, int32_t *D,
+                      cudaStream_t s);
+int launch_split_int8(const GridPlan &g, int S, const void *As, const void *Bs, int32_t *D,
+                      cudaStream_t s);
+int bf16_cluster_limit(int *limit);
+int int8_cluster_limit(int *limit);
+int launch_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, const int32_t *D,
+                           const int32_t *e, const int32_t *f, double *C, int64_t ldc,
+                           cudaStream_t s);
+
+int run_peak(int kind, int64_t work, double *rate);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace hs

@@ -1,0 +1,436 @@
+// Split-precision HSUMMA, step 3 with bf16 slices on the tcgen05 tensor cores.
+//
+// For every C block the kernel forms the exact diagonal sums
+//     D_d = sum_{s+t=d} A_s B_t,   d = 2 .. S+1,
+// of the bf16 digit slices (integers of magnitude <= 128), with the same
+// HSUMMA data movement as the binary64 kernel: one CTA per virtual processor
+// (Section III), b-wide panels of each slice multicast inside the group
+// cluster (inner level, Figure 4), outer panels staged into L2 by their owners
+// (outer level, Figure 3).  The local update runs as tcgen05.mma
+// (128 x 256 x 16, bf16 x bf16 -> fp32 in tensor memory).
+//
+// Exactness: a product of two digits is an integer of magnitude <= 2^14, so an
+// fp32 accumulator that sums at most 1024 of them per element stays an integer
+// of magnitude <= 2^24 and is exact.  The accumulator is therefore drained every
+// 16 k-stages of 64 ("chunk", 1024 products, pairs of the same diagonal
+// concatenated along k) into int32 registers.  A diagonal is cut into segments
+// of at most 127 chunks (sums <= 127 * 2^24 < 2^31); each segment's exact int32
+// sums are stored as one plane of the output, D[d-2][seg][i][j], and the
+// recombination adds the planes of a diagonal exactly.
+//
+// Roles (320 threads): warp 0 issues the copies, warp 1 owns tensor memory and
+// issues the MMAs, warps 2..9 drain the accumulators (two warps per 32-lane
+// quarter of tensor memory, 128 columns each; 128 int32 sums per thread).  Shared memory: 4 stages of
+// 16 KB (A, 128 x 64) + 32 KB (B, 256 x 64).  Tensor memory: two 128 x 256 fp32
+// accumulators (512 columns), one filled while the other drains.
+#include "internal.h"
+#include "ptx.cuh"
+#include "tc05.cuh"
+#include "../../include/hsumma.h"
+
+namespace hs {
+namespace {
+
+constexpr int TM = 128, TN = 256, BKS = 64, STAGES = 4;
+constexpr int A_BYTES = TM * BKS * 2, B_BYTES = TN * BKS * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int CH = 16;                 // k-stages per accumulator chunk
+constexpr int NEPI = 8;                // draining warps
+constexpr int NTHREADS = (2 + NEPI) * 32;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t IDESC = idesc_bf16_f32(TM, TN);
+
+struct SplitParams {
+  int32_t *D;
+  int64_t M, N, K, Kpad, Mt, Nt, Kq, Kp;
+  int P, Q, cm, cn, nsub_m, nsub_n, Bo, S, nkb, seg_chunks, nseg;
+  unsigned long long *counters;
+  int *status;
+};
+
+__device__ __forceinline__ int64_t span(int64_t lo, int64_t hi, int64_t a, int64_t b) {
+  const int64_t x = a > lo ? a : lo, y = b < hi ? b : hi;
+  return y > x ? y - x : 0;
+}
+
+// wait that also gives up as soon as another role of the CTA has aborted
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
+                                              volatile int *abort_flag, bool cluster_scope) {
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))
+      return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    bf16_diag_kernel(const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmApf,
+                     const __grid_constant__ CUtensorMap tmBpf, const SplitParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  uint64_t *full = bars, *empty = bars + STAGES;
+  uint64_t *acc_full = bars + 2 * STAGES, *acc_empty = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.y, c = blockIdx.x;
+  const int cx = (int)cluster_ctaid_x(), cy = (int)cluster_ctaid_y();
+  const int cn = p.cn, cm = p.cm;
+  const uint16_t row_mask = (uint16_t)(((1u << cn) - 1u) << (cy * cn));
+  uint16_t col_mask = 0;
+  for (int y = 0; y < cm; ++y) col_mask |= (uint16_t)(1u << (y * cn + cx));
+  const bool clustered = cn * cm > 1;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), (uint32_t)(cn + cm - 1));
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), NEPI);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 32 * 0) {
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  cluster_sync();
+
+  const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
+  const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
+  const int S = p.S, nkb = p.nkb;
+  const int64_t nout = (p.Kpad + p.Bo - 1) / p.Bo;
+  // rows per TMA box: the CTA's contiguous share of a tile when the cluster
+  // width divides the tile's 8-row pieces, else single 8-row pieces
+  const bool a_contig = (TM / 8) % cn == 0, b_contig = (TN / 8) % cm == 0;
+  const int a_box = a_contig ? TM / cn : 8, b_box = b_contig ? TN / cm : 8;
+
+  if (warp == 0) {
+    // ---------------- copies ----------------
+    if (lane == 0) {
+      unsigned long long a_ld = 0, a_dl = 0, b_ld = 0, b_dl = 0, pf = 0, nops = 0;
+      uint32_t stage = 0, phase = 0;
+      bool ok = true;
+      for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
+        const int64_t m0 = row_lo + (int64_t)mi * TM;
+        for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
+          const int64_t n0 = col_lo + (int64_t)ni * TN;
+          for (int d = 2; d <= S + 1 && ok; ++d) {
+            for (int s = 1; s < d && ok; ++s) {
+              const int t = d - s;
+              for (int kb = 0; kb < nkb; ++kb) {
+                const int64_t k0 = (int64_t)kb * BKS;
+                if (k0 % p.Bo == 0) {
+                  // outer step: owners stage outer panel o (at the start) and o + 1
+                  const int64_t o = k0 / p.Bo;
+                  for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
+                    const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
+                    if (c == (int)imin64(p.Q - 1, kq / p.Kq)) {
+                      for (int64_t kk = kq; kk < kend; kk += BKS)
+                        tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, s - 1);
+                      pf += 1;
+                    }
+                    if (r == (int)imin64(p.P - 1, kq / p.Kp)) {
+                      for (int64_t kk = kq; kk < kend; kk += BKS)
+                        tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, t - 1);
+                      pf += 1;
+                    }
+                  }
+                }
+                if (!wait_or_abort(smem_u32(&empty[stage]), phase ^ 1u, &abort_flag, true)) {
+                  if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteEmpty);
+                  abort_flag = 1;
+                  ok = false;
+                  break;
+                }
+                const uint32_t fb = smem_u32(&full[stage]);
+                mbar_arrive_expect_tx(fb, STAGE_BYTES);
+                const uint32_t a_base = smem_u32(smem + stage * STAGE_BYTES);
+                const uint32_t b_base = a_base + A_BYTES;
+                const int64_t kc = span(0, p.K, k0, k0 + BKS);
+                // A tile (128 rows): contiguous share of the cluster row, or 8-row
+                // pieces dealt round-robin when the width does not divide 16
+                for (int i = a_contig ? cx * (a_box / 8) : cx; i < TM / 8;
+                     i += a_contig ? TM / 8 : cn) {
+                  const int64_t ar = m0 + (int64_t)i * 8;
+                  const uint32_t dst = a_base + i * 8 * 128;
+                  if (cn > 1)
+                    tma_load_3d_mc(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb, row_mask);
+                  else
+                    tma_load_3d(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb);
+                  const int64_t ca = span(row_lo, row_hi, ar, ar + a_box) * kc;
+                  a_ld += ca;
+                  a_dl += ca * cn;
+                  nops += 1;
+                }
+                for (int i = b_contig ? cy * (b_box / 8) : cy; i < TN / 8;
+                     i += b_contig ? TN / 8 : cm) {
+                  const int64_t br = n0 + (int64_t)i * 8;
+                  const uint32_t dst = b_base + i * 8 * 128;
+                  if (cm > 1)
+                    tma_load_3d_mc(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb, col_mask);
+                  else
+                    tma_load_3d(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb);
+                  const int64_t cb = span(col_lo, col_hi, br, br + b_box) * kc;
+                  b_ld += cb;
+                  b_dl += cb * cm;
+                  nops += 1;
+                }
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+              }
+            }
+          }
+        }
+      }
+      // tail: every release of the last stages has landed before leaving
+      for (int i = 0; i < STAGES && ok; ++i) {
+        if (!wait_or_abort(smem_u32(&empty[stage]), phase ^ 1u, &abort_flag, true)) {
+          if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteEmpty);
+          abort_flag = 1;
+          ok = false;
+        }
+        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+      }
+      atomicAdd(&p.counters[0], a_ld);
+      atomicAdd(&p.counters[1], a_dl);
+      atomicAdd(&p.counters[2], b_ld);
+      atomicAdd(&p.counters[3], b_dl);
+      atomicAdd(&p.counters[4], pf);
+      atomicAdd(&p.counters[5], nops);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issue ----------------
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      uint32_t gc = 0;  // global chunk counter: buffer gc & 1, phase (gc >> 1) & 1
+      const uint16_t rel_mask = row_mask | col_mask;
+      bool ok = true;
+      for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
+        for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
+          for (int d = 2; d <= S + 1 && ok; ++d) {
+            const int nst = (d - 1) * nkb;
+            for (int st = 0; st < nst; ++st) {
+              const uint32_t buf = gc & 1u;
+              if (st % CH == 0) {
+                if (!wait_or_abort(smem_u32(&acc_empty[buf]), ((gc >> 1) & 1u) ^ 1u, &abort_flag,
+                                   false)) {
+                  if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteAccEmpty);
+                  abort_flag = 1;
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+              }
+              if (!wait_or_abort(smem_u32(&full[stage]), phase, &abort_flag, false)) {
+                if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteFull);
+                abort_flag = 1;
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a_addr = smem_u32(smem + stage * STAGE_BYTES);
+              const uint32_t b_addr = a_addr + A_BYTES;
+              const uint32_t dt = tmem_base + buf * TN;
+#pragma unroll
+              for (int k = 0; k < BKS / 16; ++k) {
+                mma_bf16(dt, sdesc_k128(a_addr + k * 32), sdesc_k128(b_addr + k * 32), IDESC,
+                         (st % CH != 0 || k > 0) ? 1u : 0u);
+              }
+              // release the stage to every CTA that delivers into it
+              if (clustered)
+                mma_commit_mc(smem_u32(&empty[stage]), rel_mask);
+              else
+                mma_commit(smem_u32(&empty[stage]));
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+              if (st % CH == CH - 1 || st == nst - 1) {
+                mma_commit(smem_u32(&acc_full[buf]));
+                ++gc;
+              }
+            }
+          }
+        }
+      }
+    }
+  } else {
+    // ---------------- drain: tensor memory -> exact int32 planes ----------------
+    const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+    const int h = (warp - 2) >> 2;          // column half
+    uint32_t gc = 0;
+    bool ok = true;
+    for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
+      const int64_t row = row_lo + (int64_t)mi * TM + q * 32 + lane;
+      for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
+        const int64_t n0 = col_lo + (int64_t)ni * TN + h * 128;
+        const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
+        for (int d = 2; d <= S + 1 && ok; ++d) {
+          const int nch = ((d - 1) * nkb + CH - 1) / CH;
+          for (int seg = 0; seg * p.seg_chunks < nch && ok; ++seg) {
+            const int c1 = min(nch, (seg + 1) * p.seg_chunks);
+            int acc[128];
+#pragma unroll
+            for (int i = 0; i < 128; ++i) acc[i] = 0;
+            for (int ch = seg * p.seg_chunks; ch < c1; ++ch) {
+              const uint32_t buf = gc & 1u;
+              // the whole warp decides together: tcgen05.ld below is warp-collective
+              const bool got =
+                  wait_or_abort(smem_u32(&acc_full[buf]), (gc >> 1) & 1u, &abort_flag, false);
+              if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + buf * TN + h * 128;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                uint32_t v[16];
+                tmem_ld16(ta + j * 16, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                  acc[j * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
+              }
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+              ++gc;
+            }
+            if (!ok) break;
+            if (row < row_hi) {
+              int32_t *drow =
+                  p.D + ((int64_t)((d - 2) * p.nseg + seg) * p.M + row) * p.N + n0;
+              if (nvalid == 128 && (reinterpret_cast<uintptr_t>(drow) & 15) == 0) {
+#pragma unroll
+                for (int i = 0; i < 128; i += 4)
+                  *reinterpret_cast<int4 *>(drow + i) =
+                      make_int4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+              } else {
+#pragma unroll
+                for (int i = 0; i < 128; ++i)
+                  if (i < nvalid) drow[i] = acc[i];
+              }
+            }
+          }
+        }
+      }
+    }
+    if (!ok) {
+      if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteAccFull);
+      abort_flag = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (abort_flag) bounded_sleep(2000000ull);   // in-flight copies and MMAs land
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+  cluster_sync();
+}
+
+}  // namespace
+
+int bf16_cluster_limit(int *limit) {
+  cudaError_t e = cudaFuncSetAttribute(bf16_diag_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
+  e = cudaFuncSetAttribute(bf16_diag_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16, 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 16;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  e = cudaOccupancyMaxPotentialClusterSize(&n, bf16_diag_kernel, &cfg);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxPotentialClusterSize");
+  *limit = n;
+  return HSUMMA_OK;
+}
+
+int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, int32_t *D,
+                      cudaStream_t s) {
+  const int64_t Kpad = ceil_div(g.K, 64) * 64;
+  const int a_box = (TM / 8) % g.cn == 0 ? TM / g.cn : 8;
+  const int b_box = (TN / 8) % g.cm == 0 ? TN / g.cm : 8;
+  const auto BF16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUtensorMap tA, tB, tApf, tBpf;
+  if (!encode_tmap_3d(&tA, BF16, 2, As, Kpad, g.M, S, BKS, a_box, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_tmap_3d(&tB, BF16, 2, Bs, Kpad, g.N, S, BKS, b_box, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_tmap_3d(&tApf, BF16, 2, As, Kpad, g.M, S, BKS, TM, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+      !encode_tmap_3d(&tBpf, BF16, 2, Bs, Kpad, g.N, S, BKS, TN, CU_TENSOR_MAP_SWIZZLE_NONE))
+    return HSUMMA_ERR_ARG;
+  SplitParams p;
+  p.D = D;
+  p.M = g.M;
+  p.N = g.N;
+  p.K = g.K;
+  p.Kpad = Kpad;
+  p.Mt = g.Mt;
+  p.Nt = g.Nt;
+  p.Kq = g.Kq;
+  p.Kp = g.Kp;
+  p.P = g.P;
+  p.Q = g.Q;
+  p.cm = g.cm;
+  p.cn = g.cn;
+  p.nsub_m = (int)ceil_div(g.Mt, TM);
+  p.nsub_n = (int)ceil_div(g.Nt, TN);
+  p.Bo = g.Bo;
+  p.S = S;
+  p.nkb = (int)(Kpad / BKS);
+  p.seg_chunks = kSegChunks;
+  p.nseg = split_planes(g.K, S);
+  p.counters = state().d_counters;
+  p.status = state().d_status;
+  cudaError_t e = cudaFuncSetAttribute(bf16_diag_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
+  if (g.cm * g.cn > 8) {
+    e = cudaFuncSetAttribute(bf16_diag_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.Q, (unsigned)g.P, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)g.cn;
+  at[0].val.clusterDim.y = (unsigned)g.cm;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, bf16_diag_kernel, tA, tB, tApf, tBpf, p);
+  if (e != cudaSuccess) return cuda_fail(e, "launch bf16_diag_kernel");
+  return HSUMMA_OK;
+}
+
+}  // namespace hs

@@ -1,0 +1,341 @@
+// Split-precision path, the steps around the tensor-core products:
+//   1. exponent scan   e_i = ilogb(max_k |A_ik|) + 2, f_j over the columns of B
+//   2. slicing         S digits per entry, t_s = RN(r 2^(w s)) - 2^w RN(r 2^(w(s-1))),
+//                      r = a 2^-e (round half to even), as int8 (w = 7) or bf16 (w = 8)
+//   4. recombination   C_ij = RN(2^(e_i+f_j) sum_d D_d,ij 2^(-w d)), exact sum in
+//                      128-bit integers, rounded once to binary64
+// All three work on the bit patterns with integer instructions: binary64
+// arithmetic is the slowest unit of this GPU and is not needed for any of them.
+// The digit formula is the closed form of the Ozaki splitting r <- r 2^w - rint(r 2^w)
+// (the remainder recursion telescopes because shifting by the even integer
+// 2^w t does not change a round-half-to-even decision).
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "../../include/hsumma.h"
+
+namespace hs {
+namespace {
+
+// max over |x| by bit pattern (non-negative doubles order like their bits)
+__device__ __forceinline__ unsigned long long absbits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// exponent e (ilogb + 2) from the largest |x| bit pattern; flags Inf/NaN
+__device__ __forceinline__ int exponent_from_bits(unsigned long long b, bool *nonfinite) {
+  const int E = (int)(b >> 52);
+  if (E == 0x7FF) {
+    *nonfinite = true;
+    return 0;
+  }
+  if (b == 0) return 0;
+  int ilogb;
+  if (E > 0)
+    ilogb = E - 1023;
+  else
+    ilogb = (63 - __clzll((long long)(b & 0xFFFFFFFFFFFFFull))) - 1074;
+  return ilogb + 2;
+}
+
+// rows of A: one warp per row
+__global__ void exponents_rows_kernel(const double *__restrict__ A, int64_t lda, int64_t M,
+                                      int64_t K, int32_t *__restrict__ e, int *status) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const double *a = A + row * lda;
+  unsigned long long m = 0;
+  // lda is even and A 16-byte aligned: every row starts 16-byte aligned
+  const int64_t K2 = K & ~int64_t(1);
+  for (int64_t k = 2 * lane; k < K2; k += 64) {
+    const double2 v = *reinterpret_cast<const double2 *>(a + k);
+    m = max(m, max(absbits(v.x), absbits(v.y)));
+  }
+  if ((K & 1) && lane == 0) m = max(m, absbits(a[K - 1]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    bool nf = false;
+    e[row] = exponent_from_bits(m, &nf);
+    if (nf) record_error(status, HSUMMA_ERR_NONFINITE, kSiteNonFinite);
+  }
+}
+
+// columns of B: a block covers 64 columns (32 lanes x 2), its 8 warps split k
+__global__ void exponents_cols_kernel(const double *__restrict__ B, int64_t ldb, int64_t K,
+                                      int64_t N, int32_t *__restrict__ f, int *status) {
+  __shared__ unsigned long long part[8][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j0 = (int64_t)blockIdx.x * 64 + 2 * lane;
+  unsigned long long m0 = 0, m1 = 0;
+  if (j0 + 1 < N) {
+    for (int64_t k = warp; k < K; k += 8) {
+      const double2 v = *reinterpret_cast<const double2 *>(B + k * ldb + j0);
+      m0 = max(m0, absbits(v.x));
+      m1 = max(m1, absbits(v.y));
+    }
+  } else if (j0 < N) {
+    for (int64_t k = warp; k < K; k += 8) m0 = max(m0, absbits(B[k * ldb + j0]));
+  }
+  part[warp][2 * lane] = m0;
+  part[warp][2 * lane + 1] = m1;
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    unsigned long long m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m = max(m, part[w][threadIdx.x]);
+    const int64_t j = (int64_t)blockIdx.x * 64 + threadIdx.x;
+    if (j < N) {
+      bool nf = false;
+      f[j] = exponent_from_bits(m, &nf);
+      if (nf) record_error(status, HSUMMA_ERR_NONFINITE, kSiteNonFinite);
+    }
+  }
+}
+
+// RN(|x| 2^-e 2^(w s)) for s = 1..S as signed integers, then the digits.
+template <int W, int S_MAX>
+__device__ __forceinline__ void digits_of(double x, int e, int S, int (&t)[S_MAX]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const bool neg = (bits >> 63) != 0;
+  const int E = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  int lsb;  // binary exponent of m's least significant bit
+  if (E > 0) {
+    m |= 1ull << 52;
+    lsb = E - 1075;
+  } else {
+    lsb = -1074;
+  }
+  long long prev = 0;
+#pragma unroll
+  for (int s = 1; s <= S_MAX; ++s) {
+    if (s > S) {
+      t[s - 1] = 0;
+      continue;
+    }
+    // |x| 2^-e 2^(w s) = m 2^sh
+    const int sh = lsb - e + W * s;
+    unsigned long long y;
+    if (m == 0) {
+      y = 0;
+    } else if (sh >= 0) {
+      // m 2^sh < 2^(w s - 1) <= 2^55 when e comes from the exponent scan (the
+      // guard only keeps the shift defined for other e)
+      y = m << (sh < 63 ? sh : 63);
+    } else if (-sh > 54) {
+      y = 0;        // m 2^sh < 2^53 2^-55 < 1/2
+    } else {
+      const int d = -sh;
+      const unsigned long long q = m >> d, rem = m & ((1ull << d) - 1ull),
+                               half = 1ull << (d - 1);
+      y = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    }
+    const long long Y = neg ? -(long long)y : (long long)y;
+    t[s - 1] = (int)(Y - prev * (1ll << W));
+    prev = Y;
+  }
+}
+
+constexpr int SMAX = 8;
+
+// A slices: As[s][i][k], k < Kp (zero beyond K); each thread 4 consecutive k
+template <int KIND>
+__global__ void slices_rows_kernel(const double *__restrict__ A, int64_t lda, int64_t M,
+                                   int64_t K, int64_t Kp, const int32_t *__restrict__ e,
+                                   int S, void *__restrict__ out) {
+  constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
+  const int64_t groups = Kp / 4;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= M * groups) return;
+  const int64_t i = gid / groups, k0 = (gid % groups) * 4;
+  const int ei = e[i];
+  int t[4][SMAX];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t k = k0 + u;
+    const double x = k < K ? A[i * lda + k] : 0.0;
+    digits_of<W, SMAX>(x, ei, S, t[u]);
+  }
+  for (int s = 0; s < S; ++s) {
+    const int64_t off = ((int64_t)s * M + i) * Kp + k0;
+    if (KIND == HSUMMA_INT8_SLICES) {
+      char4 v = make_char4((signed char)t[0][s], (signed char)t[1][s], (signed char)t[2][s],
+                           (signed char)t[3][s]);
+      *reinterpret_cast<char4 *>(reinterpret_cast<int8_t *>(out) + off) = v;
+    } else {
+      __nv_bfloat162 lo = __floats2bfloat162_rn((float)t[0][s], (float)t[1][s]);
+      __nv_bfloat162 hi = __floats2bfloat162_rn((float)t[2][s], (float)t[3][s]);
+      uint2 v;
+      v.x = *reinterpret_cast<uint32_t *>(&lo);
+      v.y = *reinterpret_cast<uint32_t *>(&hi);
+      *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(out) + off) = v;
+    }
+  }
+}
+
+// B slices, transposed: Bs[t][j][k]; a block transposes a 64 (k) x 64 (j) tile
+template <int KIND>
+__global__ void slices_cols_kernel(const double *__restrict__ B, int64_t ldb, int64_t K,
+                                   int64_t N, int64_t Kp, const int32_t *__restrict__ f,
+                                   int S, void *__restrict__ out) {
+  constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
+  __shared__ double tile[64][65];
+  const int64_t k0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 64;
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 256 threads: 64 x 4
+  for (int r = ty; r < 64; r += 4) {
+    const int64_t k = k0 + r, j = j0 + tx;
+    tile[r][tx] = (k < K && j < N) ? B[k * ldb + j] : 0.0;
+  }
+  __syncthreads();
+  // thread -> (j = j0 + jj, k = k0 + 4 kk .. +3)
+  for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
+    const int jj = idx >> 4, kk = (idx & 15) * 4;
+    const int64_t j = j0 + jj;
+    if (j >= N) continue;
+    const int fj = f[j];
+    int t[4][SMAX];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) digits_of<W, SMAX>(tile[kk + u][jj], fj, S, t[u]);
+    for (int s = 0; s < S; ++s) {
+      const int64_t off = ((int64_t)s * N + j) * Kp + k0 + kk;
+      if (KIND == HSUMMA_INT8_SLICES) {
+        char4 v = make_char4((signed char)t[0][s], (signed char)t[1][s],
+                             (signed char)t[2][s], (signed char)t[3][s]);
+        *reinterpret_cast<char4 *>(reinterpret_cast<int8_t *>(out) + off) = v;
+      } else {
+        __nv_bfloat162 lo = __floats2bfloat162_rn((float)t[0][s], (float)t[1][s]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn((float)t[2][s], (float)t[3][s]);
+        uint2 v;
+        v.x = *reinterpret_cast<uint32_t *>(&lo);
+        v.y = *reinterpret_cast<uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(out) + off) = v;
+      }
+    }
+  }
+}
+
+// RN(X 2^k) for a 128-bit integer X, ties to even, subnormals and overflow
+// handled: the value is rounded once, at the precision its exponent allows.
+__device__ __forceinline__ double round_scaled_i128(__int128 X, int k) {
+  if (X == 0) return 0.0;
+  const bool neg = X < 0;
+  unsigned __int128 m = neg ? (unsigned __int128)(-X) : (unsigned __int128)X;
+  const unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
+  const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  const int e = nb - 1 + k;               // exponent of the leading bit
+  int ulp = e - 52;                       // exponent of the last kept bit
+  if (ulp < -1074) ulp = -1074;
+  const int drop = ulp - k;               // low bits of m below the last kept bit
+  unsigned long long q;
+  if (drop <= 0) {
+    q = (unsigned long long)(m << (-drop));   // < 2^53
+  } else if (drop > nb) {
+    q = 0;                                  // below half of the smallest step
+  } else {
+    const unsigned __int128 qq = m >> drop;
+    const unsigned __int128 rem = m - (qq << drop);
+    const unsigned __int128 half = (unsigned __int128)1 << (drop - 1);
+    q = (unsigned long long)qq;
+    if (rem > half || (rem == half && (q & 1ull))) q += 1;
+  }
+  if (q == (1ull << 53)) {                 // rounding carried into a new binade
+    q >>= 1;
+    ulp += 1;
+  }
+  unsigned long long bits;
+  if (q < (1ull << 52)) {
+    bits = q;                               // subnormal (ulp == -1074) or zero
+  } else {
+    const long long biased = (long long)ulp + 1075;
+    if (biased >= 2047)
+      bits = 0x7FF0000000000000ull;         // overflow rounds to infinity
+    else
+      bits = ((unsigned long long)biased << 52) | (q & 0xFFFFFFFFFFFFFull);
+  }
+  if (neg) bits |= 0x8000000000000000ull;
+  return __longlong_as_double((long long)bits);
+}
+
+template <int W>
+__global__ void recombine_kernel(const int32_t *__restrict__ D, int S, int nseg, int64_t M,
+                                 int64_t N, const int32_t *__restrict__ e,
+                                 const int32_t *__restrict__ f, double *__restrict__ C,
+                                 int64_t ldc) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= N) return;
+  const int64_t plane = M * N;
+  __int128 X = 0;
+  for (int d = 2; d <= S + 1; ++d) {
+    long long Dd = 0;   // the segment planes of a diagonal sum exactly in 64 bits
+    for (int g = 0; g < nseg; ++g) Dd += D[(int64_t)((d - 2) * nseg + g) * plane + i * N + j];
+    X += (__int128)Dd << (W * (S + 1 - d));
+  }
+  C[i * ldc + j] = round_scaled_i128(X, e[i] + f[j] - W * (S + 1));
+}
+
+}  // namespace
+
+int launch_split_exponents(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                           const double *B, int64_t ldb, int32_t *e, int32_t *f,
+                           cudaStream_t s) {
+  int *status = state().d_status;
+  if (M > 0) {
+    const int64_t blocks = ceil_div(M, 8);
+    exponents_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, lda, M, K, e, status);
+  }
+  if (N > 0) {
+    exponents_cols_kernel<<<(unsigned)ceil_div(N, 64), 256, 0, s>>>(B, ldb, K, N, f, status);
+  }
+  cudaError_t err = cudaGetLastError();
+  return err == cudaSuccess ? HSUMMA_OK : cuda_fail(err, "launch exponent scan");
+}
+
+int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                        const double *B, int64_t ldb, const int32_t *e, const int32_t *f,
+                        int kind, int S, void *As, void *Bs, cudaStream_t s) {
+  const int64_t Kp = ceil_div(K, 64) * 64;
+  if (Kp == 0) return HSUMMA_OK;
+  const int64_t nA = M * (Kp / 4);
+  if (nA > 0) {
+    const unsigned blocks = (unsigned)ceil_div(nA, 256);
+    if (kind == HSUMMA_INT8_SLICES)
+      slices_rows_kernel<HSUMMA_INT8_SLICES><<<blocks, 256, 0, s>>>(A, lda, M, K, Kp, e, S, As);
+    else
+      slices_rows_kernel<HSUMMA_BF16_SLICES><<<blocks, 256, 0, s>>>(A, lda, M, K, Kp, e, S, As);
+  }
+  if (N > 0) {
+    dim3 grid((unsigned)(Kp / 64), (unsigned)ceil_div(N, 64));
+    if (kind == HSUMMA_INT8_SLICES)
+      slices_cols_kernel<HSUMMA_INT8_SLICES><<<grid, 256, 0, s>>>(B, ldb, K, N, Kp, f, S, Bs);
+    else
+      slices_cols_kernel<HSUMMA_BF16_SLICES><<<grid, 256, 0, s>>>(B, ldb, K, N, Kp, f, S, Bs);
+  }
+  cudaError_t err = cudaGetLastError();
+  return err == cudaSuccess ? HSUMMA_OK : cuda_fail(err, "launch slicing");
+}
+
+int launch_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, const int32_t *D,
+                           const int32_t *e, const int32_t *f, double *C, int64_t ldc,
+                           cudaStream_t s) {
+  const int nseg = split_planes(K, S, kind);
+  // one grid row per matrix row, in bands of at most 65535 rows; a band starts
+  // r0 rows in: D, e and C advance by r0 rows, the plane stride stays M N
+  for (int64_t r0 = 0; r0 < M; r0 += 65535) {
+    const int64_t rows = (M - r0) < 65535 ? (M - r0) : 65535;
+    dim3 grid((unsigned)ceil_div(N, 256), (unsigned)rows);
+    if (kind == HSUMMA_INT8_SLICES)
+      recombine_kernel<7><<<grid, 256, 0, s>>>(D + r0 * N, S, nseg, M, N, e + r0, f,
+                                               C + r0 * ldc, ldc);
+    else
+      recombine_kernel<8><<<grid, 256, 0, s>>>(D + r0 * N, S, nseg, M, N, e + r0, f,
+                                               C + r0 * ldc, ldc);
+  }
+  cudaError_t err = cudaGetLastError();
+  return err == cudaSuccess ? HSUMMA_OK : cuda_fail(err, "launch recombination");
+}
+
+}  // namespace hs

@@ -1,0 +1,76 @@
+"""The C-ABI library without a GPU: it builds for sm_103a, loads, exports every
+function include/hsumma.h declares, and its host-side logic (group resolution,
+workspace sizes, argument errors before initialisation) matches the oracle."""
+import ctypes
+
+import pytest
+
+import paper_1306_4161_gb300 as hs
+from paper_1306_4161_gb300 import _build
+from oracle import gpu_schedule as gs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return hs.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", hs.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    declared = set(hs.declared_functions())
+    assert declared, "no declarations parsed"
+    assert declared <= exported, sorted(declared - exported)
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_group_shape_matches_oracle(lib):
+    for P, Q in [(4, 4), (16, 16), (12, 16), (5, 7), (128, 64), (2, 8), (1, 1)]:
+        for G in range(1, min(P * Q, 300) + 1):
+            want = gs.group_shape(P, Q, G)
+            if want is None:
+                with pytest.raises(hs.HsummaError) as ei:
+                    hs.group_shape(P, Q, G)
+                assert ei.value.status == -1
+                continue
+            I, J, cm, cn = hs.group_shape(P, Q, G)
+            assert (I, J) == want, (P, Q, G)
+            assert (cm, cn) == gs.cluster_shape(P, Q, I, J, limit=16), (P, Q, G)
+
+
+def test_workspace_sizes(lib):
+    assert hs.workspace_size(100, 100, 100, "fp64") == 0
+    ws = hs.workspace_size(300, 520, 700, "bf16", 5)
+    Kp = 704
+    planes = hs.split_planes(700, "bf16", 5)
+    assert planes == 1
+    al = lambda x: (x + 255) // 256 * 256
+    assert ws == al(300 * 4) + al(520 * 4) + al(5 * 300 * Kp * 2) + al(5 * 520 * Kp * 2) + \
+        al(5 * planes * 300 * 520 * 4)
+    # a diagonal of 5 pairs over K = 32768 needs two planes (127 chunks of 1024 each)
+    assert hs.split_planes(32768, "bf16", 5) == 2
+    assert hs.split_planes(16384, "bf16", 7) == 1
+    assert hs.split_planes(16384, "int8", 8) == 1
+
+
+def test_errors_before_init(lib):
+    st = lib.hsumma_gemm(4, 4, 4, None, 4, None, 4, None, 4, 1, 1, 1, 16, 16, 0, None)
+    assert st == -5
+    assert "hsumma_init" in hs.last_error()
+    assert lib.hsumma_sync(None) == -5
+    with pytest.raises(hs.HsummaError):
+        hs.group_shape(0, 4, 1)
+    with pytest.raises(hs.HsummaError):
+        hs.workspace_size(4, 4, 4, "bf16", 0)       # S out of range
+    with pytest.raises(hs.HsummaError):
+        hs.workspace_size(4, 4, 4, "int8", 9)
+    assert lib.hsumma_split_planes(10, 0, 3) == -1   # not a split kind
+
+
+def test_mode_encoding():
+    assert hs.mode_code("bf16", 5) == 2 | (5 << 8)
+    assert hs.mode_code("fp64") == 0

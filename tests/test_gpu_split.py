@@ -1,0 +1,186 @@
+"""Parity of the split-precision path with the oracle (GPU), step by step and
+end to end: exponents, digits and recombination bit for bit, diagonal sums
+exactly, C bit for bit (the recombination rounds an exact sum once), accuracy
+within 2 K u against the compensated reference, and the counters."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import gpu_schedule as gsched
+from oracle import native, split
+from tests.gpu_util import lib_ready, pair, sample_entries, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def awkward(M, K, seed):
+    """Wide-range values with zero rows, subnormals and exact ties."""
+    A = workloads.matrix(M, K, seed, "wide")
+    A[min(2, M - 1), :] = 0.0
+    if M > 4 and K > 3:
+        A[4, 1] = 2.0 ** -1070
+        A[4, 2] = -(2.0 ** -1074)
+        A[3, :] = 2.0 ** -1060 * np.sign(A[3, :])     # a subnormal-scale row
+        A[1, 0] = 0.5 + 2.0 ** -9                       # ties in the digits
+    return A
+
+
+@pytest.mark.parametrize("kind", ["bf16", "int8"])
+def test_exponents_and_slices_bit_exact(kind):
+    hs = lib_ready()
+    torch = torch_cuda()
+    M, N, K = 70, 90, 130
+    A = awkward(M, K, 11)
+    B = awkward(N, K, 12).T.copy()
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    e, f = hs.split_exponents(dA, dB)
+    hs.sync()
+    e_o, f_o = split.row_exponents(A), split.col_exponents(B)
+    assert np.array_equal(e.cpu().numpy(), e_o)
+    assert np.array_equal(f.cpu().numpy(), f_o)
+    S = 8 if kind == "int8" else 7
+    As, Bs = hs.split_slices(dA, dB, e, f, kind, S)
+    hs.sync()
+    w = split.SLICE_BITS[kind]
+    Ad = split.split_rows(A, e_o, S, w)
+    Bd = split.split_cols(B, f_o, S, w)
+    Kp = As.shape[2]
+    got_a = As.float().cpu().numpy()
+    got_b = Bs.float().cpu().numpy()
+    assert np.array_equal(got_a[:, :, :K], Ad)
+    assert np.all(got_a[:, :, K:] == 0)
+    assert np.array_equal(got_b[:, :, :K], np.transpose(Bd, (0, 2, 1)))
+    assert np.all(got_b[:, :, K:] == 0)
+
+
+def test_nonfinite_is_reported():
+    hs = lib_ready()
+    torch = torch_cuda()
+    A = np.ones((8, 8))
+    A[3, 5] = np.inf
+    dA = torch.from_numpy(A).cuda()
+    with pytest.raises(hs.HsummaError) as ei:
+        hs.gemm(dA, dA, P=1, Q=1, G=1, b=64, Bouter=64, kind="bf16", slices=3)
+        hs.sync()
+    assert ei.value.status == -6
+    hs.sync()          # the error word was cleared
+
+
+@pytest.mark.parametrize("M,N,K,P,Q,G,S", [
+    (300, 600, 1000, 3, 3, 9, 3),       # flat, ragged everywhere
+    (300, 600, 1000, 3, 3, 1, 2),       # one 3 x 3 cluster: 8-row pieces
+    (256, 512, 512, 2, 2, 1, 4),        # one 2 x 2 cluster: contiguous shares
+    (512, 1024, 4096, 4, 4, 4, 3),      # 2 x 2 groups, several chunks per diagonal
+    (130, 260, 64, 1, 1, 1, 5),         # one CTA, 2 x 2 sub-tiles, ragged
+])
+def test_bf16_diagonals_exact(M, N, K, P, Q, G, S):
+    hs = lib_ready()
+    torch = torch_cuda()
+    A, B, dA, dB = pair(M, N, K, 21, "uniform", "wide")
+    e, f = hs.split_exponents(dA, dB)
+    As, Bs = hs.split_slices(dA, dB, e, f, "bf16", S)
+    D = hs.split_diagonals(As, Bs, M, N, K, "bf16", S, P=P, Q=Q, G=G, b=64, Bouter=128)
+    hs.sync()
+    _, parts = split.split_gemm(A, B, S, "bf16", return_parts=True)
+    Dg = D.to(torch.int64).sum(dim=1).cpu().numpy()
+    for d in range(2, S + 2):
+        assert np.array_equal(Dg[d - 2], parts["D"][d]), d
+    npairs = S * (S + 1) // 2
+    I, J, cm, cn = hs.group_shape(P, Q, G)
+    want = gsched.counters_closed_form(M, N, K, P, Q, cm, cn, 128, 256, 128, npairs)
+    c = hs.counters()
+    for k, v in want.items():
+        assert c[k] == v, (k, c[k], v)
+
+
+def test_bf16_exact_at_the_fp32_bound():
+    # every digit at its largest magnitude: products 2^14, chunk sums reach
+    # exactly 2^24 -- the fp32 accumulator must still be exact
+    hs = lib_ready()
+    torch = torch_cuda()
+    M, N, K = 256, 256, 2048
+    A = np.full((M, K), 0.5 - 2.0 ** -20)          # r 2^8 rounds to 128
+    A[1::2] *= -1.0
+    B = np.full((K, N), 0.5 - 2.0 ** -20)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    e, f = hs.split_exponents(dA, dB)
+    As, Bs = hs.split_slices(dA, dB, e, f, "bf16", 2)
+    assert As.float().abs().max().item() == 128.0
+    D = hs.split_diagonals(As, Bs, M, N, K, "bf16", 2, P=1, Q=1, G=1, b=64, Bouter=64)
+    hs.sync()
+    _, parts = split.split_gemm(A, B, 2, "bf16", return_parts=True)
+    Dg = D.to(torch.int64).sum(dim=1).cpu().numpy()
+    assert np.array_equal(Dg[0], parts["D"][2])
+    assert np.array_equal(Dg[1], parts["D"][3])
+
+
+@pytest.mark.parametrize("kind,S,dist", [("bf16", 3, "uniform"), ("bf16", 5, "wide"),
+                                         ("bf16", 6, "uniform")])
+def test_gemm_bit_exact_with_oracle(kind, S, dist):
+    hs = lib_ready()
+    M, N, K = 200, 300, 700
+    A, B, dA, dB = pair(M, N, K, 31, dist)
+    C = hs.gemm(dA, dB, P=2, Q=2, G=1, b=64, Bouter=128, kind=kind, slices=S)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, S, kind))
+
+
+def test_recombine_special_values():
+    # exact integer digits chosen to make the rounding interesting: ties,
+    # subnormal and overflowing results
+    hs = lib_ready()
+    torch = torch_cuda()
+    M, N, S = 4, 3, 3
+    D = np.zeros((S, 1, M, N), dtype=np.int32)
+    D[0, 0] = [[1, 3, -5], [2 ** 30, -(2 ** 30), 7], [0, 1, 1], [123456789, -987654321, 5]]
+    D[1, 0] = [[1, 0, 1], [255, 256, -1], [0, 0, 1], [77, 1, -2 ** 31 + 1]]
+    D[2, 0] = [[-1, 2 ** 20, 0], [1, -1, 2 ** 31 - 1], [1, 0, -1], [0, 0, 0]]
+    e = np.array([0, 2000, -1060, 5], dtype=np.int32)
+    f = np.array([0, -3, 1000], dtype=np.int32)
+    dD = torch.from_numpy(D).cuda()
+    de, df = torch.from_numpy(e).cuda(), torch.from_numpy(f).cuda()
+    C = hs.split_recombine(dD, de, df, M, N, 64, "bf16", S)
+    hs.sync()
+    Dd = {d: D[d - 2, 0].astype(np.int64) for d in range(2, S + 2)}
+    want = split.recombine(Dd, e, f, S, 8)
+    got = C.cpu().numpy()
+    assert np.array_equal(np.isinf(got), np.isinf(want))
+    fin = np.isfinite(want)
+    assert np.array_equal(got[fin], want[fin])
+
+
+def test_accuracy_within_bound_bf16_S5():
+    hs = lib_ready()
+    M, N, K = 256, 256, 4096
+    A, B, dA, dB = pair(M, N, K, 1002, "uniform")
+    C = hs.gemm(dA, dB, P=2, Q=1, G=1, b=64, Bouter=256, kind="bf16", slices=5)
+    hs.sync()
+    ref, absab = native.dot2_full(A, B)
+    assert split.max_rel_error(C.cpu().numpy(), ref, absab) <= split.tolerance(K)
+
+
+def test_full_size_16384_sampled():
+    # the bench workload: M = N = K = 16384, bf16 S = 5, 128 x 64 grid of
+    # 128 x 256 blocks in 2 x 2 groups; sampled entries bit for bit against the
+    # oracle, and within 2 K u of the compensated reference
+    hs = lib_ready()
+    torch = torch_cuda()
+    n, S = 16384, 5
+    dA = workloads.matrix_torch(n, n, 1002, "uniform", device="cuda")
+    dB = workloads.matrix_torch(n, n, 2002, "uniform", device="cuda")
+    C = hs.gemm(dA, dB, P=128, Q=64, G=2048, b=64, Bouter=256, kind="bf16", slices=S)
+    hs.sync()
+    rows, cols = sample_entries(n, n, 40, 99)
+    ur = np.unique(rows)
+    uc = np.unique(cols)
+    A = dA[torch.as_tensor(ur, device="cuda")].cpu().numpy()
+    B = dB[:, torch.as_tensor(uc, device="cuda")].cpu().numpy()
+    ri = np.searchsorted(ur, rows)
+    ci = np.searchsorted(uc, cols)
+    # the exponents use whole rows of A and whole columns of B: the sampled
+    # rows/columns carry them entirely
+    want = split.split_entries(A, B, ri, ci, S, "bf16")
+    got = C[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")].cpu().numpy()
+    assert np.array_equal(got, want)
+    ref, absab = native.dot2_entries(A, B, ri, ci)
+    assert split.max_rel_error(got, ref, absab) <= split.tolerance(n)
