@@ -1,0 +1,368 @@
+"""Benchmark: FP64-accurate TFLOP/s of C = A x B at M = N = K = 16384 on one
+GB300, split-precision (bf16 slices, tcgen05) against native binary64 (DMMA),
+each as a fraction of its roofline.
+
+One step = one hsumma_gemm call on the split path: exponent scan, slicing,
+the HSUMMA diagonal products on the tensor cores, exact recombination, on
+seeded uniform[-1, 1] inputs already resident in HBM (each 2 GiB, larger than
+L2, so no flush is needed between steps).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the plain binary64 triple loop) on a
+bounded sample of the same product (a band of rows of C) on the host cores.
+With N > 1 (torchrun) every rank runs the same problem on its own GPU
+(replicas: the single-GPU path does not shard) and value is the sum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIZE = 16384
+METRIC = "FP64-accurate TFLOP/s at n=16384, split-precision vs native FP64, % of roofline"
+SPLIT = dict(P=128, Q=64, G=2048, b=64, Bouter=256, kind="bf16", slices=5)
+NATIVE = dict(P=128, Q=128, G=4096, b=32, Bouter=128)
+WORKLOAD = ("split_vs_fp64_16384: M=N=K=16384, A,B uniform[-1,1] (SplitMix64 seeds 1002/2002), "
+            "bf16 slices S=5 (15 pair products), virtual grid 128x64 of 128x256 blocks, "
+            "G=2048 groups of 2x2 (cluster multicast), b=64, B=256; native fp64 beside it on a "
+            "128x128 grid, G=4096, b=32, B=128")
+
+
+def configure(n):
+    """Grids for an n x n x n product: 128 x 256 blocks (split) and 128 x 128
+    blocks (binary64), groups of 2 x 2 processors."""
+    global N_SIZE, SPLIT, NATIVE, WORKLOAD
+    if n % 256:
+        raise SystemExit("--size must be a multiple of 256")
+    N_SIZE = n
+    SPLIT = dict(SPLIT, P=n // 128, Q=n // 256, G=(n // 128) * (n // 256) // 4)
+    NATIVE = dict(NATIVE, P=n // 128, Q=n // 128, G=(n // 128) ** 2 // 4)
+    if n != 16384:
+        WORKLOAD = WORKLOAD.replace("16384", str(n))
+
+
+def flops(n=None):
+    n = N_SIZE if n is None else n
+    return 2.0 * n ** 3
+
+
+def read_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(A, B, target_s=15.0):
+    """The oracle triple loop on a band of rows of C, sized to about target_s
+    seconds on all host cores; returns (TFLOP/s, rows, cores, seconds)."""
+    from oracle import native
+    cores = native.default_threads()
+    n = A.shape[1]
+    rows = 8
+    while True:
+        t0 = time.perf_counter()
+        native.dgemm(A[:rows], B, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt > target_s / 4 or rows >= A.shape[0]:
+            break
+        rows = min(A.shape[0], max(rows * 2, int(rows * target_s / max(dt, 1e-3) / 2)))
+    return 2.0 * rows * n * B.shape[1] / dt / 1e12, rows, cores, dt
+
+
+def run_reference(args, rank, world):
+    import numpy as np
+    import workloads
+    out = {"impl": "reference"}
+    if rank != 0:
+        return None
+    n = N_SIZE
+    # bounded sample: a band of rows of A (whole) times B; B is the full matrix
+    B = workloads.matrix(n, n, 2002, "uniform")
+    A = workloads.matrix(256, n, 1002, "uniform")
+    rate, rows, cores, dt = cpu_oracle_rate(A, B, target_s=float(os.environ.get("HS_REF_S", 12)))
+    times = []
+    for _ in range(args.warmup):
+        from oracle import native
+        native.dgemm(A[:rows], B, nthreads=cores)
+    from oracle import native
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        native.dgemm(A[:rows], B, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    t = max(times) if times else dt
+    value = 2.0 * rows * n * n / t / 1e12
+    sample = f"{rows} rows of C = A x B at n=16384 (plain binary64 triple loop), per step"
+    out.update({
+        "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (2 GiB each)",
+                   "parallelism": "single GPU"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    })
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--native-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--size", type=int, default=N_SIZE,
+                    help="n of the n x n x n product (multiple of 256; default 16384)")
+    args = ap.parse_args()
+    configure(args.size)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    import paper_1306_4161_gb300 as hs
+    import workloads
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hs.init(local)
+    n = N_SIZE
+    dA = workloads.matrix_torch(n, n, 1002, "uniform", device="cuda")
+    dB = workloads.matrix_torch(n, n, 2002, "uniform", device="cuda")
+    dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        hs.gemm(dA, dB, out=dC, **SPLIT)
+
+    for _ in range(args.warmup):
+        step()
+    hs.sync()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    hs.sync()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * flops() / (ms * 1e-3) / 1e12
+
+    # per-kernel breakdown of the same path through the step entry points, with
+    # events on the launching stream; the diagonal products dominate
+    S = SPLIT["slices"]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    dur = np.zeros(4)
+    nb = max(1, min(3, args.steps))
+    for _ in range(nb):
+        ev[0].record(stream)
+        e, f = hs.split_exponents(dA, dB)
+        ev[1].record(stream)
+        As, Bs = hs.split_slices(dA, dB, e, f, "bf16", S)
+        ev[2].record(stream)
+        D = hs.split_diagonals(As, Bs, n, n, n, "bf16", S, P=SPLIT["P"], Q=SPLIT["Q"],
+                               G=SPLIT["G"], b=SPLIT["b"], Bouter=SPLIT["Bouter"])
+        ev[3].record(stream)
+        hs.split_recombine(D, e, f, n, n, n, "bf16", S)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        dur += np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+    dur /= nb
+    counters = hs.counters()
+    del As, Bs, D
+    torch.cuda.empty_cache()
+    npairs = S * (S + 1) // 2
+    peaks = read_peaks()
+    bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    gemm_tflops = npairs * flops() / (dur[2] * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "kernel": "bf16_diag_kernel",
+                "achieved": gemm_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": gemm_tflops / bf16_peak,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)",
+                "algorithmic": f"{npairs} bf16 products x 2 n^3 per launch",
+                "traffic": None}
+    breakdown_ms = {"exponent_scan": dur[0], "slicing": dur[1], "diagonal_products": dur[2],
+                    "recombination": dur[3]}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if rank == 0 or world > 1:
+        hA = dA.cpu().pin_memory()
+        hB = dB.cpu().pin_memory()
+        hC = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        hs.gemm_host(hA, hB, hC, **SPLIT)
+        t0 = time.perf_counter()
+        reps = max(1, min(2, args.steps))
+        for _ in range(reps):
+            hs.gemm_host(hA, hB, hC, **SPLIT)
+        te = (time.perf_counter() - t0) / reps
+        e2e = {"value": world * flops() / te / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
+               "ms_per_step": te * 1e3}
+        del hA, hB, hC
+
+    # accuracy of the measured product on sampled entries (compensated reference)
+    acc = {}
+    try:
+        from oracle import native, split
+        x = workloads.splitmix64(77, 0, 2048)
+        rows = np.unique((x[0::2] % np.uint64(n)).astype(np.int64))[:256]
+        cols = (x[1::2] % np.uint64(n)).astype(np.int64)[:rows.size]
+        Ah = dA[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+        Bh = dB.cpu().numpy()
+        ref, absab = native.dot2_entries(Ah, Bh, np.arange(rows.size), cols)
+        got = dC[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")]
+        acc["split_max_rel_err"] = split.max_rel_error(got.cpu().numpy(), ref, absab)
+        acc["tolerance_2Ku"] = split.tolerance(n)
+    except Exception as ex:  # accuracy is reported, not required for timing
+        acc["error"] = repr(ex)
+
+    # native binary64 path on the same inputs
+    native_out = None
+    if args.native_steps > 0:
+        dC2 = torch.empty_like(dC)
+        hs.gemm(dA, dB, out=dC2, **NATIVE)
+        hs.sync()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.native_steps):
+            hs.gemm(dA, dB, out=dC2, **NATIVE)
+        f1.record(stream)
+        barrier()
+        nms = f0.elapsed_time(f1) / args.native_steps
+        ntf = flops() / (nms * 1e-3) / 1e12
+        dmma_peak = hs.peak("dmma", 4000) / 1e12
+        native_out = {"tflops": ntf, "ms_per_step": nms,
+                      "roofline": {"bound": "fp64 tensor (DMMA)", "achieved": ntf,
+                                   "peak": dmma_peak, "unit": "TFLOP/s",
+                                   "frac": ntf / dmma_peak,
+                                   "peak_source": "measured by hsumma_peak(DMMA) in this run"}}
+        try:
+            got = dC2[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")]
+            acc["native_max_rel_err"] = split.max_rel_error(got.cpu().numpy(), ref, absab)
+        except Exception:
+            pass
+        del dC2
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        Ah = dA[:256].cpu().numpy()
+        Bh = dB.cpu().numpy()
+        rate, rws, cores, dt = cpu_oracle_rate(Ah, Bh, target_s=12.0)
+        cpu = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"{rws} rows of C at n=16384 by the plain binary64 triple loop "
+                         f"({dt:.1f} s)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC,
+            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (2 GiB each)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 6 * args.steps, "clocks": clk,
+            "breakdown_ms": breakdown_ms, "native_fp64": native_out, "accuracy": acc,
+            "counters": counters,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -15,9 +15,10 @@
  * Conventions for every entry point:
  *   - matrices are row-major binary64; A is M x K with leading dimension
  *     lda >= K, B is K x N (ldb >= N), C is M x N (ldc >= N); leading
- *     dimensions are counted in elements and must be multiples of 2 (the
- *     Tensor Memory Accelerator needs 16-byte row strides); base pointers must
- *     be 16-byte aligned;
+ *     dimensions are counted in elements; base pointers must be 8-byte
+ *     aligned.  The Tensor Memory Accelerator needs 16-byte aligned rows: with
+ *     an odd leading dimension or a base that is not 16-byte aligned, the
+ *     binary64 path first copies A or B into library workspace;
  *   - pointers named d_* are device pointers owned by the caller; h_* are host
  *     pointers owned by the caller; the library never frees caller memory;
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream); work is
@@ -105,7 +106,8 @@ int hsumma_workspace_size(int64_t M, int64_t N, int64_t K, int mode,
  * between groups").  Blocks are ceil(M/P) x ceil(N/Q) and the last ones may
  * be short (the paper assumes divisibility; short blocks are allowed here);
  * 1 <= P, Q <= 65535; G must factor as above; b a multiple of 16 in 16..256
- * for FP64 and of 64 in 64..256 for the split kinds; Bouter a multiple of b.  P = Q = G = b = Bouter = 0 asks the library to choose them
+ * for FP64 and of 64 in 64..256 for the split kinds; Bouter a multiple of b.
+ * P = Q = G = b = Bouter = 0 asks the library to choose them
  * (the learned cost model if one is loaded, else exhaustive timing of the
  * candidate set).  C is overwritten (beta = 0).  M, N or K = 0 is allowed
  * (K = 0 writes zeros).  The split kinds (Ozaki-style) need

@@ -107,9 +107,16 @@ def _check(status: int):
         raise HsummaError(status, last_error())
 
 
-def _stream_ptr(stream=None):
+_DEFAULT = object()
+
+
+def _stream_ptr(stream=_DEFAULT):
+    """cudaStream_t of a torch stream; torch's current stream by default; None
+    is the legacy default stream."""
+    if stream is None:
+        return ctypes.c_void_p(0)
     import torch
-    s = stream if stream is not None else torch.cuda.current_stream()
+    s = stream if stream is not _DEFAULT else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
 
 
@@ -160,7 +167,7 @@ def _check_f64(t, name):
         raise ValueError(f"{name} must be 2-D with unit column stride")
 
 
-def gemm(A, B, *, P, Q, G, b, Bouter, kind="fp64", slices=0, out=None, stream=None):
+def gemm(A, B, *, P, Q, G, b, Bouter, kind="fp64", slices=0, out=None, stream=_DEFAULT):
     """C = A x B by HSUMMA on a virtual P x Q grid with G groups (torch tensors on
     the GPU, float64, row-major)."""
     import torch
@@ -173,14 +180,15 @@ def gemm(A, B, *, P, Q, G, b, Bouter, kind="fp64", slices=0, out=None, stream=No
     _ensure_init(A)
     C = out if out is not None else torch.empty((M, N), dtype=torch.float64, device=A.device)
     _check_f64(C, "C")
-    _check(lib().hsumma_gemm(M, N, K, A.data_ptr(), A.stride(0) if M else max(K, 2),
-                             B.data_ptr(), B.stride(0) if K else max(N, 2), C.data_ptr(),
-                             C.stride(0) if M else max(N, 2), P, Q, G, b, Bouter,
-                             mode_code(kind, slices), _stream_ptr(stream)))
+    lda = A.stride(0) if (M and K) else max(K, 1)
+    ldb = B.stride(0) if (K and N) else max(N, 1)
+    ldc = C.stride(0) if (M and N) else max(N, 1)
+    _check(lib().hsumma_gemm(M, N, K, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(), ldc,
+                             P, Q, G, b, Bouter, mode_code(kind, slices), _stream_ptr(stream)))
     return C
 
 
-def gemm_host(A, B, C, *, P, Q, G, b, Bouter, kind="fp64", slices=0, stream=None):
+def gemm_host(A, B, C, *, P, Q, G, b, Bouter, kind="fp64", slices=0, stream=_DEFAULT):
     """The same product from host memory (numpy or CPU torch float64 arrays,
     row-major); C is written in place."""
     def ptr_ld(x):
@@ -196,7 +204,7 @@ def gemm_host(A, B, C, *, P, Q, G, b, Bouter, kind="fp64", slices=0, stream=None
     return C
 
 
-def sync(stream=None):
+def sync(stream=_DEFAULT):
     _check(lib().hsumma_sync(_stream_ptr(stream)))
 
 
@@ -207,7 +215,7 @@ def counters() -> dict:
 
 
 # ---- split path, step by step ----
-def split_exponents(A, B, stream=None):
+def split_exponents(A, B, stream=_DEFAULT):
     import torch
     _check_f64(A, "A")
     _check_f64(B, "B")
@@ -222,7 +230,7 @@ def split_exponents(A, B, stream=None):
     return e, f
 
 
-def split_slices(A, B, e, f, kind, S, stream=None):
+def split_slices(A, B, e, f, kind, S, stream=_DEFAULT):
     import torch
     _ensure_init(A)
     M, K = A.shape
@@ -244,7 +252,7 @@ def split_planes(K, kind, S) -> int:
     return n
 
 
-def split_diagonals(As, Bs, M, N, K, kind, S, *, P, Q, G, b, Bouter, stream=None):
+def split_diagonals(As, Bs, M, N, K, kind, S, *, P, Q, G, b, Bouter, stream=_DEFAULT):
     import torch
     _ensure_init(As)
     g = split_planes(K, kind, S)
@@ -255,12 +263,12 @@ def split_diagonals(As, Bs, M, N, K, kind, S, *, P, Q, G, b, Bouter, stream=None
     return D
 
 
-def split_recombine(D, e, f, M, N, K, kind, S, stream=None):
+def split_recombine(D, e, f, M, N, K, kind, S, stream=_DEFAULT):
     import torch
     _ensure_init(D)
     C = torch.empty((M, N), dtype=torch.float64, device=D.device)
     _check(lib().hsumma_split_recombine(M, N, K, KINDS[kind], S, D.data_ptr(), e.data_ptr(),
-                                        f.data_ptr(), C.data_ptr(), max(N, 2),
+                                        f.data_ptr(), C.data_ptr(), max(N, 1),
                                         _stream_ptr(stream)))
     return C
 

@@ -143,24 +143,25 @@ static int check_matrix_args(int64_t M, int64_t N, int64_t K, const void *A, int
     set_error("sizes above 2^31 are not supported");
     return HSUMMA_ERR_UNSUPPORTED;
   }
-  if (lda < (K > 0 ? K : 1) || ldb < (N > 0 ? N : 1) || ldc < (N > 0 ? N : 1)) {
+  if ((M && K && lda < K) || (K && N && ldb < N) || (C && M && N && ldc < N)) {
     set_error("leading dimensions too small (lda=%lld ldb=%lld ldc=%lld)", (long long)lda,
               (long long)ldb, (long long)ldc);
     return HSUMMA_ERR_ARG;
   }
-  if ((lda | ldb | ldc) & 1) {
-    set_error("leading dimensions must be even (16-byte row strides)");
+  if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 7) {
+    set_error("matrix base pointers must be 8-byte aligned");
     return HSUMMA_ERR_ARG;
   }
-  if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15) {
-    set_error("matrix base pointers must be 16-byte aligned");
-    return HSUMMA_ERR_ARG;
-  }
-  if ((M && K && !A) || (K && N && !B) || (M && N && !C)) {
+  if ((M && K && !A) || (K && N && !B)) {
     set_error("null matrix pointer");
     return HSUMMA_ERR_ARG;
   }
   return HSUMMA_OK;
+}
+
+// The Tensor Memory Accelerator needs 16-byte aligned bases and row strides.
+static bool tma_ready(const void *p, int64_t ld) {
+  return (((uintptr_t)p) & 15) == 0 && (ld & 1) == 0;
 }
 
 }  // namespace hs
@@ -380,7 +381,35 @@ int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
     e = cudaMemset2DAsync(C, ldc * 8, 0, N * 8, M, s);
     return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "cudaMemset2DAsync");
   }
-  if (kind == HSUMMA_FP64) return launch_fp64_hsumma(g, A, lda, B, ldb, C, ldc, s);
+  if (kind == HSUMMA_FP64) {
+    // operands the Tensor Memory Accelerator cannot address directly (odd
+    // leading dimension, base not 16-byte aligned) are copied into library
+    // workspace with even row strides first
+    const bool ra = !tma_ready(A, lda), rb = !tma_ready(B, ldb);
+    if (ra || rb) {
+      const int64_t la = (K + 1) & ~int64_t(1), lb = (N + 1) & ~int64_t(1);
+      const size_t ba = ra ? ((size_t)M * la * 8 + 255) & ~size_t(255) : 0;
+      const size_t bb = rb ? (size_t)K * lb * 8 : 0;
+      st = ensure_workspace(ba + bb);
+      if (st != HSUMMA_OK) return st;
+      uint8_t *ws = reinterpret_cast<uint8_t *>(g_state.workspace);
+      if (ra) {
+        double *a2 = reinterpret_cast<double *>(ws);
+        e = cudaMemcpy2DAsync(a2, la * 8, A, lda * 8, K * 8, M, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "repack A");
+        A = a2;
+        lda = la;
+      }
+      if (rb) {
+        double *b2 = reinterpret_cast<double *>(ws + ba);
+        e = cudaMemcpy2DAsync(b2, lb * 8, B, ldb * 8, N * 8, K, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "repack B");
+        B = b2;
+        ldb = lb;
+      }
+    }
+    return launch_fp64_hsumma(g, A, lda, B, ldb, C, ldc, s);
+  }
 
   // split path: exponents, slices, exact diagonal sums, recombination
   // exactness of the recombination: a diagonal's planes sum to at most
@@ -511,7 +540,7 @@ int hsumma_split_exponents(int64_t M, int64_t N, int64_t K, const double *A, int
     set_error("hsumma_init has not been called");
     return HSUMMA_ERR_NOT_INIT;
   }
-  int st = check_matrix_args(M, N, K, A, lda, B, ldb, A, lda);
+  int st = check_matrix_args(M, N, K, A, lda, B, ldb, nullptr, 0);
   if (st != HSUMMA_OK) return st;
   if ((M && !e) || (N && !f)) {
     set_error("null exponent pointer");
@@ -528,7 +557,7 @@ int hsumma_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
     set_error("hsumma_init has not been called");
     return HSUMMA_ERR_NOT_INIT;
   }
-  int st = check_matrix_args(M, N, K, A, lda, B, ldb, A, lda);
+  int st = check_matrix_args(M, N, K, A, lda, B, ldb, nullptr, 0);
   if (st != HSUMMA_OK) return st;
   int k2, s2;
   st = split_kind_and_S(HSUMMA_MODE(kind, S), &k2, &s2);

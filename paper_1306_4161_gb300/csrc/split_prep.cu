@@ -47,13 +47,17 @@ __global__ void exponents_rows_kernel(const double *__restrict__ A, int64_t lda,
   if (row >= M) return;
   const double *a = A + row * lda;
   unsigned long long m = 0;
-  // lda is even and A 16-byte aligned: every row starts 16-byte aligned
-  const int64_t K2 = K & ~int64_t(1);
-  for (int64_t k = 2 * lane; k < K2; k += 64) {
-    const double2 v = *reinterpret_cast<const double2 *>(a + k);
-    m = max(m, max(absbits(v.x), absbits(v.y)));
+  if ((reinterpret_cast<uintptr_t>(a) & 15) == 0) {
+    // 16-byte aligned row: pairs
+    const int64_t K2 = K & ~int64_t(1);
+    for (int64_t k = 2 * lane; k < K2; k += 64) {
+      const double2 v = *reinterpret_cast<const double2 *>(a + k);
+      m = max(m, max(absbits(v.x), absbits(v.y)));
+    }
+    if ((K & 1) && lane == 0) m = max(m, absbits(a[K - 1]));
+  } else {
+    for (int64_t k = lane; k < K; k += 32) m = max(m, absbits(a[k]));
   }
-  if ((K & 1) && lane == 0) m = max(m, absbits(a[K - 1]));
 #pragma unroll
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) {
@@ -70,14 +74,18 @@ __global__ void exponents_cols_kernel(const double *__restrict__ B, int64_t ldb,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t j0 = (int64_t)blockIdx.x * 64 + 2 * lane;
   unsigned long long m0 = 0, m1 = 0;
-  if (j0 + 1 < N) {
+  const bool pairs = ((reinterpret_cast<uintptr_t>(B) | (uintptr_t)(ldb * 8)) & 15) == 0;
+  if (j0 + 1 < N && pairs) {
     for (int64_t k = warp; k < K; k += 8) {
       const double2 v = *reinterpret_cast<const double2 *>(B + k * ldb + j0);
       m0 = max(m0, absbits(v.x));
       m1 = max(m1, absbits(v.y));
     }
-  } else if (j0 < N) {
-    for (int64_t k = warp; k < K; k += 8) m0 = max(m0, absbits(B[k * ldb + j0]));
+  } else {
+    for (int64_t k = warp; k < K; k += 8) {
+      if (j0 < N) m0 = max(m0, absbits(B[k * ldb + j0]));
+      if (j0 + 1 < N) m1 = max(m1, absbits(B[k * ldb + j0 + 1]));
+    }
   }
   part[warp][2 * lane] = m0;
   part[warp][2 * lane + 1] = m1;

@@ -184,3 +184,59 @@ def test_full_size_16384_sampled():
     assert np.array_equal(got, want)
     ref, absab = native.dot2_entries(A, B, ri, ci)
     assert split.max_rel_error(got, ref, absab) <= split.tolerance(n)
+
+
+@pytest.mark.parametrize("M,N,K,P,Q,G,S", [
+    (300, 600, 1000, 3, 3, 9, 3),
+    (300, 600, 1000, 3, 3, 1, 2),
+    (512, 512, 4096, 4, 4, 4, 6),
+    (130, 260, 64, 1, 1, 1, 8),
+])
+def test_int8_diagonals_exact(M, N, K, P, Q, G, S):
+    hs = lib_ready()
+    torch = torch_cuda()
+    A, B, dA, dB = pair(M, N, K, 23, "wide", "uniform")
+    e, f = hs.split_exponents(dA, dB)
+    As, Bs = hs.split_slices(dA, dB, e, f, "int8", S)
+    D = hs.split_diagonals(As, Bs, M, N, K, "int8", S, P=P, Q=Q, G=G, b=128, Bouter=256)
+    hs.sync()
+    _, parts = split.split_gemm(A, B, S, "int8", return_parts=True)
+    Dg = D.to(torch.int64).sum(dim=1).cpu().numpy()
+    for d in range(2, S + 2):
+        assert np.array_equal(Dg[d - 2], parts["D"][d]), d
+    npairs = S * (S + 1) // 2
+    I, J, cm, cn = hs.group_shape(P, Q, G)
+    want = gsched.counters_closed_form(M, N, K, P, Q, cm, cn, 128, 128, 256, npairs)
+    c = hs.counters()
+    for k, v in want.items():
+        assert c[k] == v, (k, c[k], v)
+
+
+@pytest.mark.parametrize("S,dist", [(6, "uniform"), (8, "wide")])
+def test_int8_gemm_bit_exact_with_oracle(S, dist):
+    hs = lib_ready()
+    M, N, K = 200, 300, 700
+    A, B, dA, dB = pair(M, N, K, 37, dist)
+    C = hs.gemm(dA, dB, P=2, Q=2, G=1, b=128, Bouter=256, kind="int8", slices=S)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, S, "int8"))
+
+
+def test_odd_leading_dimensions():
+    hs = lib_ready()
+    torch = torch_cuda()
+    M, N, K = 37, 41, 53
+    A, B, _, _ = pair(M, N, K, 41, "smallint")
+    # views with odd leading dimensions and an 8-byte (not 16-byte) aligned base
+    bigA = torch.zeros((M, K + 2), dtype=torch.float64, device="cuda")
+    bigB = torch.zeros((K, N + 2), dtype=torch.float64, device="cuda")
+    dA = bigA[:, 1:K + 1]
+    dB = bigB[:, 1:N + 1]
+    dA.copy_(torch.from_numpy(A))
+    dB.copy_(torch.from_numpy(B))
+    C = hs.gemm(dA, dB, P=2, Q=2, G=1, b=16, Bouter=32)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), native.dgemm(A, B))
+    C = hs.gemm(dA, dB, P=2, Q=2, G=4, b=64, Bouter=64, kind="bf16", slices=2)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 2, "bf16"))
