@@ -218,6 +218,23 @@ __device__ __forceinline__ void regs_dec() {
   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
 }
 
+// Which virtual processor a CTA plays.  Clusters are launched in cluster-index
+// order; consecutive clusters are walked down columns of `rows` cluster rows,
+// so the clusters resident at one time cover a square-ish part of C and the
+// panels they stream stay in L2.  Returns the processor row r and column c of
+// this CTA (its position inside the cluster is unchanged).
+__device__ __forceinline__ void raster_proc(int cm, int cn, int cy, int cx, int rows,
+                                            int *r, int *c) {
+  const int ncx = (int)gridDim.x / cn, ncy = (int)gridDim.y / cm;
+  const int L = ((int)blockIdx.y / cm) * ncx + (int)blockIdx.x / cn;
+  const int group = L / (rows * ncx);
+  const int in_group = min(rows, ncy - group * rows);
+  const int idx = L - group * rows * ncx;
+  const int gy = group * rows + idx % in_group, gx = idx / in_group;
+  *r = gy * cm + cy;
+  *c = gx * cn + cx;
+}
+
 // Byte offset of 16-byte chunk `chunk` (0..7) of row `row` inside a 128-byte
 // swizzled tile (CU_TENSOR_MAP_SWIZZLE_128B): chunk index XOR (row mod 8).
 __device__ __forceinline__ uint32_t swz128(uint32_t row, uint32_t byte_in_row) {

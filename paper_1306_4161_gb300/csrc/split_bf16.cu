@@ -81,9 +81,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = blockIdx.y, c = blockIdx.x;
   const int cx = (int)cluster_ctaid_x(), cy = (int)cluster_ctaid_y();
   const int cn = p.cn, cm = p.cm;
+  int r, c;
+  raster_proc(cm, cn, cy, cx, 8, &r, &c);
   const uint16_t row_mask = (uint16_t)(((1u << cn) - 1u) << (cy * cn));
   uint16_t col_mask = 0;
   for (int y = 0; y < cm; ++y) col_mask |= (uint16_t)(1u << (y * cn + cx));

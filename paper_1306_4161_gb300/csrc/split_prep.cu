@@ -124,12 +124,11 @@ __device__ __forceinline__ void digits_of(double x, int e, int S, int (&t)[S_MAX
       t[s - 1] = 0;
       continue;
     }
-    // |x| 2^-e 2^(w s) = m 2^sh
+    // |x| 2^-e 2^(w s) = m 2^sh, rounded to nearest (ties to even):
+    // RNE(m / 2^d) = (m + 2^(d-1) - 1 + ((m >> d) & 1)) >> d for 1 <= d <= 54
     const int sh = lsb - e + W * s;
     unsigned long long y;
-    if (m == 0) {
-      y = 0;
-    } else if (sh >= 0) {
+    if (sh >= 0) {
       // m 2^sh < 2^(w s - 1) <= 2^55 when e comes from the exponent scan (the
       // guard only keeps the shift defined for other e)
       y = m << (sh < 63 ? sh : 63);
@@ -137,9 +136,7 @@ __device__ __forceinline__ void digits_of(double x, int e, int S, int (&t)[S_MAX
       y = 0;        // m 2^sh < 2^53 2^-55 < 1/2
     } else {
       const int d = -sh;
-      const unsigned long long q = m >> d, rem = m & ((1ull << d) - 1ull),
-                               half = 1ull << (d - 1);
-      y = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+      y = (m + ((1ull << (d - 1)) - 1ull) + ((m >> d) & 1ull)) >> d;
     }
     const long long Y = neg ? -(long long)y : (long long)y;
     t[s - 1] = (int)(Y - prev * (1ll << W));
@@ -161,12 +158,21 @@ __global__ void slices_rows_kernel(const double *__restrict__ A, int64_t lda, in
   const int64_t i = gid / groups, k0 = (gid % groups) * 4;
   const int ei = e[i];
   int t[4][SMAX];
+  double x[4];
+  const double *a = A + i * lda + k0;
+  if (k0 + 3 < K && (reinterpret_cast<uintptr_t>(a) & 15) == 0) {
+    const double2 v0 = reinterpret_cast<const double2 *>(a)[0];
+    const double2 v1 = reinterpret_cast<const double2 *>(a)[1];
+    x[0] = v0.x;
+    x[1] = v0.y;
+    x[2] = v1.x;
+    x[3] = v1.y;
+  } else {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int64_t k = k0 + u;
-    const double x = k < K ? A[i * lda + k] : 0.0;
-    digits_of<W, SMAX>(x, ei, S, t[u]);
+    for (int u = 0; u < 4; ++u) x[u] = k0 + u < K ? a[u] : 0.0;
   }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) digits_of<W, SMAX>(x[u], ei, S, t[u]);
   for (int s = 0; s < S; ++s) {
     const int64_t off = ((int64_t)s * M + i) * Kp + k0;
     if (KIND == HSUMMA_INT8_SLICES) {
@@ -227,7 +233,7 @@ __global__ void slices_cols_kernel(const double *__restrict__ B, int64_t ldb, in
 
 // RN(X 2^k) for a 128-bit integer X, ties to even, subnormals and overflow
 // handled: the value is rounded once, at the precision its exponent allows.
-__device__ __forceinline__ double round_scaled_i128(__int128 X, int k) {
+__device__ __noinline__ double round_scaled_i128(__int128 X, int k) {
   if (X == 0) return 0.0;
   const bool neg = X < 0;
   unsigned __int128 m = neg ? (unsigned __int128)(-X) : (unsigned __int128)X;
@@ -267,22 +273,78 @@ __device__ __forceinline__ double round_scaled_i128(__int128 X, int k) {
   return __longlong_as_double((long long)bits);
 }
 
-template <int W>
-__global__ void recombine_kernel(const int32_t *__restrict__ D, int S, int nseg, int64_t M,
-                                 int64_t N, const int32_t *__restrict__ e,
-                                 const int32_t *__restrict__ f, double *__restrict__ C,
-                                 int64_t ldc) {
+// The same for X that fits in 64 bits and a normal result (the common case):
+// 64-bit integer work only; anything else goes to the general routine.
+__device__ __forceinline__ double round_scaled(__int128 X, int k) {
+  const long long lo = (long long)X;
+  if ((__int128)lo == X && lo != 0) {
+    const bool neg = lo < 0;
+    const unsigned long long m = neg ? 0ull - (unsigned long long)lo : (unsigned long long)lo;
+    const int nb = 64 - __clzll((long long)m);
+    const int drop = nb - 53;
+    unsigned long long q;
+    int ulp;
+    if (drop <= 0) {
+      q = m << (-drop);
+      ulp = k + drop;
+    } else {
+      q = (m + ((1ull << (drop - 1)) - 1ull) + ((m >> drop) & 1ull)) >> drop;
+      ulp = k + drop;
+      if (q == (1ull << 53)) {
+        q >>= 1;
+        ulp += 1;
+      }
+    }
+    const int biased = ulp + 1075;
+    if (biased >= 1 && biased <= 2046) {
+      const unsigned long long bits = ((unsigned long long)biased << 52) |
+                                      (q & 0xFFFFFFFFFFFFFull) |
+                                      (neg ? 0x8000000000000000ull : 0ull);
+      return __longlong_as_double((long long)bits);
+    }
+  }
+  return round_scaled_i128(X, k);
+}
+
+// X = sum_d D_d 2^(w (S+1-d)) by Horner's rule (constant shifts), rounded once.
+template <int W, int S>
+__global__ void recombine_kernel(const int32_t *__restrict__ D, int nseg, int64_t M, int64_t N,
+                                 const int32_t *__restrict__ e, const int32_t *__restrict__ f,
+                                 double *__restrict__ C, int64_t ldc) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = blockIdx.y;
   if (j >= N) return;
-  const int64_t plane = M * N;
+  const int64_t plane = M * N, off = i * N + j;
   __int128 X = 0;
+#pragma unroll
   for (int d = 2; d <= S + 1; ++d) {
     long long Dd = 0;   // the segment planes of a diagonal sum exactly in 64 bits
-    for (int g = 0; g < nseg; ++g) Dd += D[(int64_t)((d - 2) * nseg + g) * plane + i * N + j];
-    X += (__int128)Dd << (W * (S + 1 - d));
+    for (int g = 0; g < nseg; ++g) Dd += __ldg(D + (int64_t)((d - 2) * nseg + g) * plane + off);
+    X = (X << W) + (__int128)Dd;
   }
-  C[i * ldc + j] = round_scaled_i128(X, e[i] + f[j] - W * (S + 1));
+  C[i * ldc + j] = round_scaled(X, e[i] + f[j] - W * (S + 1));
+}
+
+template <int W, int S>
+void recombine_launch(dim3 grid, cudaStream_t s, const int32_t *D, int nseg, int64_t M,
+                      int64_t N, const int32_t *e, const int32_t *f, double *C, int64_t ldc) {
+  recombine_kernel<W, S><<<grid, 256, 0, s>>>(D, nseg, M, N, e, f, C, ldc);
+}
+
+template <int W>
+void recombine_dispatch(int S, dim3 grid, cudaStream_t s, const int32_t *D, int nseg,
+                        int64_t M, int64_t N, const int32_t *e, const int32_t *f, double *C,
+                        int64_t ldc) {
+  switch (S) {
+    case 1: recombine_launch<W, 1>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+    case 2: recombine_launch<W, 2>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+    case 3: recombine_launch<W, 3>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+    case 4: recombine_launch<W, 4>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+    case 5: recombine_launch<W, 5>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+    case 6: recombine_launch<W, 6>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+    case 7: recombine_launch<W, 7>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+    default: recombine_launch<W, 8>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+  }
 }
 
 }  // namespace
@@ -336,11 +398,9 @@ int launch_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, con
     const int64_t rows = (M - r0) < 65535 ? (M - r0) : 65535;
     dim3 grid((unsigned)ceil_div(N, 256), (unsigned)rows);
     if (kind == HSUMMA_INT8_SLICES)
-      recombine_kernel<7><<<grid, 256, 0, s>>>(D + r0 * N, S, nseg, M, N, e + r0, f,
-                                               C + r0 * ldc, ldc);
+      recombine_dispatch<7>(S, grid, s, D + r0 * N, nseg, M, N, e + r0, f, C + r0 * ldc, ldc);
     else
-      recombine_kernel<8><<<grid, 256, 0, s>>>(D + r0 * N, S, nseg, M, N, e + r0, f,
-                                               C + r0 * ldc, ldc);
+      recombine_dispatch<8>(S, grid, s, D + r0 * N, nseg, M, N, e + r0, f, C + r0 * ldc, ldc);
   }
   cudaError_t err = cudaGetLastError();
   return err == cudaSuccess ? HSUMMA_OK : cuda_fail(err, "launch recombination");

@@ -111,9 +111,15 @@ def test_argument_errors():
         with pytest.raises(hs.HsummaError) as ei:
             hs.gemm(dA, dB, **kw)
         assert ei.value.status == code
-    bad = torch.empty(64 * 64 + 1, dtype=torch.float64, device="cuda")[1:].view(64, 64)
-    with pytest.raises(hs.HsummaError):
-        hs.gemm(bad, dB, P=1, Q=1, G=1, b=16, Bouter=16)
+    # a base that is not 8-byte aligned is rejected before any device access
+    dC = torch.empty((64, 64), dtype=torch.float64, device="cuda")
+    st = hs.lib().hsumma_gemm(64, 64, 64, dA.data_ptr() + 4, 64, dB.data_ptr(), 64,
+                              dC.data_ptr(), 64, 1, 1, 1, 16, 16, 0, None)
+    assert st == -1 and "aligned" in hs.last_error()
+    # a leading dimension below the row length
+    st = hs.lib().hsumma_gemm(64, 64, 64, dA.data_ptr(), 63, dB.data_ptr(), 64,
+                              dC.data_ptr(), 64, 1, 1, 1, 16, 16, 0, None)
+    assert st == -1
 
 
 def test_host_buffers_entry():

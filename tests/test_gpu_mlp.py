@@ -62,8 +62,11 @@ def test_adam_matches_oracle():
     hs._check(hs.lib().hsumma_mlp_adam(mlp.N_PARAMS, dth.data_ptr(), dg.data_ptr(), dm.data_ptr(),
                                         dv.data_ptr(), 3, 1e-3, 0.9, 0.999, 1e-8, None))
     hs.sync(None)
-    f = lambda a: a.astype(np.float32).astype(np.float64)
-    t1, m1, v1 = mlp.adam_step(f(th), f(gr), f(m0), f(v0), 3)
+    f = lambda a: np.asarray(a).astype(np.float32).astype(np.float64)
+    # the kernel trains in fp32: its hyperparameters are the fp32 roundings
+    # (0.999 is not exact in fp32, so 1 - beta2 differs by ~1e-5 relative)
+    hp = {k: float(f(v)) for k, v in dict(lr=1e-3, b1=0.9, b2=0.999, eps=1e-8).items()}
+    t1, m1, v1 = mlp.adam_step(f(th), f(gr), f(m0), f(v0), 3, **hp)
     assert np.allclose(dth.cpu().numpy(), t1, rtol=1e-5, atol=1e-7)
     assert np.allclose(dm.cpu().numpy(), m1, rtol=1e-5, atol=1e-7)
     assert np.allclose(dv.cpu().numpy(), v1, rtol=1e-5, atol=1e-9)
