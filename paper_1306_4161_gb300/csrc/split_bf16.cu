@@ -66,6 +66,18 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
   }
 }
 
+// cluster tile L -> processor row r and column c of this CTA: tiles are
+// walked down columns of 8 cluster rows (see raster_proc)
+__device__ __forceinline__ void tile_proc(int L, int ncx, int ncy, int cm, int cn, int cy,
+                                          int cx, int *r, int *c) {
+  const int rows = 8;
+  const int group = L / (rows * ncx);
+  const int in_group = min(rows, ncy - group * rows);
+  const int idx = L - group * rows * ncx;
+  *r = (group * rows + idx % in_group) * cm + cy;
+  *c = (idx / in_group) * cn + cx;
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
     bf16_diag_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB,
@@ -83,8 +95,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cx = (int)cluster_ctaid_x(), cy = (int)cluster_ctaid_y();
   const int cn = p.cn, cm = p.cm;
-  int r, c;
-  raster_proc(cm, cn, cy, cx, 8, &r, &c);
+  // persistent clusters: cluster `cid` plays the virtual processors of the
+  // cluster tiles L = cid, cid + ncl, ... (walked in raster order), so the
+  // clusters resident together work on neighbouring blocks in step
+  const int ncl = (int)gridDim.x / cn, cid = (int)blockIdx.x / cn;
+  const int ncx = p.Q / cn, ncy = p.P / cm, ntiles = ncx * ncy;
   const uint16_t row_mask = (uint16_t)(((1u << cn) - 1u) << (cy * cn));
   uint16_t col_mask = 0;
   for (int y = 0; y < cm; ++y) col_mask |= (uint16_t)(1u << (y * cn + cx));
@@ -116,8 +131,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
   cluster_sync();
 
-  const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
-  const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
   const int S = p.S, nkb = p.nkb;
   const int64_t nout = (p.Kpad + p.Bo - 1) / p.Bo;
   // rows per TMA box: the CTA's contiguous share of a tile when the cluster
@@ -131,72 +144,78 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       unsigned long long a_ld = 0, a_dl = 0, b_ld = 0, b_dl = 0, pf = 0, nops = 0;
       uint32_t stage = 0, phase = 0;
       bool ok = true;
-      for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-        const int64_t m0 = row_lo + (int64_t)mi * TM;
-        for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-          const int64_t n0 = col_lo + (int64_t)ni * TN;
-          for (int d = 2; d <= S + 1 && ok; ++d) {
-            for (int s = 1; s < d && ok; ++s) {
-              const int t = d - s;
-              for (int kb = 0; kb < nkb; ++kb) {
-                const int64_t k0 = (int64_t)kb * BKS;
-                if (k0 % p.Bo == 0) {
-                  // outer step: owners stage outer panel o (at the start) and o + 1
-                  const int64_t o = k0 / p.Bo;
-                  for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
-                    const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
-                    if (c == (int)imin64(p.Q - 1, kq / p.Kq)) {
-                      for (int64_t kk = kq; kk < kend; kk += BKS)
-                        tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, s - 1);
-                      pf += 1;
-                    }
-                    if (r == (int)imin64(p.P - 1, kq / p.Kp)) {
-                      for (int64_t kk = kq; kk < kend; kk += BKS)
-                        tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, t - 1);
-                      pf += 1;
+      for (int L = cid; L < ntiles && ok; L += ncl) {
+        int r, c;
+        tile_proc(L, ncx, ncy, cm, cn, cy, cx, &r, &c);
+        const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
+        const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
+        for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
+          const int64_t m0 = row_lo + (int64_t)mi * TM;
+          for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
+            const int64_t n0 = col_lo + (int64_t)ni * TN;
+            for (int d = 2; d <= S + 1 && ok; ++d) {
+              for (int s = 1; s < d && ok; ++s) {
+                const int t = d - s;
+                for (int kb = 0; kb < nkb; ++kb) {
+                  const int64_t k0 = (int64_t)kb * BKS;
+                  if (k0 % p.Bo == 0) {
+                    // outer step: owners stage outer panel o (at the start) and o + 1
+                    const int64_t o = k0 / p.Bo;
+                    for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
+                      const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
+                      if (c == (int)imin64(p.Q - 1, kq / p.Kq)) {
+                        for (int64_t kk = kq; kk < kend; kk += BKS)
+                          tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, s - 1);
+                        pf += 1;
+                      }
+                      if (r == (int)imin64(p.P - 1, kq / p.Kp)) {
+                        for (int64_t kk = kq; kk < kend; kk += BKS)
+                          tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, t - 1);
+                        pf += 1;
+                      }
                     }
                   }
+                  if (!wait_or_abort(smem_u32(&empty[stage]), phase ^ 1u, &abort_flag, true)) {
+                    if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteEmpty);
+                    abort_flag = 1;
+                    ok = false;
+                    break;
+                  }
+                  const uint32_t fb = smem_u32(&full[stage]);
+                  mbar_arrive_expect_tx(fb, STAGE_BYTES);
+                  const uint32_t a_base = smem_u32(smem + stage * STAGE_BYTES);
+                  const uint32_t b_base = a_base + A_BYTES;
+                  const int64_t kc = span(0, p.K, k0, k0 + BKS);
+                  // A tile (128 rows): contiguous share of the cluster row, or 8-row
+                  // pieces dealt round-robin when the width does not divide 16
+                  for (int i = a_contig ? cx * (a_box / 8) : cx; i < TM / 8;
+                       i += a_contig ? TM / 8 : cn) {
+                    const int64_t ar = m0 + (int64_t)i * 8;
+                    const uint32_t dst = a_base + i * 8 * 128;
+                    if (cn > 1)
+                      tma_load_3d_mc(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb, row_mask);
+                    else
+                      tma_load_3d(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb);
+                    const int64_t ca = span(row_lo, row_hi, ar, ar + a_box) * kc;
+                    a_ld += ca;
+                    a_dl += ca * cn;
+                    nops += 1;
+                  }
+                  for (int i = b_contig ? cy * (b_box / 8) : cy; i < TN / 8;
+                       i += b_contig ? TN / 8 : cm) {
+                    const int64_t br = n0 + (int64_t)i * 8;
+                    const uint32_t dst = b_base + i * 8 * 128;
+                    if (cm > 1)
+                      tma_load_3d_mc(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb, col_mask);
+                    else
+                      tma_load_3d(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb);
+                    const int64_t cb = span(col_lo, col_hi, br, br + b_box) * kc;
+                    b_ld += cb;
+                    b_dl += cb * cm;
+                    nops += 1;
+                  }
+                  if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
-                if (!wait_or_abort(smem_u32(&empty[stage]), phase ^ 1u, &abort_flag, true)) {
-                  if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteEmpty);
-                  abort_flag = 1;
-                  ok = false;
-                  break;
-                }
-                const uint32_t fb = smem_u32(&full[stage]);
-                mbar_arrive_expect_tx(fb, STAGE_BYTES);
-                const uint32_t a_base = smem_u32(smem + stage * STAGE_BYTES);
-                const uint32_t b_base = a_base + A_BYTES;
-                const int64_t kc = span(0, p.K, k0, k0 + BKS);
-                // A tile (128 rows): contiguous share of the cluster row, or 8-row
-                // pieces dealt round-robin when the width does not divide 16
-                for (int i = a_contig ? cx * (a_box / 8) : cx; i < TM / 8;
-                     i += a_contig ? TM / 8 : cn) {
-                  const int64_t ar = m0 + (int64_t)i * 8;
-                  const uint32_t dst = a_base + i * 8 * 128;
-                  if (cn > 1)
-                    tma_load_3d_mc(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb, row_mask);
-                  else
-                    tma_load_3d(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb);
-                  const int64_t ca = span(row_lo, row_hi, ar, ar + a_box) * kc;
-                  a_ld += ca;
-                  a_dl += ca * cn;
-                  nops += 1;
-                }
-                for (int i = b_contig ? cy * (b_box / 8) : cy; i < TN / 8;
-                     i += b_contig ? TN / 8 : cm) {
-                  const int64_t br = n0 + (int64_t)i * 8;
-                  const uint32_t dst = b_base + i * 8 * 128;
-                  if (cm > 1)
-                    tma_load_3d_mc(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb, col_mask);
-                  else
-                    tma_load_3d(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb);
-                  const int64_t cb = span(col_lo, col_hi, br, br + b_box) * kc;
-                  b_ld += cb;
-                  b_dl += cb * cm;
-                  nops += 1;
-                }
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
               }
             }
           }
@@ -225,46 +244,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t gc = 0;  // global chunk counter: buffer gc & 1, phase (gc >> 1) & 1
       const uint16_t rel_mask = row_mask | col_mask;
       bool ok = true;
-      for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-        for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-          for (int d = 2; d <= S + 1 && ok; ++d) {
-            const int nst = (d - 1) * nkb;
-            for (int st = 0; st < nst; ++st) {
-              const uint32_t buf = gc & 1u;
-              if (st % CH == 0) {
-                if (!wait_or_abort(smem_u32(&acc_empty[buf]), ((gc >> 1) & 1u) ^ 1u, &abort_flag,
-                                   false)) {
-                  if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteAccEmpty);
+      for (int L = cid; L < ntiles && ok; L += ncl) {
+        int r, c;
+        tile_proc(L, ncx, ncy, cm, cn, cy, cx, &r, &c);
+        const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
+        const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
+        for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
+          for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
+            for (int d = 2; d <= S + 1 && ok; ++d) {
+              const int nst = (d - 1) * nkb;
+              for (int st = 0; st < nst; ++st) {
+                const uint32_t buf = gc & 1u;
+                if (st % CH == 0) {
+                  if (!wait_or_abort(smem_u32(&acc_empty[buf]), ((gc >> 1) & 1u) ^ 1u, &abort_flag,
+                                     false)) {
+                    if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteAccEmpty);
+                    abort_flag = 1;
+                    ok = false;
+                    break;
+                  }
+                  tc_fence_after();
+                }
+                if (!wait_or_abort(smem_u32(&full[stage]), phase, &abort_flag, false)) {
+                  if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteFull);
                   abort_flag = 1;
                   ok = false;
                   break;
                 }
                 tc_fence_after();
-              }
-              if (!wait_or_abort(smem_u32(&full[stage]), phase, &abort_flag, false)) {
-                if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteFull);
-                abort_flag = 1;
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t a_addr = smem_u32(smem + stage * STAGE_BYTES);
-              const uint32_t b_addr = a_addr + A_BYTES;
-              const uint32_t dt = tmem_base + buf * TN;
-#pragma unroll
-              for (int k = 0; k < BKS / 16; ++k) {
-                mma_bf16(dt, sdesc_k128(a_addr + k * 32), sdesc_k128(b_addr + k * 32), IDESC,
-                         (st % CH != 0 || k > 0) ? 1u : 0u);
-              }
-              // release the stage to every CTA that delivers into it
-              if (clustered)
-                mma_commit_mc(smem_u32(&empty[stage]), rel_mask);
-              else
-                mma_commit(smem_u32(&empty[stage]));
-              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-              if (st % CH == CH - 1 || st == nst - 1) {
-                mma_commit(smem_u32(&acc_full[buf]));
-                ++gc;
+                const uint32_t a_addr = smem_u32(smem + stage * STAGE_BYTES);
+                const uint32_t b_addr = a_addr + A_BYTES;
+                const uint32_t dt = tmem_base + buf * TN;
+  #pragma unroll
+                for (int k = 0; k < BKS / 16; ++k) {
+                  mma_bf16(dt, sdesc_k128(a_addr + k * 32), sdesc_k128(b_addr + k * 32), IDESC,
+                           (st % CH != 0 || k > 0) ? 1u : 0u);
+                }
+                // release the stage to every CTA that delivers into it
+                if (clustered)
+                  mma_commit_mc(smem_u32(&empty[stage]), rel_mask);
+                else
+                  mma_commit(smem_u32(&empty[stage]));
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                if (st % CH == CH - 1 || st == nst - 1) {
+                  mma_commit(smem_u32(&acc_full[buf]));
+                  ++gc;
+                }
               }
             }
           }
@@ -277,56 +302,62 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int h = (warp - 2) >> 2;          // column half
     uint32_t gc = 0;
     bool ok = true;
-    for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-      const int64_t row = row_lo + (int64_t)mi * TM + q * 32 + lane;
-      for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-        const int64_t n0 = col_lo + (int64_t)ni * TN + h * 128;
-        const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
-        for (int d = 2; d <= S + 1 && ok; ++d) {
-          const int nch = ((d - 1) * nkb + CH - 1) / CH;
-          for (int seg = 0; seg * p.seg_chunks < nch && ok; ++seg) {
-            const int c1 = min(nch, (seg + 1) * p.seg_chunks);
-            int acc[128];
-#pragma unroll
-            for (int i = 0; i < 128; ++i) acc[i] = 0;
-            for (int ch = seg * p.seg_chunks; ch < c1; ++ch) {
-              const uint32_t buf = gc & 1u;
-              // the whole warp decides together: tcgen05.ld below is warp-collective
-              const bool got =
-                  wait_or_abort(smem_u32(&acc_full[buf]), (gc >> 1) & 1u, &abort_flag, false);
-              if (!__all_sync(0xffffffffu, got)) {
-                ok = false;
-                break;
+    for (int L = cid; L < ntiles && ok; L += ncl) {
+      int r, c;
+      tile_proc(L, ncx, ncy, cm, cn, cy, cx, &r, &c);
+      const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
+      const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
+      for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
+        const int64_t row = row_lo + (int64_t)mi * TM + q * 32 + lane;
+        for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
+          const int64_t n0 = col_lo + (int64_t)ni * TN + h * 128;
+          const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
+          for (int d = 2; d <= S + 1 && ok; ++d) {
+            const int nch = ((d - 1) * nkb + CH - 1) / CH;
+            for (int seg = 0; seg * p.seg_chunks < nch && ok; ++seg) {
+              const int c1 = min(nch, (seg + 1) * p.seg_chunks);
+              int acc[128];
+  #pragma unroll
+              for (int i = 0; i < 128; ++i) acc[i] = 0;
+              for (int ch = seg * p.seg_chunks; ch < c1; ++ch) {
+                const uint32_t buf = gc & 1u;
+                // the whole warp decides together: tcgen05.ld below is warp-collective
+                const bool got =
+                    wait_or_abort(smem_u32(&acc_full[buf]), (gc >> 1) & 1u, &abort_flag, false);
+                if (!__all_sync(0xffffffffu, got)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + buf * TN + h * 128;
+  #pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  uint32_t v[16];
+                  tmem_ld16(ta + j * 16, v);
+                  tmem_ld_wait();
+  #pragma unroll
+                  for (int i = 0; i < 16; ++i)
+                    acc[j * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+                ++gc;
               }
-              tc_fence_after();
-              const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + buf * TN + h * 128;
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                uint32_t v[16];
-                tmem_ld16(ta + j * 16, v);
-                tmem_ld_wait();
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                  acc[j * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
-              }
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
-              ++gc;
-            }
-            if (!ok) break;
-            if (row < row_hi) {
-              int32_t *drow =
-                  p.D + ((int64_t)((d - 2) * p.nseg + seg) * p.M + row) * p.N + n0;
-              if (nvalid == 128 && (reinterpret_cast<uintptr_t>(drow) & 15) == 0) {
-#pragma unroll
-                for (int i = 0; i < 128; i += 4)
-                  *reinterpret_cast<int4 *>(drow + i) =
-                      make_int4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
-              } else {
-#pragma unroll
-                for (int i = 0; i < 128; ++i)
-                  if (i < nvalid) drow[i] = acc[i];
+              if (!ok) break;
+              if (row < row_hi) {
+                int32_t *drow =
+                    p.D + ((int64_t)((d - 2) * p.nseg + seg) * p.M + row) * p.N + n0;
+                if (nvalid == 128 && (reinterpret_cast<uintptr_t>(drow) & 15) == 0) {
+  #pragma unroll
+                  for (int i = 0; i < 128; i += 4)
+                    *reinterpret_cast<int4 *>(drow + i) =
+                        make_int4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+                } else {
+  #pragma unroll
+                  for (int i = 0; i < 128; ++i)
+                    if (i < nvalid) drow[i] = acc[i];
+                }
               }
             }
           }
@@ -417,8 +448,11 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
                              1);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   }
+  // persistent grid: as many clusters as can be resident at once, each
+  // looping over cluster tiles
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)g.Q, (unsigned)g.P, 1);
+  const int ntiles = (g.Q / g.cn) * (g.P / g.cm);
+  cfg.gridDim = dim3((unsigned)(ntiles * g.cn), (unsigned)g.cm, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = s;
@@ -429,6 +463,15 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  int active = 0;
+  e = cudaOccupancyMaxActiveClusters(&active, bf16_diag_kernel, &cfg);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveClusters");
+  if (active < 1) {
+    set_error("no cluster of %d x %d CTAs fits on the device", g.cm, g.cn);
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  const int ncl = ntiles < active ? ntiles : active;
+  cfg.gridDim = dim3((unsigned)(ncl * g.cn), (unsigned)g.cm, 1);
   e = cudaLaunchKernelEx(&cfg, bf16_diag_kernel, tA, tB, tApf, tBpf, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch bf16_diag_kernel");
   return HSUMMA_OK;
