@@ -29,6 +29,7 @@ struct DeviceState {
   size_t workspace_bytes = 0;
   void *host_staging = nullptr;              // device buffers of hsumma_gemm_host
   size_t host_staging_bytes = 0;
+  bool bf16_single_sm = false;               // HSUMMA_BF16_SINGLE_SM=1: no CTA pairs
 };
 
 DeviceState &state();
@@ -74,6 +75,8 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
                       cudaStream_t s);
 int launch_split_int8(const GridPlan &g, int S, const void *As, const void *Bs, int32_t *D,
                       cudaStream_t s);
+int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void *Bs,
+                           int32_t *D, cudaStream_t s);
 int bf16_cluster_limit(int *limit);
 int int8_cluster_limit(int *limit);
 int launch_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, const int32_t *D,

@@ -448,8 +448,9 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
                              1);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   }
-  // persistent grid: as many clusters as can be resident at once, each
-  // looping over cluster tiles
+  // one cluster per cluster tile (the kernel can also loop over tiles with a
+  // smaller grid, but clusters resident together drift apart along k and then
+  // share less in L2 than freshly launched ones)
   cudaLaunchConfig_t cfg = {};
   const int ntiles = (g.Q / g.cn) * (g.P / g.cm);
   cfg.gridDim = dim3((unsigned)(ntiles * g.cn), (unsigned)g.cm, 1);
@@ -463,15 +464,6 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  int active = 0;
-  e = cudaOccupancyMaxActiveClusters(&active, bf16_diag_kernel, &cfg);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveClusters");
-  if (active < 1) {
-    set_error("no cluster of %d x %d CTAs fits on the device", g.cm, g.cn);
-    return HSUMMA_ERR_UNSUPPORTED;
-  }
-  const int ncl = ntiles < active ? ntiles : active;
-  cfg.gridDim = dim3((unsigned)(ncl * g.cn), (unsigned)g.cm, 1);
   e = cudaLaunchKernelEx(&cfg, bf16_diag_kernel, tA, tB, tApf, tBpf, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch bf16_diag_kernel");
   return HSUMMA_OK;

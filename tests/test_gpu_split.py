@@ -240,3 +240,31 @@ def test_odd_leading_dimensions():
     C = hs.gemm(dA, dB, P=2, Q=2, G=4, b=64, Bouter=64, kind="bf16", slices=2)
     hs.sync()
     assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 2, "bf16"))
+
+
+@pytest.mark.parametrize("M,N,K,P,Q,G,S", [
+    (256, 256, 1024, 2, 1, 1, 3),       # one CTA pair
+    (512, 512, 512, 4, 2, 1, 2),        # 4 x 2 cluster: B halves multicast to 2 CTAs
+    (600, 300, 640, 6, 1, 1, 2),        # 6 x 1 cluster: 8-row pieces for the B halves
+    (520, 1100, 700, 4, 4, 4, 3),       # 2 x 2 groups, ragged blocks and sub-tiles
+])
+def test_bf16_pair_kernel_exact(M, N, K, P, Q, G, S):
+    # group clusters with an even number of rows run the CTA-pair kernel
+    hs = lib_ready()
+    torch = torch_cuda()
+    I, J, cm, cn = hs.group_shape(P, Q, G)
+    assert cm % 2 == 0
+    A, B, dA, dB = pair(M, N, K, 29, "wide", "uniform")
+    e, f = hs.split_exponents(dA, dB)
+    As, Bs = hs.split_slices(dA, dB, e, f, "bf16", S)
+    D = hs.split_diagonals(As, Bs, M, N, K, "bf16", S, P=P, Q=Q, G=G, b=64, Bouter=128)
+    hs.sync()
+    _, parts = split.split_gemm(A, B, S, "bf16", return_parts=True)
+    Dg = D.to(torch.int64).sum(dim=1).cpu().numpy()
+    for d in range(2, S + 2):
+        assert np.array_equal(Dg[d - 2], parts["D"][d]), d
+    npairs = S * (S + 1) // 2
+    want = gsched.counters_closed_form(M, N, K, P, Q, cm, cn, 128, 256, 128, npairs)
+    c = hs.counters()
+    for k, v in want.items():
+        assert c[k] == v, (k, c[k], v)
