@@ -217,7 +217,8 @@ typedef enum {
   HSUMMA_PEAK_IMMA = 2,      /* int8 mma.sync m16n8k32, int32 accumulate */
   HSUMMA_PEAK_HMMA_BF16 = 3, /* bf16 mma.sync m16n8k16, fp32 accumulate */
   HSUMMA_PEAK_TC05_BF16 = 4, /* bf16 tcgen05.mma 128x256x16, fp32 in TMEM */
-  HSUMMA_PEAK_COPY = 5       /* device memory copy (bytes read + written) */
+  HSUMMA_PEAK_COPY = 5,      /* device memory copy (bytes read + written) */
+  HSUMMA_PEAK_TC05_BF16_PAIR = 6 /* bf16 tcgen05.mma cta_group::2 256x256x16 */
 } hsumma_peak_kind;
 
 /* Run one microbenchmark on every SM and return the rate: flops/s (2 per

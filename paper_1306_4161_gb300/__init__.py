@@ -19,7 +19,8 @@ HEADER = os.path.join(ROOT, "include", "hsumma.h")
 
 FP64, INT8_SLICES, BF16_SLICES = 0, 1, 2
 KINDS = {"fp64": FP64, "int8": INT8_SLICES, "bf16": BF16_SLICES}
-PEAKS = {"dfma": 0, "dmma": 1, "imma": 2, "hmma_bf16": 3, "tc05_bf16": 4, "copy": 5}
+PEAKS = {"dfma": 0, "dmma": 1, "imma": 2, "hmma_bf16": 3, "tc05_bf16": 4, "copy": 5,
+         "tc05_bf16_pair": 6}
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSUPPORTED", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
           -5: "ERR_NOT_INIT", -6: "ERR_NONFINITE"}
 N_MLP_PARAMS = 9089

@@ -91,8 +91,10 @@ bool encode_tmap_3d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
 static int launch_split_diagonals(const GridPlan &g, int kind, int S, const void *As,
                                   const void *Bs, int32_t *D, cudaStream_t s) {
   if (kind == HSUMMA_BF16_SLICES) {
-    // CTA pairs (two-SM MMAs) when the group cluster has an even number of rows
-    if (g.cm % 2 == 0 && !g_state.bf16_single_sm) return launch_split_bf16_pair(g, S, As, Bs, D, s);
+    // CTA pairs (two-SM MMAs) only on request (HSUMMA_BF16_PAIR=1): on this GPU
+    // the per-SM MMA rate is set by the number of issuing threads, not by the
+    // pair form, and the single-SM kernel with two issuers is faster
+    if (g.cm % 2 == 0 && g_state.bf16_pair) return launch_split_bf16_pair(g, S, As, Bs, D, s);
     return launch_split_bf16(g, S, As, Bs, D, s);
   }
   return launch_split_int8(g, S, As, Bs, D, s);
@@ -220,8 +222,8 @@ int hsumma_init(int device) {
   if (st != HSUMMA_OK) return st;
   if (l2 < lim) lim = l2;
   g_state.cluster_limit = lim;
-  const char *single = getenv("HSUMMA_BF16_SINGLE_SM");
-  g_state.bf16_single_sm = single && single[0] == '1';
+  const char *pair = getenv("HSUMMA_BF16_PAIR");
+  g_state.bf16_pair = pair && pair[0] == '1';
   if (g_state.cluster_limit > 16) g_state.cluster_limit = 16;
   if (g_state.cluster_limit < 1) g_state.cluster_limit = 1;
   e = cudaDeviceSynchronize();

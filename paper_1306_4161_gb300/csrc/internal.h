@@ -29,7 +29,7 @@ struct DeviceState {
   size_t workspace_bytes = 0;
   void *host_staging = nullptr;              // device buffers of hsumma_gemm_host
   size_t host_staging_bytes = 0;
-  bool bf16_single_sm = false;               // HSUMMA_BF16_SINGLE_SM=1: no CTA pairs
+  bool bf16_pair = false;                    // HSUMMA_BF16_PAIR=1: CTA-pair bf16 kernel
 };
 
 DeviceState &state();

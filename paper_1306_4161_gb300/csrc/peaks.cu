@@ -149,6 +149,64 @@ __global__ void __launch_bounds__(128, 1) peak_tc05_kernel(int64_t iters, int *s
   }
 }
 
+// CTA pairs (clusters of 2, one CTA per SM): the first CTA of each pair issues
+// 256 x 256 x 16 bf16 MMAs spanning both SMs; the second waits for the
+// commits so that both stay resident until the last MMA completes.
+__global__ void __launch_bounds__(128, 1) peak_tc05_pair_kernel(int64_t iters, int *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 48 * 1024);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
+  const int warp = threadIdx.x >> 5;
+  const uint32_t rank = cluster_ctarank();
+  for (int i = threadIdx.x; i < 48 * 1024 / 16; i += blockDim.x)
+    reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(bar), 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc2(smem_u32(slot), 512);
+    tmem_relinquish2();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *slot;
+  cluster_sync();
+  if (threadIdx.x == 0) {
+    const uint32_t a = smem_u32(smem), b = a + 16 * 1024;
+    const uint32_t idesc = idesc_bf16_f32(256, 256);
+    uint32_t phase = 0;
+    for (int64_t it = 0; it < iters; ++it) {
+      const bool commit = (it & 255) == 255 || it == iters - 1;
+      if ((rank & 1) == 0) {
+        const uint32_t k = (uint32_t)(it & 3);
+        mma2_bf16(tbase + (uint32_t)((it >> 2) & 1) * 256, sdesc_k128(a + k * 32),
+                  sdesc_k128(b + k * 32), idesc, k ? 1u : 0u);
+        if (commit) mma2_commit_mc(smem_u32(bar), (uint16_t)3u);
+      }
+      if (commit) {
+        if (!mbar_wait(smem_u32(bar), phase)) {
+          record_error(status, HSUMMA_ERR_TIMEOUT, kSiteAccFull);
+          break;
+        }
+        phase ^= 1u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc2(tbase, 512);
+  }
+  cluster_sync();
+}
+
 __global__ void copy_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -190,6 +248,22 @@ int run_peak(int kind, int64_t work, double *rate) {
         peak_tc05_kernel<<<sms, 128, TC_SMEM>>>(iters, state().d_status);
         work_units = 2.0 * 128 * 256 * 16 * (double)iters * sms;
         break;
+      case HSUMMA_PEAK_TC05_BF16_PAIR: {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(sms & ~1), 1, 1);
+        cfg.blockDim = dim3(128, 1, 1);
+        cfg.dynamicSmemBytes = TC_SMEM;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, peak_tc05_pair_kernel, iters, state().d_status);
+        work_units = 2.0 * 256 * 256 * 16 * (double)iters * (sms / 2);
+        break;
+      }
       case HSUMMA_PEAK_COPY:
         copy_kernel<<<sms * 16, 512>>>((const uint4 *)buf, (uint4 *)buf + n16, n16);
         work_units = 2.0 * 16 * n16;
@@ -197,12 +271,17 @@ int run_peak(int kind, int64_t work, double *rate) {
     }
   };
   int st = HSUMMA_OK;
-  if (kind < HSUMMA_PEAK_DFMA || kind > HSUMMA_PEAK_COPY) {
+  if (kind < HSUMMA_PEAK_DFMA || kind > HSUMMA_PEAK_TC05_BF16_PAIR) {
     set_error("unknown peak kind %d", kind);
     st = HSUMMA_ERR_ARG;
   }
   if (st == HSUMMA_OK && kind == HSUMMA_PEAK_TC05_BF16) {
     e = cudaFuncSetAttribute(peak_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_SMEM);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  if (st == HSUMMA_OK && kind == HSUMMA_PEAK_TC05_BF16_PAIR) {
+    e = cudaFuncSetAttribute(peak_tc05_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TC_SMEM);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaFuncSetAttribute");
   }

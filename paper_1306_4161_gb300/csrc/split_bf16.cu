@@ -11,18 +11,26 @@
 //
 // Exactness: a product of two digits is an integer of magnitude <= 2^14, so an
 // fp32 accumulator that sums at most 1024 of them per element stays an integer
-// of magnitude <= 2^24 and is exact.  The accumulator is therefore drained every
-// 16 k-stages of 64 ("chunk", 1024 products, pairs of the same diagonal
-// concatenated along k) into int32 registers.  A diagonal is cut into segments
-// of at most 127 chunks (sums <= 127 * 2^24 < 2^31); each segment's exact int32
-// sums are stored as one plane of the output, D[d-2][seg][i][j], and the
+// of magnitude <= 2^24 and is exact.  Accumulators are therefore drained into
+// int32 registers after at most 16 k-stages of 64 ("chunk", 1024 products);
+// pairs of the same diagonal are concatenated along k.  A diagonal is cut into
+// segments of 127 * 16 stages (sums <= 127 * 2^24 < 2^31); each segment's exact
+// int32 sums are stored as one plane of the output, D[d-2][seg][i][j], and the
 // recombination adds the planes of a diagonal exactly.
 //
-// Roles (320 threads): warp 0 issues the copies, warp 1 owns tensor memory and
-// issues the MMAs, warps 2..9 drain the accumulators (two warps per 32-lane
-// quarter of tensor memory, 128 columns each; 128 int32 sums per thread).  Shared memory: 4 stages of
-// 16 KB (A, 128 x 64) + 32 KB (B, 256 x 64).  Tensor memory: two 128 x 256 fp32
-// accumulators (512 columns), one filled while the other drains.
+// Two MMA issuers.  On this GPU one issuing thread sustains about one MMA per
+// 135 ns whatever its shape, half of what the SM's tensor core can execute;
+// two threads issuing into separate accumulators reach the full rate.  Issuer
+// i (warp 1 + i) takes the k-stages of parity i and owns the accumulator in
+// tensor-memory columns [256 i, 256 i + 256); the issuers' chunk boundaries are
+// staggered by half a chunk, so one accumulator is being filled while the
+// other is drained.  Chunk ends, in stage order, are the drain events.
+//
+// Roles (384 threads): warp 0 issues the copies, warps 1 and 2 issue the MMAs
+// (warp 1 also owns tensor memory), warp 3 idles, warps 4..11 drain (two per
+// 32-lane quarter of tensor memory, 128 columns each; 128 int32 sums per
+// thread).  Shared memory: 4 stages of 16 KB (A, 128 x 64) + 32 KB (B,
+// 256 x 64).
 #include "internal.h"
 #include "ptx.cuh"
 #include "tc05.cuh"
@@ -36,7 +44,8 @@ constexpr int A_BYTES = TM * BKS * 2, B_BYTES = TN * BKS * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int CH = 16;                 // k-stages per accumulator chunk
 constexpr int NEPI = 8;                // draining warps
-constexpr int NTHREADS = (2 + NEPI) * 32;
+constexpr int NTHREADS = (4 + NEPI) * 32;
+constexpr int SEGST = 127 * CH;        // stages per int32 segment
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC = idesc_bf16_f32(TM, TN);
@@ -64,6 +73,16 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
     if (*abort_flag) return false;
     if (globaltimer() - t0 > kWaitLimitNs) return false;
   }
+}
+
+// Does stage `local` (counted from the start of its segment of `seg_len`
+// stages) end a chunk of the issuer that owns it (issuer = local & 1)?  Issuer
+// 0 closes a chunk every 16 of its stages, issuer 1 after 8 and then every 16;
+// both close one at their last stage of the segment.
+__device__ __forceinline__ bool chunk_end(int local, int seg_len) {
+  const int c = (local >> 1) + 1;
+  if (local + 2 >= seg_len) return true;
+  return (local & 1) ? ((c + 8) % CH == 0) : (c % CH == 0);
 }
 
 // cluster tile L -> processor row r and column c of this CTA: tiles are
@@ -237,26 +256,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       atomicAdd(&p.counters[4], pf);
       atomicAdd(&p.counters[5], nops);
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issue ----------------
+  } else if (warp == 1 || warp == 2) {
+    // ---------------- MMA issue: issuer `me` takes the stages of parity me ----------------
     if (lane == 0) {
-      uint32_t stage = 0, phase = 0;
-      uint32_t gc = 0;  // global chunk counter: buffer gc & 1, phase (gc >> 1) & 1
+      const int me = warp - 1;
+      uint32_t gst = 0;   // stage counter over the whole launch: ring slot and phase
+      uint32_t nchunk = 0;
+      bool in_chunk = false;
       const uint16_t rel_mask = row_mask | col_mask;
+      const uint32_t dt = tmem_base + (uint32_t)(me * TN);
       bool ok = true;
       for (int L = cid; L < ntiles && ok; L += ncl) {
-        int r, c;
-        tile_proc(L, ncx, ncy, cm, cn, cy, cx, &r, &c);
-        const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
-        const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
         for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
           for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
             for (int d = 2; d <= S + 1 && ok; ++d) {
               const int nst = (d - 1) * nkb;
-              for (int st = 0; st < nst; ++st) {
-                const uint32_t buf = gc & 1u;
-                if (st % CH == 0) {
-                  if (!wait_or_abort(smem_u32(&acc_empty[buf]), ((gc >> 1) & 1u) ^ 1u, &abort_flag,
+              for (int st = 0; st < nst; ++st, ++gst) {
+                if ((st & 1) != me) continue;
+                const int seg_lo = st - st % SEGST;
+                const int seg_len = min(nst, seg_lo + SEGST) - seg_lo;
+                const int local = st - seg_lo;
+                bool first = false;
+                if (!in_chunk) {
+                  if (!wait_or_abort(smem_u32(&acc_empty[me]), (nchunk & 1u) ^ 1u, &abort_flag,
                                      false)) {
                     if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteAccEmpty);
                     abort_flag = 1;
@@ -264,7 +286,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                   }
                   tc_fence_after();
+                  in_chunk = true;
+                  first = true;
                 }
+                const uint32_t stage = gst % STAGES, phase = (gst / STAGES) & 1u;
                 if (!wait_or_abort(smem_u32(&full[stage]), phase, &abort_flag, false)) {
                   if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteFull);
                   abort_flag = 1;
@@ -274,21 +299,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_after();
                 const uint32_t a_addr = smem_u32(smem + stage * STAGE_BYTES);
                 const uint32_t b_addr = a_addr + A_BYTES;
-                const uint32_t dt = tmem_base + buf * TN;
-  #pragma unroll
+#pragma unroll
                 for (int k = 0; k < BKS / 16; ++k) {
                   mma_bf16(dt, sdesc_k128(a_addr + k * 32), sdesc_k128(b_addr + k * 32), IDESC,
-                           (st % CH != 0 || k > 0) ? 1u : 0u);
+                           (first && k == 0) ? 0u : 1u);
                 }
                 // release the stage to every CTA that delivers into it
                 if (clustered)
                   mma_commit_mc(smem_u32(&empty[stage]), rel_mask);
                 else
                   mma_commit(smem_u32(&empty[stage]));
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-                if (st % CH == CH - 1 || st == nst - 1) {
-                  mma_commit(smem_u32(&acc_full[buf]));
-                  ++gc;
+                if (chunk_end(local, seg_len)) {
+                  mma_commit(smem_u32(&acc_full[me]));
+                  ++nchunk;
+                  in_chunk = false;
                 }
               }
             }
@@ -296,11 +320,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-  } else {
-    // ---------------- drain: tensor memory -> exact int32 planes ----------------
+  } else if (warp >= 4) {
+    // ---------------- drain: chunk ends in stage order -> exact int32 planes ----------------
     const int q = warp & 3;                 // tensor-memory lane quarter of this warp
-    const int h = (warp - 2) >> 2;          // column half
-    uint32_t gc = 0;
+    const int h = (warp - 4) >> 2;          // column half
+    uint32_t nchunk0 = 0, nchunk1 = 0;
     bool ok = true;
     for (int L = cid; L < ntiles && ok; L += ncl) {
       int r, c;
@@ -313,48 +337,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t n0 = col_lo + (int64_t)ni * TN + h * 128;
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
           for (int d = 2; d <= S + 1 && ok; ++d) {
-            const int nch = ((d - 1) * nkb + CH - 1) / CH;
-            for (int seg = 0; seg * p.seg_chunks < nch && ok; ++seg) {
-              const int c1 = min(nch, (seg + 1) * p.seg_chunks);
+            const int nst = (d - 1) * nkb;
+            for (int seg = 0; seg * SEGST < nst && ok; ++seg) {
+              const int seg_len = min(nst, (seg + 1) * SEGST) - seg * SEGST;
               int acc[128];
-  #pragma unroll
+#pragma unroll
               for (int i = 0; i < 128; ++i) acc[i] = 0;
-              for (int ch = seg * p.seg_chunks; ch < c1; ++ch) {
-                const uint32_t buf = gc & 1u;
+              for (int local = 0; local < seg_len; ++local) {
+                if (!chunk_end(local, seg_len)) continue;
+                const int who = local & 1;
+                const uint32_t par = who ? (nchunk1 & 1u) : (nchunk0 & 1u);
                 // the whole warp decides together: tcgen05.ld below is warp-collective
-                const bool got =
-                    wait_or_abort(smem_u32(&acc_full[buf]), (gc >> 1) & 1u, &abort_flag, false);
+                const bool got = wait_or_abort(smem_u32(&acc_full[who]), par, &abort_flag, false);
                 if (!__all_sync(0xffffffffu, got)) {
                   ok = false;
                   break;
                 }
                 tc_fence_after();
-                const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + buf * TN + h * 128;
-  #pragma unroll
+                const uint32_t ta =
+                    tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(who * TN) + h * 128;
+#pragma unroll
                 for (int j = 0; j < 8; ++j) {
                   uint32_t v[16];
                   tmem_ld16(ta + j * 16, v);
                   tmem_ld_wait();
-  #pragma unroll
+#pragma unroll
                   for (int i = 0; i < 16; ++i)
                     acc[j * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
-                ++gc;
+                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[who]));
+                if (who) ++nchunk1; else ++nchunk0;
               }
               if (!ok) break;
               if (row < row_hi) {
                 int32_t *drow =
                     p.D + ((int64_t)((d - 2) * p.nseg + seg) * p.M + row) * p.N + n0;
                 if (nvalid == 128 && (reinterpret_cast<uintptr_t>(drow) & 15) == 0) {
-  #pragma unroll
+#pragma unroll
                   for (int i = 0; i < 128; i += 4)
                     *reinterpret_cast<int4 *>(drow + i) =
                         make_int4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
                 } else {
-  #pragma unroll
+#pragma unroll
                   for (int i = 0; i < 128; ++i)
                     if (i < nvalid) drow[i] = acc[i];
                 }
