@@ -29,12 +29,12 @@ sys.path.insert(0, ROOT)
 
 N_SIZE = 16384
 METRIC = "FP64-accurate TFLOP/s at n=16384, split-precision vs native FP64, % of roofline"
-SPLIT = dict(P=128, Q=64, G=2048, b=64, Bouter=256, kind="bf16", slices=5)
+SPLIT = dict(P=128, Q=64, G=256, b=64, Bouter=1024, kind="bf16", slices=5)
 NATIVE = dict(P=128, Q=128, G=4096, b=32, Bouter=128)
 WORKLOAD = ("split_vs_fp64_16384: M=N=K=16384, A,B uniform[-1,1] (SplitMix64 seeds 1002/2002), "
             "bf16 slices S=5 (15 pair products), virtual grid 128x64 of 128x256 blocks, "
-            "G=2048 groups of 2x2 (cluster multicast), b=64, B=256; native fp64 beside it on a "
-            "128x128 grid, G=4096, b=32, B=128")
+            "G=256 groups of 8x4 (inner level served from L2), b=64, B=1024 (owner L2 prefetch); "
+            "native fp64 beside it on a 128x128 grid, G=4096, b=32, B=128")
 
 
 def configure(n):
@@ -44,7 +44,7 @@ def configure(n):
     if n % 256:
         raise SystemExit("--size must be a multiple of 256")
     N_SIZE = n
-    SPLIT = dict(SPLIT, P=n // 128, Q=n // 256, G=(n // 128) * (n // 256) // 4)
+    SPLIT = dict(SPLIT, P=n // 128, Q=n // 256, G=max(1, (n // 128) * (n // 256) // 32))
     NATIVE = dict(NATIVE, P=n // 128, Q=n // 128, G=(n // 128) ** 2 // 4)
     if n != 16384:
         WORKLOAD = WORKLOAD.replace("16384", str(n))
@@ -53,6 +53,20 @@ def configure(n):
 def flops(n=None):
     n = N_SIZE if n is None else n
     return 2.0 * n ** 3
+
+
+def measured_traffic(kernel="bf16_diag_kernel"):
+    """DRAM bytes per launch from the committed ncu record, only while the
+    kernel's source is the one the counters were taken on (else None)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["sha256_prefix"]:
+            return None
+        return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    except Exception:
+        return None
 
 
 def read_peaks():
@@ -272,7 +286,8 @@ def main():
                 "frac": gemm_tflops / bf16_peak,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)",
                 "algorithmic": f"{npairs} bf16 products x 2 n^3 per launch",
-                "traffic": None}
+                "traffic": measured_traffic() if N_SIZE == 16384 and SPLIT["G"] == 256 else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write)"}
     breakdown_ms = {"exponent_scan": dur[0], "slicing": dur[1], "diagonal_products": dur[2],
                     "recombination": dur[3]}
 

@@ -178,18 +178,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int kb = 0; kb < nkb; ++kb) {
                   const int64_t k0 = (int64_t)kb * BKS;
                   if (k0 % p.Bo == 0) {
-                    // outer step: owners stage outer panel o (at the start) and o + 1
+                    // outer step o of pair (s, t): the owners stage the next outer
+                    // panel into L2 -- panel o + 1 of this pair, or, at the last
+                    // outer step, panel 0 of the next pair of the sub-tile -- so the
+                    // prefetch runs one outer block ahead without gaps; the sub-tile's
+                    // very first panel is staged at its own start
                     const int64_t o = k0 / p.Bo;
-                    for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
+                    int ns = s + 1, nd = d;            // next pair in the sweep order
+                    if (ns >= nd) { ++nd; ns = 1; }
+                    const bool first = (d == 2 && s == 1 && o == 0);
+                    for (int w = first ? 0 : 1; w <= 1; ++w) {
+                      int64_t q = o + w;
+                      int ps = s, pt = t;
+                      if (q >= nout) {
+                        if (nd > S + 1) break;
+                        q = 0;
+                        ps = ns;
+                        pt = nd - ns;
+                      }
                       const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
                       if (c == (int)imin64(p.Q - 1, kq / p.Kq)) {
                         for (int64_t kk = kq; kk < kend; kk += BKS)
-                          tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, s - 1);
+                          tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, ps - 1);
                         pf += 1;
                       }
                       if (r == (int)imin64(p.P - 1, kq / p.Kp)) {
                         for (int64_t kk = kq; kk < kend; kk += BKS)
-                          tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, t - 1);
+                          tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, pt - 1);
                         pf += 1;
                       }
                     }
