@@ -193,6 +193,31 @@ int hsumma_mlp_backward(int batch, const float *d_theta, const float *d_X,
                         const float *d_target, float *d_grad, float *d_loss,
                         void *stream);
 
+/* hsumma_mlp_backward without allocation.  The paper has no counterpart: this
+ * is a library facility for callers that must not allocate device memory once
+ * they are running, such as a serving process that refines its cost model
+ * between requests while its memory is fully planned (or held by a caching
+ * allocator), or one that cannot take the device-wide synchronisation that
+ * cudaMalloc and cudaFree bring while other streams are busy.
+ * hsumma_mlp_backward grows a buffer of per-block partial gradients with
+ * cudaMalloc; this variant keeps them in one fixed array in the library's
+ * device image (about 18.6 MB, held by every device that loads the library
+ * until the process exits) and calls no cudaMalloc, cudaFree or allocating
+ * routine.  Arguments, layout and results are those of hsumma_mlp_backward;
+ * the caller passes every input and output.
+ *   batch: 1..HSUMMA_MLP_NOALLOC_MAX_BATCH; a larger batch returns
+ *          HSUMMA_ERR_ARG (message in hsumma_last_error) and launches nothing.
+ * The first call on each device (with that device current) looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (nothing in it needs clearing, every slot read is written first in
+ * the same call): calls that overlap on the GPU, on different streams or from
+ * different host threads, race and give wrong gradients. */
+#define HSUMMA_MLP_NOALLOC_MAX_BATCH 4096
+int hsumma_mlp_backward_noalloc(int batch, const float *d_theta, const float *d_X,
+                                const float *d_target, float *d_grad, float *d_loss,
+                                void *stream);
+
 /* One Adam step (fp32), step number t >= 1, on n parameters. */
 int hsumma_mlp_adam(int n, float *d_theta, const float *d_grad, float *d_m,
                     float *d_v, int t, float lr, float beta1, float beta2,

@@ -67,6 +67,7 @@ _SIGS = {
                                _i32),
     "hsumma_mlp_forward": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hsumma_mlp_backward": ([_i32, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "hsumma_mlp_backward_noalloc": ([_i32, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "hsumma_mlp_adam": ([_i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float,
                          ctypes.c_float, ctypes.c_float, _vp], _i32),
     "hsumma_mlp_pick": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),

@@ -12,6 +12,7 @@
 // block order by a second kernel.
 #include <cuda_bf16.h>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 #include "../../include/hsumma.h"
@@ -325,6 +326,20 @@ int mlp_pick_device(int n, const float *d_theta, const float *d_X, float *d_pred
   return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "launch mlp pick");
 }
 
+// Scratch of hsumma_mlp_backward_noalloc: the per-block gradient partials
+// (kNoAllocBlocks x NPARAM floats) followed by the per-block loss partials
+// (kNoAllocBlocks floats), 18.6 MB in all.  It lives in the library's own
+// device image, so every device that loads the library holds it until the
+// process exits; nothing is allocated when the entry point runs.
+constexpr int kNoAllocBlocks = (HSUMMA_MLP_NOALLOC_MAX_BATCH + WARPS - 1) / WARPS;
+constexpr int kNoAllocDevices = 64;
+static __device__ __align__(256) float g_noalloc_scratch[(size_t)kNoAllocBlocks * (NPARAM + 1)];
+
+// Device address of g_noalloc_scratch on each device (host-side, filled on the
+// first call made with that device current).
+static std::mutex g_noalloc_mutex;
+static float *g_noalloc_addr[kNoAllocDevices] = {};
+
 }  // namespace hs
 
 using namespace hs;
@@ -377,6 +392,53 @@ int hsumma_mlp_backward(int batch, const float *theta, const float *X, const flo
   mlp_reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(nb, batch, partial, ploss, grad, loss);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "launch mlp backward");
+}
+
+// Same gradient and loss as hsumma_mlp_backward, with the block partials kept
+// in the fixed scratch above instead of a buffer grown with cudaMalloc.  Every
+// slot the reduction reads (blocks 0..nb-1) is written by the backward kernel
+// earlier in the same call, so nothing has to be cleared between calls.
+int hsumma_mlp_backward_noalloc(int batch, const float *theta, const float *X,
+                                const float *target, float *grad, float *loss, void *stream) {
+  if (batch <= 0 || !theta || !X || !target || !grad) {
+    set_error("bad MLP arguments");
+    return HSUMMA_ERR_ARG;
+  }
+  if (batch > HSUMMA_MLP_NOALLOC_MAX_BATCH) {
+    set_error("hsumma_mlp_backward_noalloc: batch %d exceeds its fixed scratch of "
+              "HSUMMA_MLP_NOALLOC_MAX_BATCH = %d samples",
+              batch, HSUMMA_MLP_NOALLOC_MAX_BATCH);
+    return HSUMMA_ERR_ARG;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocDevices) {
+    set_error("hsumma_mlp_backward_noalloc: device ordinal beyond 63");
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  float *partial = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void *addr = nullptr;
+      e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(mlp scratch)");
+      g_noalloc_addr[dev] = static_cast<float *>(addr);
+    }
+    partial = g_noalloc_addr[dev];
+  }
+  const int nb = grid_for(batch);  // <= ceil(batch / WARPS) <= kNoAllocBlocks
+  float *ploss = partial + (size_t)kNoAllocBlocks * NPARAM;
+  const int smem = 2 * NPARAM * (int)sizeof(float);
+  e = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mlp backward)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  mlp_backward_kernel<<<nb, WARPS * 32, smem, s>>>(batch, theta, X, target, partial, ploss);
+  mlp_reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(nb, batch, partial, ploss, grad, loss);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "launch mlp backward (no-alloc)");
 }
 
 int hsumma_mlp_adam(int n, float *theta, const float *grad, float *m, float *v, int t, float lr,
