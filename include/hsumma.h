@@ -1,9 +1,9 @@
 /*
  * hsumma.h -- C ABI of the single-GPU (sm_103a) Hierarchical SUMMA library.
  *
- * The library computes C = A x B (Section II-A: "C = A x B over a
- * two-dimensional p = s x t processor grid"; Section III, Algorithm 1) on one
- * GPU.  The paper's virtual processor grid becomes a grid of P x Q thread
+ * The library computes C = A x B (Section II-A: the product on a
+ * two-dimensional grid of p = s x t processors; Section III, Algorithm 1) on
+ * one GPU.  The paper's virtual processor grid becomes a grid of P x Q thread
  * blocks, one per virtual processor; its two broadcast levels become
  *   - the outer, between-group level (Section III, Figure 3): B-wide panels of
  *     A and B staged from HBM into L2 by the owner of each outer block, and
@@ -101,17 +101,16 @@ int hsumma_workspace_size(int64_t M, int64_t N, int64_t K, int mode,
                           size_t *bytes);
 
 /* C = A x B by HSUMMA on a virtual P x Q grid (Algorithm 1): G groups, inner
- * block b, outer block Bouter (b <= Bouter, b | Bouter; Section III: "the
- * block size inside a group should be less than or equal to the block size
- * between groups").  Blocks are ceil(M/P) x ceil(N/Q) and the last ones may
+ * block b, outer block Bouter (b <= Bouter, b | Bouter; Section III requires
+ * the in-group block to be no wider than the between-group one).  Blocks are ceil(M/P) x ceil(N/Q) and the last ones may
  * be short (the paper assumes divisibility; short blocks are allowed here);
  * 1 <= P, Q <= 65535; G must factor as above; b a multiple of 16 in 16..256
  * for FP64 and of 64 in 64..256 for the split kinds; Bouter a multiple of b.
  * P = Q = G = b = Bouter = 0 asks the library to choose them
  * (the learned cost model if one is loaded, else exhaustive timing of the
  * candidate set).  C is overwritten (beta = 0).  M, N or K = 0 is allowed
- * (K = 0 writes zeros).  The split kinds (Ozaki-style) need
- * finite inputs and K small enough for exact integer sums. */
+ * (K = 0 writes zeros).  The split kinds (Ozaki-style error-free slicing)
+ * need finite inputs and K small enough for exact integer sums. */
 int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *d_A, int64_t lda,
                 const double *d_B, int64_t ldb, double *d_C, int64_t ldc, int P,
                 int Q, int G, int b, int Bouter, int mode, void *stream);
@@ -230,9 +229,53 @@ int hsumma_mlp_pick(int n, const float *d_theta, const float *d_X,
 
 /* Load a trained model into the library (host arrays: 9089 parameters, the
  * 10 feature means and 10 standard deviations) for hsumma_gemm's automatic
- * choice; NULL theta unloads it. */
+ * choice; NULL theta unloads it.  Either way every cached choice is dropped. */
 int hsumma_mlp_load(const float *h_theta, const float *h_mean,
                     const float *h_std);
+
+/* ---- Automatic configuration ----
+ * The paper picks the group count by timing a few runs (Section V-A-1,
+ * Section VI) and fixes b and B by hand.  Here the candidates for a product
+ * are enumerated by the library, scored by the loaded cost model, or timed one
+ * by one (exhaustive search: the fallback, and the judge of the model). */
+
+/* Candidate configurations for a product: *count = their number (at most 72);
+ * the first min(count, max) are written to cfg as (P, Q, G, b, Bouter)
+ * quintuples.  Blocks of 1 or 2 kernel sub-tiles per direction; group counts
+ * 1, p/16, p/8, p/4, p/2 and p (p = PQ), one per distinct realised cluster
+ * shape; b = the kernel's stage width (32 FP64, 128 INT8, 64 BF16), which does
+ * not change the schedule on this GPU; Bouter in {b, 4b, 16b}.  Host only. */
+int hsumma_candidates(int64_t M, int64_t N, int64_t K, int mode, int *h_cfg,
+                      int max, int *h_count);
+
+/* The cost model's 10 input features of n configurations (h_cfg: n
+ * quintuples as above), written to h_X (n x 10 floats, row-major):
+ * log2 of M, N, K, P, Q, G, b, Bouter; the mode kind (0, 1, 2); S (0 for
+ * FP64).  The model sees them standardised with the loaded means and
+ * deviations.  Host only. */
+int hsumma_features(int64_t M, int64_t N, int64_t K, int mode,
+                    const int *h_cfg, int n, float *h_X);
+
+/* Choice policies and how a choice was made. */
+enum {
+  HSUMMA_CHOOSE_AUTO = 0,   /* cached, else the model, else timing */
+  HSUMMA_CHOOSE_MODEL = 1,  /* the loaded model (HSUMMA_ERR_UNSUPPORTED if none) */
+  HSUMMA_CHOOSE_TIMED = 2   /* exhaustive timing, always */
+};
+enum { HSUMMA_CHOSEN_CACHED = 0, HSUMMA_CHOSEN_MODEL = 1, HSUMMA_CHOSEN_TIMED = 2 };
+
+/* The configuration hsumma_gemm runs with when P = Q = G = b = Bouter = 0:
+ * written to h_cfg[5] with *h_how one of HSUMMA_CHOSEN_*.  The model scores
+ * every candidate on the device (bf16) and takes the smallest predicted time;
+ * timing runs every candidate once on these operands, after one untimed run,
+ * overwriting C, and takes the fastest that launched.  Either way the stream
+ * is synchronised and the choice is cached per (M, N, K, mode) until the next
+ * hsumma_mlp_load or hsumma_finalize.  Operands follow hsumma_gemm's rules
+ * (they are only read by timing). */
+int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *d_A,
+                  int64_t lda, const double *d_B, int64_t ldb, double *d_C,
+                  int64_t ldc, int mode, int policy, int *h_cfg, int *h_how,
+                  void *stream);
 
 /* ---- Peak microbenchmarks (roofline denominators) ---- */
 

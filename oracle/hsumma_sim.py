@@ -27,7 +27,7 @@ holder of the outer A block sends its b-wide slice along the in-group row
 (row_comm), the holder of the outer B block along the in-group column (col_comm);
 then the local update.
 
-Readings of garbled indices (listed in the design doc): the outer A broadcast runs
+Readings of garbled indices: the outer A broadcast runs
 over the J group columns (the text's range 1..I is read as 1..J) and the inner
 one over the Q/J in-group columns; B swaps the roles; Algorithm 1's tests on
 i/x for the A pivot are read as tests on j/y (the A pivot is a column index).

@@ -8,8 +8,8 @@ Rump ("Error-free transformations of matrix multiplication by using fast
 routines of matrix multiplication and its applications", Numer. Algorithms
 59, 2012), with integer-valued slices as in Ootomo, Ozaki and Yokota ("DGEMM on
 integer matrix multiplication unit", IJHPCA 2024).  The steps below are written
-from those definitions; the readings where they leave a choice are listed in
-DESIGN.md ("Readings").
+from those definitions; where they leave a choice, the reading taken is stated
+at the step.
 
 Steps, for slice width w bits and S slices:
   1. scaling: e_i = ilogb(max_k |A_ik|) + 2 (0 for an all-zero row), so that

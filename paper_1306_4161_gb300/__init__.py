@@ -72,6 +72,11 @@ _SIGS = {
                          ctypes.c_float, ctypes.c_float, _vp], _i32),
     "hsumma_mlp_pick": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hsumma_mlp_load": ([_vp, _vp, _vp], _i32),
+    "hsumma_candidates": ([_i64, _i64, _i64, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_int)],
+                          _i32),
+    "hsumma_features": ([_i64, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
+    "hsumma_choose": ([_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _i32, _vp,
+                       ctypes.POINTER(ctypes.c_int), _vp], _i32),
     "hsumma_peak": ([_i32, _i64, ctypes.POINTER(ctypes.c_double)], _i32),
 }
 
@@ -169,9 +174,11 @@ def _check_f64(t, name):
         raise ValueError(f"{name} must be 2-D with unit column stride")
 
 
-def gemm(A, B, *, P, Q, G, b, Bouter, kind="fp64", slices=0, out=None, stream=_DEFAULT):
+def gemm(A, B, *, P=0, Q=0, G=0, b=0, Bouter=0, kind="fp64", slices=0, out=None,
+         stream=_DEFAULT):
     """C = A x B by HSUMMA on a virtual P x Q grid with G groups (torch tensors on
-    the GPU, float64, row-major)."""
+    the GPU, float64, row-major).  P = Q = G = b = Bouter = 0 (the default) lets
+    the library choose them (see choose())."""
     import torch
     _check_f64(A, "A")
     _check_f64(B, "B")
@@ -280,3 +287,64 @@ def peak(kind: str, work: int) -> float:
     r = ctypes.c_double()
     _check(lib().hsumma_peak(PEAKS[kind], work, ctypes.byref(r)))
     return r.value
+
+
+# ---- automatic configuration ----
+CHOOSE = {"auto": 0, "model": 1, "timed": 2}
+CHOSEN = {0: "cached", 1: "model", 2: "timed"}
+
+
+def candidates(M, N, K, kind="fp64", slices=0) -> list[tuple[int, int, int, int, int]]:
+    """The (P, Q, G, b, Bouter) configurations the automatic choice considers."""
+    n = ctypes.c_int()
+    _check(lib().hsumma_candidates(M, N, K, mode_code(kind, slices), None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_int * (5 * max(n.value, 1)))()
+    _check(lib().hsumma_candidates(M, N, K, mode_code(kind, slices), buf, n.value,
+                                   ctypes.byref(n)))
+    return [tuple(buf[5 * i:5 * i + 5]) for i in range(n.value)]
+
+
+def features(M, N, K, cfgs, kind="fp64", slices=0):
+    """The cost model's raw input features (n x 10 float32) of configurations."""
+    import numpy as np
+    cfg = np.ascontiguousarray(np.asarray(cfgs, dtype=np.int32).reshape(-1, 5))
+    X = np.empty((cfg.shape[0], 10), dtype=np.float32)
+    _check(lib().hsumma_features(M, N, K, mode_code(kind, slices), cfg.ctypes.data,
+                                 cfg.shape[0], X.ctypes.data))
+    return X
+
+
+def choose(A, B, C=None, *, kind="fp64", slices=0, policy="auto", stream=_DEFAULT):
+    """(P, Q, G, b, Bouter) that gemm(A, B) runs with when asked to choose, and
+    how it was chosen ("cached", "model" or "timed").  Timing overwrites C."""
+    import torch
+    _check_f64(A, "A")
+    _check_f64(B, "B")
+    M, K = A.shape
+    N = B.shape[1]
+    _ensure_init(A)
+    if C is None:
+        C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    cfg = (ctypes.c_int * 5)()
+    how = ctypes.c_int()
+    _check(lib().hsumma_choose(M, N, K, A.data_ptr(), A.stride(0) if (M and K) else max(K, 1),
+                               B.data_ptr(), B.stride(0) if (K and N) else max(N, 1),
+                               C.data_ptr(), C.stride(0) if (M and N) else max(N, 1),
+                               mode_code(kind, slices), CHOOSE[policy], cfg, ctypes.byref(how),
+                               _stream_ptr(stream)))
+    return tuple(cfg), CHOSEN[how.value]
+
+
+def load_model(theta, mean, std):
+    """Load a trained cost model (9089 parameters, 10 feature means and
+    deviations) into the library; theta=None unloads it."""
+    import numpy as np
+    if theta is None:
+        _check(lib().hsumma_mlp_load(None, None, None))
+        return
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    mu = np.ascontiguousarray(mean, dtype=np.float32)
+    sd = np.ascontiguousarray(std, dtype=np.float32)
+    if th.size != N_MLP_PARAMS or mu.size != 10 or sd.size != 10:
+        raise ValueError("a cost model has 9089 parameters and 10 means and deviations")
+    _check(lib().hsumma_mlp_load(th.ctypes.data, mu.ctypes.data, sd.ctypes.data))

@@ -1,0 +1,392 @@
+"""Autotuner and learned cost model of the automatic configuration.
+
+The paper picks the number of groups by timing a few runs (Section V-A-1,
+Section VI) and otherwise runs HSUMMA with G = sqrt(p) and b = B (Section IV);
+it leaves the grid and the panel sizes to the user.  This module
+
+  - times the library's candidate configurations (hsumma_candidates) of seeded
+    products on the GPU (each run after an L2 flush, CUDA events, best of two);
+  - trains the 10 -> 64 -> 64 -> 64 -> 1 GELU network on those timings on the
+    GPU with the library's kernels (hsumma_mlp_backward, hsumma_mlp_adam:
+    fp32, full batch, Adam with cosine-decayed step size, MSE on standardised
+    ln t);
+  - evaluates its picks (hsumma_mlp_pick: bf16 scoring + argmin on the device)
+    on held-out products by the pick's time over the exhaustive best, beside the
+    paper's standard setting (G = sqrt(p), b = B, one sub-tile per block);
+  - loads a trained model into the library (hsumma_mlp_load) so that hsumma_gemm
+    with P = Q = G = b = Bouter = 0 uses it.
+
+    python -m paper_1306_4161_gb300.autotune collect --out DIR
+    python -m paper_1306_4161_gb300.autotune train --data DIR --out DIR/cost_model.npz
+    python -m paper_1306_4161_gb300.autotune evaluate --data DIR --model DIR/cost_model.npz
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+import paper_1306_4161_gb300 as hs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TUNING_DIR = os.path.join(HERE, "tuning")
+MODEL_PATH = os.path.join(TUNING_DIR, "cost_model.npz")
+KIND_CODE = {"fp64": 0, "int8": 1, "bf16": 2}
+KIND_NAME = {v: k for k, v in KIND_CODE.items()}
+LAYERS = ((10, 64), (64, 64), (64, 64), (64, 1))   # (fan_in, fan_out), row-major W[out][in]
+
+
+def _workloads():
+    root = os.path.dirname(HERE)
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import workloads
+    return workloads
+
+
+# ---------------------------------------------------------------- the baseline
+def _divisors(n: int) -> list[int]:
+    small = [d for d in range(1, int(math.isqrt(n)) + 1) if n % d == 0]
+    return sorted(set(small + [n // d for d in small]))
+
+
+def paper_rule(M, N, K, kind, S):
+    """HSUMMA's standard setting (Section IV: G = sqrt(p), b = B) on the grid of
+    one kernel sub-tile per block: the valid group count nearest sqrt(p) on a
+    log scale (ties: the smaller), b the stage width and B = b."""
+    P, Q, _, b, _ = hs.candidates(M, N, K, kind, S)[0]
+    p = P * Q
+    valid = []
+    for G in _divisors(p):
+        try:
+            hs.group_shape(P, Q, G)
+            valid.append(G)
+        except hs.HsummaError:
+            pass
+    half = 0.5 * math.log2(p)
+    G = min(valid, key=lambda g: (abs(math.log2(g) - half), g))
+    return (P, Q, G, b, b)
+
+
+# ---------------------------------------------------------------- timing
+class Timer:
+    """Device time of one call on torch's current stream, after writing a
+    buffer larger than the L2 (so every run starts with a cold L2)."""
+
+    def __init__(self, flush_bytes: int = 256 << 20):
+        import torch
+        self.torch = torch
+        self.flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+
+    def time(self, fn, reps: int = 2) -> float:
+        best = math.inf
+        for _ in range(reps):
+            self.flush.zero_()
+            self.e0.record()
+            fn()
+            self.e1.record()
+            self.e1.synchronize()
+            best = min(best, self.e0.elapsed_time(self.e1))
+        return best
+
+
+def operands(M, N, K, seed):
+    """Seeded uniform[-1, 1) operands on the device and an output buffer (the
+    values do not change any timing)."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    A = torch.rand((M, K), generator=g, dtype=torch.float64, device="cuda") * 2 - 1
+    B = torch.rand((K, N), generator=g, dtype=torch.float64, device="cuda") * 2 - 1
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    return A, B, C
+
+
+def time_config(timer, A, B, C, cfg, kind, S, reps=2) -> float:
+    P, Q, G, b, Bo = cfg
+    try:
+        return timer.time(lambda: hs.gemm(A, B, P=P, Q=Q, G=G, b=b, Bouter=Bo, kind=kind,
+                                          slices=S, out=C), reps)
+    except hs.HsummaError:
+        return math.inf
+
+
+# ---------------------------------------------------------------- collection
+def collect(out_dir, n_samples=2000, per_shape=20, n_heldout=200, seed=4000, reps=2,
+            log=print):
+    """Training samples: per_shape seeded candidates of each of a seeded
+    sequence of products, timed, until n_samples are taken.  Held-out set:
+    every candidate plus the paper's setting of each of n_heldout other
+    products.  Writes samples.npz (rows M, N, K, kind, S, P, Q, G, b, B, ms;
+    column 11 numbers the product) and heldout.npz under out_dir."""
+    import torch
+    wl = _workloads()
+    os.makedirs(out_dir, exist_ok=True)
+    hs.init(0)
+    timer = Timer()
+    t0 = time.time()
+    train_shapes = wl.tuning_shapes(4 * n_samples // per_shape + 8, seed + 1)
+    held_shapes = wl.tuning_shapes(n_heldout, seed + 2)
+
+    rows = []
+    for i, (M, N, K, kind, S) in enumerate(train_shapes):
+        if len(rows) >= n_samples:
+            break
+        A, B, C = operands(M, N, K, seed + 10 + i)
+        cands = hs.candidates(M, N, K, kind, S)
+        order = np.argsort(wl.splitmix64(seed + 100000 + i, 0, len(cands)), kind="stable")
+        chosen = sorted(order[:min(per_shape, n_samples - len(rows))].tolist())
+        time_config(timer, A, B, C, cands[0], kind, S, reps=1)     # grows the workspace
+        for j in chosen:
+            ms = time_config(timer, A, B, C, cands[j], kind, S, reps)
+            rows.append((M, N, K, KIND_CODE[kind], S, *cands[j], ms, i))
+        hs.sync()
+        del A, B, C
+        if (i + 1) % 10 == 0:
+            log(f"train {i + 1} shapes, {len(rows)} samples, {time.time() - t0:.0f}s")
+    rows = np.array(rows, dtype=np.float64)
+    np.savez_compressed(os.path.join(out_dir, "samples.npz"), rows=rows)
+
+    shape_rows, offs, cfgs, mss, base_cfg, base_ms = [], [0], [], [], [], []
+    for i, (M, N, K, kind, S) in enumerate(held_shapes):
+        A, B, C = operands(M, N, K, seed + 20000 + i)
+        cands = hs.candidates(M, N, K, kind, S)
+        time_config(timer, A, B, C, cands[0], kind, S, reps=1)
+        ms = [time_config(timer, A, B, C, c, kind, S, reps) for c in cands]
+        base = paper_rule(M, N, K, kind, S)
+        bms = time_config(timer, A, B, C, base, kind, S, reps)
+        hs.sync()
+        shape_rows.append((M, N, K, KIND_CODE[kind], S))
+        cfgs.extend(cands)
+        mss.extend(ms)
+        offs.append(len(cfgs))
+        base_cfg.append(base)
+        base_ms.append(bms)
+        del A, B, C
+        if (i + 1) % 10 == 0:
+            log(f"held-out {i + 1}/{n_heldout} shapes, {time.time() - t0:.0f}s")
+            _save_heldout(out_dir, shape_rows, offs, cfgs, mss, base_cfg, base_ms)
+    _save_heldout(out_dir, shape_rows, offs, cfgs, mss, base_cfg, base_ms)
+    torch.cuda.synchronize()
+    log(f"collected in {time.time() - t0:.0f}s")
+
+
+def _save_heldout(out_dir, shape_rows, offs, cfgs, mss, base_cfg, base_ms):
+    np.savez_compressed(os.path.join(out_dir, "heldout.npz"),
+                        shapes=np.array(shape_rows, dtype=np.int64),
+                        offsets=np.array(offs, dtype=np.int64),
+                        cfg=np.array(cfgs, dtype=np.int64).reshape(-1, 5),
+                        ms=np.array(mss, dtype=np.float64),
+                        base_cfg=np.array(base_cfg, dtype=np.int64).reshape(-1, 5),
+                        base_ms=np.array(base_ms, dtype=np.float64))
+
+
+def load_heldout(path):
+    d = np.load(path)
+    n = len(d["shapes"])
+    out = []
+    for i in range(n):
+        a, b = int(d["offsets"][i]), int(d["offsets"][i + 1])
+        M, N, K, kc, S = (int(v) for v in d["shapes"][i])
+        out.append(dict(M=M, N=N, K=K, kind=KIND_NAME[kc], S=S, cfg=d["cfg"][a:b],
+                        ms=d["ms"][a:b], base_cfg=tuple(int(v) for v in d["base_cfg"][i]),
+                        base_ms=float(d["base_ms"][i])))
+    return out
+
+
+def split_by_product(rows, frac=0.1):
+    """Training and validation rows: the last frac of the products (column 11)
+    are the validation set."""
+    ids = np.unique(rows[:, 11])
+    cut = ids[int(round(len(ids) * (1 - frac)))] if len(ids) > 1 else ids[-1] + 1
+    return rows[rows[:, 11] < cut], rows[rows[:, 11] >= cut]
+
+
+def sample_features(rows):
+    """Raw features (n x 10) and ln t of training rows (M, N, K, kind, S, cfg, ms)."""
+    X = np.empty((len(rows), 10), dtype=np.float32)
+    for i, r in enumerate(rows):
+        M, N, K, kc, S = (int(v) for v in r[:5])
+        X[i] = hs.features(M, N, K, [tuple(int(v) for v in r[5:10])], KIND_NAME[kc], S)[0]
+    return X, np.log(rows[:, 10])
+
+
+# ---------------------------------------------------------------- training
+def init_params(seed: int) -> np.ndarray:
+    """Glorot-uniform weights from the seeded uniform stream, zero biases."""
+    wl = _workloads()
+    u = wl.matrix(1, hs.N_MLP_PARAMS, seed, "uniform")[0]
+    theta = np.zeros(hs.N_MLP_PARAMS, dtype=np.float64)
+    off = 0
+    for fi, fo in LAYERS:
+        lim = math.sqrt(6.0 / (fi + fo))
+        theta[off:off + fi * fo] = lim * u[off:off + fi * fo]
+        off += fi * fo + fo
+    assert off == hs.N_MLP_PARAMS
+    return theta.astype(np.float32)
+
+
+def train(X, y, steps=6000, lr=3e-3, seed=4003, log=print, X_val=None, y_val=None,
+          check_every=250):
+    """Fit the network to ln t on the GPU: full-batch Adam (beta = 0.9, 0.999;
+    eps = 1e-8) with the step size decayed on a cosine from lr to 0.  Features
+    and targets are standardised with the training set's statistics.  With a
+    validation set, the parameters of the checkpoint (every check_every steps)
+    with the smallest validation error are kept.  Returns the model dict."""
+    import torch
+    hs.init(0)
+    lib = hs.lib()
+    mean = X.mean(axis=0).astype(np.float32)
+    std = X.std(axis=0).astype(np.float32)
+    std[std == 0] = 1.0
+    ym, ys = float(y.mean()), float(y.std()) or 1.0
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    dX, dy = dev((X - mean) / std), dev((y - ym) / ys)
+    theta = dev(init_params(seed))
+    m = torch.zeros_like(theta)
+    v = torch.zeros_like(theta)
+    grad = torch.empty_like(theta)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    n = X.shape[0]
+    stream = hs._stream_ptr()
+    hist = []
+    best = (math.inf, 0, None)
+    if X_val is not None:
+        dXv, yv = dev((X_val - mean) / std), (np.asarray(y_val) - ym) / ys
+        pv = torch.empty(len(yv), dtype=torch.float32, device="cuda")
+    for t in range(1, steps + 1):
+        lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (t - 1) / steps))
+        hs._check(lib.hsumma_mlp_backward(n, theta.data_ptr(), dX.data_ptr(), dy.data_ptr(),
+                                          grad.data_ptr(), loss.data_ptr(), stream))
+        hs._check(lib.hsumma_mlp_adam(hs.N_MLP_PARAMS, theta.data_ptr(), grad.data_ptr(),
+                                      m.data_ptr(), v.data_ptr(), t, lr_t, 0.9, 0.999, 1e-8,
+                                      stream))
+        if t == 1 or t % 500 == 0 or t == steps:
+            hist.append((t, float(loss.item())))
+            log(f"step {t}: mse {hist[-1][1]:.5f}")
+        if X_val is not None and (t % check_every == 0 or t == steps):
+            hs._check(lib.hsumma_mlp_forward(len(yv), theta.data_ptr(), dXv.data_ptr(),
+                                             pv.data_ptr(), None, stream))
+            err = float(np.mean((pv.cpu().numpy().astype(np.float64) - yv) ** 2))
+            if err < best[0]:
+                best = (err, t, theta.cpu().numpy().copy())
+    hs.sync()
+    out = dict(theta=theta.cpu().numpy(), mean=mean, std=std, y_mean=np.float64(ym),
+               y_std=np.float64(ys), history=np.array(hist))
+    if best[2] is not None:
+        log(f"kept step {best[1]}: validation mse {best[0]:.5f}")
+        out.update(theta=best[2], val_mse=np.float64(best[0]), val_step=np.int64(best[1]))
+    return out
+
+
+def save_model(model, path):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    np.savez(path, **model)
+
+
+def read_model(path=MODEL_PATH):
+    d = np.load(path)
+    return {k: d[k] for k in d.files}
+
+
+def load_into_library(path=MODEL_PATH):
+    """Load the trained model at path into the library (hsumma_gemm's automatic
+    choice then uses it)."""
+    m = read_model(path)
+    hs.load_model(m["theta"], m["mean"], m["std"])
+    return m
+
+
+# ---------------------------------------------------------------- evaluation
+def pick(model, M, N, K, kind, S, cfgs) -> int:
+    """Index of the configuration the model picks: bf16 scoring and argmin on
+    the device (hsumma_mlp_pick), as in the library's automatic choice."""
+    import torch
+    X = hs.features(M, N, K, cfgs, kind, S)
+    Xn = (X - model["mean"]) / model["std"]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    dth, dX = dev(model["theta"]), dev(Xn)
+    pred = torch.empty(len(cfgs), dtype=torch.float32, device="cuda")
+    best = torch.empty(1, dtype=torch.int32, device="cuda")
+    hs._check(hs.lib().hsumma_mlp_pick(len(cfgs), dth.data_ptr(), dX.data_ptr(),
+                                       pred.data_ptr(), best.data_ptr(), hs._stream_ptr()))
+    return int(best.item())
+
+
+def _stats(r):
+    r = np.asarray(r, dtype=np.float64)
+    return dict(geomean=float(np.exp(np.mean(np.log(r)))), mean=float(r.mean()),
+                median=float(np.median(r)), p90=float(np.quantile(r, 0.9)), max=float(r.max()),
+                within_10pct=float(np.mean(r <= 1.10)), n=int(r.size))
+
+
+def evaluate(model, heldout, picker=None):
+    """Ratios of the model's pick and of the paper's setting to the exhaustive
+    best (the fastest candidate), over the held-out products, overall and per
+    kind."""
+    picker = picker or (lambda h: pick(model, h["M"], h["N"], h["K"], h["kind"], h["S"],
+                                       [tuple(int(v) for v in c) for c in h["cfg"]]))
+    rows = []
+    for h in heldout:
+        ms = h["ms"]
+        best = float(np.min(ms))
+        j = picker(h)
+        rows.append((h["kind"], ms[j] / best, h["base_ms"] / best))
+    out = {"model": _stats([r[1] for r in rows]), "paper_rule": _stats([r[2] for r in rows])}
+    for k in KIND_CODE:
+        sel = [r for r in rows if r[0] == k]
+        if sel:
+            out[k] = {"model": _stats([r[1] for r in sel]),
+                      "paper_rule": _stats([r[2] for r in sel])}
+    return out
+
+
+# ---------------------------------------------------------------- CLI
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_1306_4161_gb300.autotune")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("collect")
+    c.add_argument("--out", default=TUNING_DIR)
+    c.add_argument("--samples", type=int, default=2000)
+    c.add_argument("--per-shape", type=int, default=20)
+    c.add_argument("--heldout", type=int, default=200)
+    c.add_argument("--seed", type=int, default=4000)
+    t = sub.add_parser("train")
+    t.add_argument("--data", default=TUNING_DIR)
+    t.add_argument("--out", default=MODEL_PATH)
+    t.add_argument("--steps", type=int, default=6000)
+    t.add_argument("--lr", type=float, default=3e-3)
+    t.add_argument("--seed", type=int, default=4003)
+    e = sub.add_parser("evaluate")
+    e.add_argument("--data", default=TUNING_DIR)
+    e.add_argument("--model", default=MODEL_PATH)
+    e.add_argument("--report", default=None)
+    a = ap.parse_args(argv)
+    if a.cmd == "collect":
+        collect(a.out, a.samples, a.per_shape, a.heldout, a.seed)
+    elif a.cmd == "train":
+        rows = np.load(os.path.join(a.data, "samples.npz"))["rows"]
+        rows = rows[np.isfinite(rows[:, 10])]
+        tr, va = split_by_product(rows)
+        X, y = sample_features(tr)
+        Xv, yv = sample_features(va)
+        save_model(train(X, y, a.steps, a.lr, a.seed, X_val=Xv, y_val=yv), a.out)
+    else:
+        hs.init(0)
+        rep = evaluate(read_model(a.model), load_heldout(os.path.join(a.data, "heldout.npz")))
+        text = json.dumps(rep, indent=1)
+        print(text)
+        if a.report:
+            with open(a.report, "w") as f:
+                f.write(text + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,313 @@
+// Automatic configuration of hsumma_gemm: which (P, Q, G, b, B) to run a
+// product with.  The paper leaves the group count to a few sampled runs
+// (Section V-A-1, Section VI) and fixes b and B by hand; here a candidate set is
+// enumerated per product, scored by the learned cost model when one is loaded
+// (hsumma_mlp_load), and otherwise timed one by one on the caller's operands
+// (exhaustive search, which is also the model's judge).  Choices are cached per
+// (M, N, K, mode) for the life of the process or until a model is (un)loaded.
+//
+// Candidate set for a product (a design of this library, not of the paper):
+//   blocks of 1 or 2 sub-tiles per direction: P = ceil(M / (f_m TM)),
+//   Q = ceil(N / (f_n TN)), f_m, f_n in {1, 2}, with the kernels' sub-tiles
+//   TM x TN (binary64 128 x 128, int8 128 x 128, bf16 128 x 256);
+//   group counts G in {1, p/16, p/8, p/4, p/2, p} (p = PQ) that factor as
+//   I | P, J | Q, one per distinct realised cluster shape (flat, or a cluster
+//   of the group's CTAs);
+//   b = the kernel's stage width (32, 128, 64): b does not change the
+//   arithmetic or the schedule on this GPU, only the counters' bookkeeping;
+//   B in {b, 4b, 16b} (how far ahead the owners stage outer panels in L2).
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+#include "../../include/hsumma.h"
+
+namespace hs {
+namespace {
+
+struct Cand {
+  int P, Q, G, b, Bo;
+};
+
+void path_shape(int kind, int *tm, int *tn, int *b) {
+  if (kind == HSUMMA_FP64) {
+    *tm = 128, *tn = 128, *b = 32;
+  } else if (kind == HSUMMA_INT8_SLICES) {
+    *tm = 128, *tn = 128, *b = 128;
+  } else {
+    *tm = 128, *tn = 256, *b = 64;
+  }
+}
+
+void enumerate(int64_t M, int64_t N, int kind, std::vector<Cand> &out) {
+  int tm, tn, b;
+  path_shape(kind, &tm, &tn, &b);
+  std::vector<std::pair<int64_t, int64_t>> grids;
+  for (int fm = 1; fm <= 2; ++fm)
+    for (int fn = 1; fn <= 2; ++fn) {
+      int64_t P = ceil_div(M, (int64_t)fm * tm), Q = ceil_div(N, (int64_t)fn * tn);
+      if (P < 1) P = 1;
+      if (Q < 1) Q = 1;
+      if (P > 65535 || Q > 65535 || P * Q > (int64_t)1 << 30) continue;
+      bool seen = false;
+      for (auto &g : grids) seen |= g.first == P && g.second == Q;
+      if (seen) continue;
+      grids.emplace_back(P, Q);
+      const int64_t p = P * Q;
+      std::vector<std::pair<int, int>> shapes;
+      for (int64_t div : {p, (int64_t)16, (int64_t)8, (int64_t)4, (int64_t)2, (int64_t)1}) {
+        if (p % div) continue;
+        const int G = (int)(p / div);  // p / p = 1 first, then p/16 ... p
+        int I, J, cm, cn;
+        if (hsumma_group_shape((int)P, (int)Q, G, &I, &J, &cm, &cn) != HSUMMA_OK) continue;
+        bool dup = false;
+        for (auto &s : shapes) dup |= s.first == cm && s.second == cn;
+        if (dup) continue;
+        shapes.emplace_back(cm, cn);
+        for (int r : {1, 4, 16}) out.push_back({(int)P, (int)Q, G, b, r * b});
+      }
+    }
+}
+
+void features(int64_t M, int64_t N, int64_t K, int kind, int S, const Cand &c, float *x) {
+  auto lg = [](double v) { return (float)std::log2(v < 1.0 ? 1.0 : v); };
+  x[0] = lg((double)M);
+  x[1] = lg((double)N);
+  x[2] = lg((double)K);
+  x[3] = lg(c.P);
+  x[4] = lg(c.Q);
+  x[5] = lg(c.G);
+  x[6] = lg(c.b);
+  x[7] = lg(c.Bo);
+  x[8] = (float)kind;
+  x[9] = kind == HSUMMA_FP64 ? 0.f : (float)S;
+}
+
+std::mutex g_mu;
+std::map<std::tuple<int64_t, int64_t, int64_t, int>, Cand> g_cache;
+
+int decode_mode(int mode, int *kind, int *S) {
+  *kind = mode & 0xff;
+  *S = (mode >> 8) & 0xff;
+  if (*kind == HSUMMA_FP64) return HSUMMA_OK;
+  if ((*kind == HSUMMA_INT8_SLICES && *S >= 1 && *S <= 8) ||
+      (*kind == HSUMMA_BF16_SLICES && *S >= 1 && *S <= 7))
+    return HSUMMA_OK;
+  set_error("bad mode %#x", mode);
+  return HSUMMA_ERR_ARG;
+}
+
+// Score the candidates with the loaded model on the device; *best is the index
+// of the smallest predicted time.
+int pick_by_model(int64_t M, int64_t N, int64_t K, int kind, int S,
+                  const std::vector<Cand> &cands, cudaStream_t s, int *best) {
+  float mean[kModelFeatures], stdv[kModelFeatures];
+  const float *theta = loaded_model(mean, stdv);
+  if (!theta) {
+    set_error("no cost model loaded (hsumma_mlp_load)");
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  const int n = (int)cands.size();
+  std::vector<float> X((size_t)n * kModelFeatures);
+  for (int i = 0; i < n; ++i) {
+    float *x = &X[(size_t)i * kModelFeatures];
+    features(M, N, K, kind, S, cands[i], x);
+    for (int j = 0; j < kModelFeatures; ++j)
+      x[j] = (x[j] - mean[j]) / (stdv[j] > 0.f ? stdv[j] : 1.f);
+  }
+  DeviceState &st = state();
+  const size_t need = ((size_t)kModelParams + (size_t)n * (kModelFeatures + 1) + 1) * 4;
+  if (st.tune_bytes < need) {
+    if (st.tune_buf) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+      cudaFree(st.tune_buf);
+      st.tune_buf = nullptr;
+      st.tune_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&st.tune_buf, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(model scoring)");
+    st.tune_bytes = need;
+  }
+  float *d_theta = static_cast<float *>(st.tune_buf);
+  float *d_X = d_theta + kModelParams;
+  float *d_pred = d_X + (size_t)n * kModelFeatures;
+  int32_t *d_best = reinterpret_cast<int32_t *>(d_pred + n);
+  cudaError_t e = cudaMemcpyAsync(d_theta, theta, kModelParams * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_X, X.data(), X.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy model inputs");
+  int rc = mlp_pick_device(n, d_theta, d_X, d_pred, d_best, s);
+  if (rc != HSUMMA_OK) return rc;
+  int32_t h_best = -1;
+  e = cudaMemcpyAsync(&h_best, d_best, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "read model choice");
+  if (h_best < 0 || h_best >= n) {
+    set_error("model choice out of range (%d of %d)", h_best, n);
+    return HSUMMA_ERR_CUDA;
+  }
+  *best = h_best;
+  return HSUMMA_OK;
+}
+
+// Time every candidate once on the caller's operands (C is overwritten) after
+// one untimed run; *best is the fastest that ran.
+int pick_by_timing(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                   const double *B, int64_t ldb, double *C, int64_t ldc, int mode,
+                   const std::vector<Cand> &cands, cudaStream_t s, int *best) {
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  void *sp = reinterpret_cast<void *>(s);
+  float best_ms = INFINITY;
+  int bi = -1;
+  int rc = HSUMMA_OK;
+  for (size_t i = 0; i < cands.size(); ++i) {   // one untimed run first
+    const Cand &w = cands[i];
+    if (hsumma_gemm(M, N, K, A, lda, B, ldb, C, ldc, w.P, w.Q, w.G, w.b, w.Bo, mode, sp) ==
+        HSUMMA_OK)
+      break;
+  }
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const Cand &c = cands[i];
+    cudaEventRecord(e0, s);
+    if (hsumma_gemm(M, N, K, A, lda, B, ldb, C, ldc, c.P, c.Q, c.G, c.b, c.Bo, mode, sp) !=
+        HSUMMA_OK)
+      continue;  // a candidate this device cannot launch
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "cudaEventSynchronize");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      bi = (int)i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HSUMMA_OK) return rc;
+  const int sync_rc = hsumma_sync(sp);  // device-side status of the timed runs
+  if (sync_rc != HSUMMA_OK) return sync_rc;
+  if (bi < 0) {
+    set_error("no candidate configuration ran");
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  *best = bi;
+  return HSUMMA_OK;
+}
+
+}  // namespace
+
+void forget_choices() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_cache.clear();
+}
+
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" {
+
+int hsumma_candidates(int64_t M, int64_t N, int64_t K, int mode, int *cfg, int max,
+                      int *count) {
+  int kind, S;
+  int st = decode_mode(mode, &kind, &S);
+  if (st != HSUMMA_OK) return st;
+  if (M < 0 || N < 0 || K < 0 || !count || (max > 0 && !cfg)) {
+    set_error("bad arguments");
+    return HSUMMA_ERR_ARG;
+  }
+  std::vector<Cand> c;
+  enumerate(M, N, kind, c);
+  *count = (int)c.size();
+  for (int i = 0; i < (int)c.size() && i < max; ++i) {
+    cfg[5 * i + 0] = c[i].P;
+    cfg[5 * i + 1] = c[i].Q;
+    cfg[5 * i + 2] = c[i].G;
+    cfg[5 * i + 3] = c[i].b;
+    cfg[5 * i + 4] = c[i].Bo;
+  }
+  return HSUMMA_OK;
+}
+
+int hsumma_features(int64_t M, int64_t N, int64_t K, int mode, const int *cfg, int n,
+                    float *X) {
+  int kind, S;
+  int st = decode_mode(mode, &kind, &S);
+  if (st != HSUMMA_OK) return st;
+  if (n < 0 || (n > 0 && (!cfg || !X))) {
+    set_error("bad arguments");
+    return HSUMMA_ERR_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const Cand c{cfg[5 * i], cfg[5 * i + 1], cfg[5 * i + 2], cfg[5 * i + 3], cfg[5 * i + 4]};
+    features(M, N, K, kind, S, c, X + (size_t)i * kModelFeatures);
+  }
+  return HSUMMA_OK;
+}
+
+int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                  const double *B, int64_t ldb, double *C, int64_t ldc, int mode, int policy,
+                  int *cfg, int *how, void *stream) {
+  if (state().device < 0) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  int kind, S;
+  int st = decode_mode(mode, &kind, &S);
+  if (st != HSUMMA_OK) return st;
+  if (!cfg || !how || policy < 0 || policy > 2 || M < 0 || N < 0 || K < 0) {
+    set_error("bad arguments");
+    return HSUMMA_ERR_ARG;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const auto key = std::make_tuple(M, N, K, mode);
+  if (policy == HSUMMA_CHOOSE_AUTO) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      const Cand &c = it->second;
+      cfg[0] = c.P, cfg[1] = c.Q, cfg[2] = c.G, cfg[3] = c.b, cfg[4] = c.Bo;
+      *how = HSUMMA_CHOSEN_CACHED;
+      return HSUMMA_OK;
+    }
+  }
+  std::vector<Cand> cands;
+  enumerate(M, N, kind, cands);
+  if (cands.empty()) {
+    set_error("no candidate configuration for %lld x %lld", (long long)M, (long long)N);
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
+  int bi = 0;
+  float mean[kModelFeatures], stdv[kModelFeatures];
+  const bool have_model = loaded_model(mean, stdv) != nullptr;
+  if (M == 0 || N == 0 || K == 0) {
+    bi = 0;  // nothing to compute: any candidate does
+    *how = HSUMMA_CHOSEN_MODEL;
+  } else if (policy == HSUMMA_CHOOSE_MODEL || (policy == HSUMMA_CHOOSE_AUTO && have_model)) {
+    st = pick_by_model(M, N, K, kind, S, cands, s, &bi);
+    if (st != HSUMMA_OK) return st;
+    *how = HSUMMA_CHOSEN_MODEL;
+  } else {
+    st = pick_by_timing(M, N, K, A, lda, B, ldb, C, ldc, mode, cands, s, &bi);
+    if (st != HSUMMA_OK) return st;
+    *how = HSUMMA_CHOSEN_TIMED;
+  }
+  const Cand &c = cands[bi];
+  cfg[0] = c.P, cfg[1] = c.Q, cfg[2] = c.G, cfg[3] = c.b, cfg[4] = c.Bo;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_cache[key] = c;
+  return HSUMMA_OK;
+}
+
+}  // extern "C"

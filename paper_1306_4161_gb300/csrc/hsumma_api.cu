@@ -240,6 +240,8 @@ void hsumma_finalize(void) {
   cudaFree(g_state.d_status);
   if (g_state.workspace) cudaFree(g_state.workspace);
   if (g_state.host_staging) cudaFree(g_state.host_staging);
+  if (g_state.tune_buf) cudaFree(g_state.tune_buf);
+  forget_choices();
   g_state = DeviceState();
   g_init = false;
 }
@@ -377,8 +379,14 @@ int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
   if (st != HSUMMA_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (P == 0 && Q == 0 && G == 0 && b == 0 && Bouter == 0) {
-    set_error("automatic configuration needs a loaded cost model (not built yet)");
-    return HSUMMA_ERR_UNSUPPORTED;
+    // automatic configuration: cached, else the loaded cost model's pick, else
+    // the fastest candidate timed on these operands
+    int cfg[5], how;
+    st = hsumma_choose(M, N, K, A, lda, B, ldb, C, ldc, mode, HSUMMA_CHOOSE_AUTO, cfg, &how,
+                       stream);
+    if (st != HSUMMA_OK) return st;
+    return hsumma_gemm(M, N, K, A, lda, B, ldb, C, ldc, cfg[0], cfg[1], cfg[2], cfg[3], cfg[4],
+                       mode, stream);
   }
   GridPlan g;
   st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, &g);

@@ -30,6 +30,8 @@ struct DeviceState {
   void *host_staging = nullptr;              // device buffers of hsumma_gemm_host
   size_t host_staging_bytes = 0;
   bool bf16_pair = false;                    // HSUMMA_BF16_PAIR=1: CTA-pair bf16 kernel
+  void *tune_buf = nullptr;                  // model scoring inputs of hsumma_choose
+  size_t tune_bytes = 0;
 };
 
 DeviceState &state();
@@ -84,6 +86,16 @@ int launch_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, con
                            cudaStream_t s);
 
 int run_peak(int kind, int64_t work, double *rate);
+
+// Learned cost model (mlp.cu): the parameters and feature standardisation
+// loaded by hsumma_mlp_load (host copies; nullptr when none is loaded), and the
+// bf16 scoring + argmin of n standardised feature rows on the device.
+constexpr int kModelParams = 9089, kModelFeatures = 10;
+const float *loaded_model(float *mean, float *stdv);
+int mlp_pick_device(int n, const float *d_theta, const float *d_X, float *d_pred,
+                    int32_t *d_best, cudaStream_t s);
+// Automatic configuration (autotune.cu): forget every cached choice.
+void forget_choices();
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

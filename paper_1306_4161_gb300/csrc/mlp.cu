@@ -466,6 +466,7 @@ int hsumma_mlp_pick(int n, const float *theta, const float *X, float *pred, int3
 int hsumma_mlp_load(const float *theta, const float *mean, const float *stdv) {
   if (!theta) {
     g_model.loaded = false;
+    forget_choices();
     return HSUMMA_OK;
   }
   if (!mean || !stdv) {
@@ -476,6 +477,7 @@ int hsumma_mlp_load(const float *theta, const float *mean, const float *stdv) {
   memcpy(g_model.mean, mean, sizeof(g_model.mean));
   memcpy(g_model.stdv, stdv, sizeof(g_model.stdv));
   g_model.loaded = true;
+  forget_choices();
   return HSUMMA_OK;
 }
 

@@ -1,0 +1,113 @@
+"""Host logic of the automatic configuration (no GPU): the candidate sets
+follow the group rule of Section III as the oracle states it, the features are
+the stated logarithms, the seeded tuning shapes keep their ranges, the paper's
+standard setting picks G nearest sqrt(p) (Section IV), and -- once tuning data
+is committed -- the committed model, evaluated by the float64 oracle network,
+stays within 10% of the exhaustive best on the held-out products."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import paper_1306_4161_gb300 as hs
+import workloads
+from oracle import cost_model, gpu_schedule as gsched, mlp
+from paper_1306_4161_gb300 import _build, autotune
+
+SHAPES = [(16384, 16384, 16384, "bf16", 5), (1024, 1024, 1024, "fp64", 0),
+          (1152, 7552, 2048, "int8", 4), (128, 128, 128, "fp64", 0), (3000, 200, 64, "bf16", 3),
+          (8192, 1024, 4096, "int8", 8), (5000, 7000, 3000, "fp64", 0)]
+TILE = {"fp64": (128, 128, 32), "int8": (128, 128, 128), "bf16": (128, 256, 64)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+
+
+@pytest.mark.parametrize("M,N,K,kind,S", SHAPES)
+def test_candidates_follow_the_group_rule(M, N, K, kind, S):
+    tm, tn, b = TILE[kind]
+    cands = hs.candidates(M, N, K, kind, S)
+    assert 1 <= len(cands) <= 72
+    assert len(set(cands)) == len(cands)
+    grids = {(math.ceil(M / (fm * tm)), math.ceil(N / (fn * tn))) for fm in (1, 2) for fn in (1, 2)}
+    shapes = {}
+    for P, Q, G, bb, Bo in cands:
+        assert (P, Q) in grids
+        assert bb == b and Bo in (b, 4 * b, 16 * b)
+        ij = gsched.group_shape(P, Q, G)
+        assert ij is not None, (P, Q, G)
+        assert (P * Q) // G in (1, 2, 4, 8, 16, P * Q)
+        cl = gsched.cluster_shape(P, Q, ij[0], ij[1], limit=16)
+        assert hs.group_shape(P, Q, G) == (*ij, *cl)
+        shapes.setdefault((P, Q), {}).setdefault(cl, set()).add(G)
+    for (P, Q), by_shape in shapes.items():
+        for cl, gs_ in by_shape.items():
+            assert len(gs_) == 1, (P, Q, cl, gs_)     # one G per realised cluster shape
+
+
+def test_features_are_the_stated_logarithms():
+    cfgs = [(8, 8, 4, 32, 128), (3, 5, 15, 64, 1024)]
+    X = hs.features(1000, 2048, 300, cfgs, "bf16", 5)
+    for x, (P, Q, G, b, Bo) in zip(X, cfgs):
+        want = [math.log2(v) for v in (1000, 2048, 300, P, Q, G, b, Bo)] + [2.0, 5.0]
+        assert np.allclose(x, want, rtol=1e-6)
+    assert hs.features(64, 64, 64, cfgs[:1], "fp64")[0, 8:].tolist() == [0.0, 0.0]
+
+
+def test_tuning_shapes_ranges_and_determinism():
+    sh = workloads.tuning_shapes(300, 11)
+    assert sh == workloads.tuning_shapes(300, 11)
+    for M, N, K, kind, S in sh:
+        lo, hi = workloads.TUNING_RANGES[kind]
+        for d in (M, N, K):
+            assert lo <= d <= hi and d % 128 == 0
+        s_lo, s_hi = workloads.TUNING_SLICES[kind]
+        assert s_lo <= S <= s_hi
+    kinds = [s[3] for s in sh]
+    assert kinds.count("fp64") == kinds.count("int8") == kinds.count("bf16") == 100
+    # log-uniform: about half of the draws below the geometric midpoint
+    Ms = np.array([s[0] for s in sh if s[3] == "bf16"])
+    assert 0.3 < np.mean(Ms < math.sqrt(1024 * 8192)) < 0.7
+
+
+@pytest.mark.parametrize("M,N,K,kind,S", SHAPES)
+def test_paper_setting_is_g_nearest_sqrt_p(M, N, K, kind, S):
+    P, Q, G, b, Bo = autotune.paper_rule(M, N, K, kind, S)
+    assert (P, Q) == hs.candidates(M, N, K, kind, S)[0][:2]
+    valid = [g for g in range(1, P * Q + 1) if (P * Q) % g == 0 and gsched.group_shape(P, Q, g)]
+    assert G == cost_model.paper_rule_groups(P * Q, valid)
+    assert Bo == b == TILE[kind][2]
+
+
+def test_initial_parameters():
+    th = autotune.init_params(5)
+    assert th.shape == (mlp.N_PARAMS,) and th.dtype == np.float32
+    layers = mlp.unpack(th.astype(np.float64))
+    for (W, bias), (fi, fo) in zip(layers, autotune.LAYERS):
+        assert W.shape == (fo, fi)
+        assert np.all(bias == 0)
+        lim = math.sqrt(6.0 / (fi + fo))
+        assert np.abs(W).max() <= lim and np.abs(W).max() > 0.8 * lim
+
+
+def test_committed_model_on_held_out_products_by_oracle_network():
+    path = os.path.join(autotune.TUNING_DIR, "heldout.npz")
+    if not (os.path.exists(path) and os.path.exists(autotune.MODEL_PATH)):
+        pytest.skip("no committed tuning data")
+    model = autotune.read_model()
+    held = autotune.load_heldout(path)
+
+    def picker(h):
+        cfgs = [tuple(int(v) for v in c) for c in h["cfg"]]
+        X = hs.features(h["M"], h["N"], h["K"], cfgs, h["kind"], h["S"]).astype(np.float64)
+        Xn = (X - model["mean"].astype(np.float64)) / model["std"].astype(np.float64)
+        pred, _ = mlp.forward(model["theta"].astype(np.float64), Xn)
+        return int(np.argmin(pred))
+
+    rep = autotune.evaluate(model, held, picker=picker)
+    assert rep["model"]["n"] == 200
+    assert rep["model"]["geomean"] <= 1.10
+    assert rep["model"]["geomean"] < rep["paper_rule"]["geomean"]

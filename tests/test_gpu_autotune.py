@@ -1,0 +1,169 @@
+"""The automatic configuration on the GPU: every cluster shape its candidate
+sets realise runs each kernel to the oracle's result; training by the library's
+kernels follows the float64 oracle's Adam trajectory; hsumma_gemm with
+P = Q = G = b = Bouter = 0 picks by the model, by timing, or from its cache and
+computes the right product; and the committed model's picks (bf16 on the
+device) stay within 10% of the exhaustive best on the held-out products and
+beat the paper's standard setting."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import gpu_schedule as gsched
+from oracle import mlp, split
+from tests.gpu_util import lib_ready, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TILES = {"fp64": (128, 128, 32, 448), "int8": (128, 128, 128, 640), "bf16": (128, 256, 64, 448)}
+CLUSTERS = [(1, 2), (1, 4), (1, 8), (1, 16), (2, 1), (2, 2), (2, 4), (2, 8), (4, 1), (4, 2),
+            (4, 3), (4, 4), (5, 2), (5, 3), (6, 2), (7, 2), (8, 1), (8, 2), (16, 1)]
+
+
+def realise(cm, cn):
+    """The smallest grid (P, Q, G) whose groups the oracle's rule realises as
+    cm x cn clusters."""
+    best = None
+    for P in range(1, 17):
+        for Q in range(1, 17):
+            if best and P * Q >= best[0] * best[1]:
+                continue
+            for G in range(1, P * Q + 1):
+                if (P * Q) % G:
+                    continue
+                ij = gsched.group_shape(P, Q, G)
+                if ij and gsched.cluster_shape(P, Q, ij[0], ij[1], limit=16) == (cm, cn):
+                    best = (P, Q, G)
+                    break
+    return best
+
+
+@pytest.mark.parametrize("kind", ["fp64", "int8", "bf16"])
+@pytest.mark.parametrize("cm,cn", CLUSTERS)
+def test_every_cluster_shape_matches_oracle(kind, cm, cn):
+    hs = lib_ready()
+    torch = torch_cuda()
+    P, Q, G = realise(cm, cn)
+    assert hs.group_shape(P, Q, G)[2:] == (cm, cn)
+    tm, tn, b, K = TILES[kind]
+    M, N = P * tm - 29, Q * tn - 13          # short last blocks
+    seed = 700 + 10 * cm + cn
+    if kind == "fp64":
+        A = workloads.matrix(M, K, seed, "smallint")
+        B = workloads.matrix(K, N, seed + 1, "smallint")
+        want = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+        S = 0
+    else:
+        A = workloads.matrix(M, K, seed, "uniform")
+        B = workloads.matrix(K, N, seed + 1, "wide")
+        S = 3
+        want = split.split_gemm(A, B, S, kind)
+    C = hs.gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), P=P, Q=Q, G=G, b=b,
+                Bouter=4 * b, kind=kind, slices=S)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), want)
+
+
+def test_training_follows_oracle_adam():
+    hs = lib_ready()
+    torch_cuda()
+    from paper_1306_4161_gb300 import autotune
+    n, steps, lr = 300, 25, 1e-3
+    X = workloads.matrix(n, 10, 61, "uniform") * 3.0 + 1.0
+    y = workloads.matrix(1, n, 62, "uniform")[0] * 2.0
+    model = autotune.train(X.astype(np.float32), y, steps=steps, lr=lr, seed=63,
+                           log=lambda *_: None)
+    # the oracle's run: same standardisation and schedule, float64 arithmetic
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    X32 = X.astype(np.float32).astype(np.float64)
+    mu, sd = X32.mean(axis=0), X32.std(axis=0)
+    assert np.allclose(model["mean"], mu, rtol=1e-5, atol=1e-6)
+    assert np.allclose(model["std"], sd, rtol=1e-5)
+    Xn = f32((X32 - f32(model["mean"])) / f32(model["std"]))
+    yn = f32((y - y.mean()) / y.std())
+    th0 = f32(autotune.init_params(63))
+    th, m, v = th0.copy(), np.zeros_like(th0), np.zeros_like(th0)
+    hp = dict(b1=float(f32(0.9)), b2=float(f32(0.999)), eps=float(f32(1e-8)))
+    losses = {}
+    for t in range(1, steps + 1):
+        lr_t = float(f32(lr * 0.5 * (1.0 + math.cos(math.pi * (t - 1) / steps))))
+        losses[t], g = mlp.loss_and_grad(th, Xn, yn)   # loss before step t's update
+        th, m, v = mlp.adam_step(th, g, m, v, t, lr=lr_t, **hp)
+    moved = np.linalg.norm(th - th0)
+    assert moved > 0
+    assert np.linalg.norm(model["theta"].astype(np.float64) - th) <= 2e-2 * moved
+    for t, L in model["history"]:
+        assert L == pytest.approx(losses[int(t)], rel=2e-3), t
+    assert losses[steps] < losses[1]
+
+
+def _exact_pair(torch, M, N, K, seed):
+    A = workloads.matrix(M, K, seed, "smallint")
+    B = workloads.matrix(K, N, seed + 1, "smallint")
+    want = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    return torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), want
+
+
+def test_automatic_choice_by_model_then_cached():
+    hs = lib_ready()
+    torch = torch_cuda()
+    from paper_1306_4161_gb300 import autotune
+    theta = autotune.init_params(71)            # any network gives a valid pick
+    hs.load_model(theta, np.zeros(10), np.ones(10))
+    try:
+        M, N, K = 1000, 1200, 512
+        dA, dB, want = _exact_pair(torch, M, N, K, 72)
+        cfg, how = hs.choose(dA, dB, kind="fp64")
+        assert how == "model"
+        assert cfg in hs.candidates(M, N, K, "fp64")
+        X = (hs.features(M, N, K, hs.candidates(M, N, K, "fp64"), "fp64") - 0.0) / 1.0
+        pred, _ = mlp.forward(theta.astype(np.float64), X.astype(np.float64))
+        j = hs.candidates(M, N, K, "fp64").index(cfg)
+        assert pred[j] <= pred.min() + 0.02 * (abs(pred.min()) + 1.0)   # bf16 scoring
+        C = hs.gemm(dA, dB)                     # P = Q = G = b = Bouter = 0
+        hs.sync()
+        assert np.array_equal(C.cpu().numpy(), want)
+        assert hs.choose(dA, dB, kind="fp64") == (cfg, "cached")
+    finally:
+        hs.load_model(None, None, None)
+
+
+def test_automatic_choice_by_timing_without_model():
+    hs = lib_ready()
+    torch = torch_cuda()
+    hs.load_model(None, None, None)
+    with pytest.raises(hs.HsummaError) as ei:
+        hs.choose(*_exact_pair(torch, 64, 64, 64, 80)[:2], kind="fp64", policy="model")
+    assert ei.value.status == -2
+    M, N, K = 700, 900, 384
+    dA, dB, want = _exact_pair(torch, M, N, K, 81)
+    cfg, how = hs.choose(dA, dB, kind="fp64")
+    assert how == "timed" and cfg in hs.candidates(M, N, K, "fp64")
+    C = hs.gemm(dA, dB)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), want)
+    # the split path chooses the same way and stays bit-exact with the oracle
+    A = workloads.matrix(300, 200, 82, "uniform")
+    B = workloads.matrix(200, 520, 83, "wide")
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = hs.gemm(dA, dB, kind="bf16", slices=4)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 4, "bf16"))
+    assert hs.choose(dA, dB, kind="bf16", slices=4)[1] == "cached"
+
+
+def test_committed_model_beats_paper_setting_on_held_out_products():
+    hs = lib_ready()
+    torch_cuda()
+    from paper_1306_4161_gb300 import autotune
+    path = os.path.join(autotune.TUNING_DIR, "heldout.npz")
+    if not (os.path.exists(path) and os.path.exists(autotune.MODEL_PATH)):
+        pytest.skip("no committed tuning data")
+    rep = autotune.evaluate(autotune.read_model(), autotune.load_heldout(path))
+    print("HELDOUT", rep["model"], rep["paper_rule"])
+    assert rep["model"]["n"] == 200
+    assert rep["model"]["geomean"] <= 1.10
+    assert rep["model"]["geomean"] < rep["paper_rule"]["geomean"]
