@@ -130,9 +130,16 @@ def _stream_ptr(stream=_DEFAULT):
 _inited = None
 
 
-def init(device: int = 0):
+def init(device: int = 0, cost_model: bool = True):
+    """Initialise the library on a device; with cost_model, load the trained
+    model shipped in tuning/cost_model.npz for the automatic configuration
+    (when the file is present)."""
     global _inited
     _check(lib().hsumma_init(device))
+    if cost_model and _inited != device:
+        from . import autotune
+        if os.path.exists(autotune.MODEL_PATH):
+            autotune.load_into_library(autotune.MODEL_PATH)
     _inited = device
 
 

@@ -128,7 +128,7 @@ def test_automatic_choice_by_model_then_cached():
         assert np.array_equal(C.cpu().numpy(), want)
         assert hs.choose(dA, dB, kind="fp64") == (cfg, "cached")
     finally:
-        hs.load_model(None, None, None)
+        autotune.load_into_library()
 
 
 def test_automatic_choice_by_timing_without_model():
@@ -153,6 +153,26 @@ def test_automatic_choice_by_timing_without_model():
     hs.sync()
     assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 4, "bf16"))
     assert hs.choose(dA, dB, kind="bf16", slices=4)[1] == "cached"
+    from paper_1306_4161_gb300 import autotune
+    autotune.load_into_library()
+    assert hs.choose(dA, dB, kind="bf16", slices=4)[1] == "model"   # loading drops the cache
+
+
+def test_library_loads_the_shipped_model():
+    hs = lib_ready()
+    torch = torch_cuda()
+    from paper_1306_4161_gb300 import autotune
+    if not os.path.exists(autotune.MODEL_PATH):
+        pytest.skip("no committed model")
+    autotune.load_into_library()
+    A = workloads.matrix(2048, 1536, 90, "uniform")
+    B = workloads.matrix(1536, 3072, 91, "uniform")
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    cfg, how = hs.choose(dA, dB, kind="bf16", slices=5)
+    assert how == "model" and cfg in hs.candidates(2048, 3072, 1536, "bf16", 5)
+    C = hs.gemm(dA, dB, kind="bf16", slices=5)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 5, "bf16"))
 
 
 def test_committed_model_beats_paper_setting_on_held_out_products():
@@ -167,3 +187,33 @@ def test_committed_model_beats_paper_setting_on_held_out_products():
     assert rep["model"]["n"] == 200
     assert rep["model"]["geomean"] <= 1.10
     assert rep["model"]["geomean"] < rep["paper_rule"]["geomean"]
+
+
+def test_model_pick_holds_when_retimed():
+    # the committed table is re-measured for a few held-out products: the
+    # model's pick against the stored exhaustive best, timed afresh
+    hs = lib_ready()
+    torch_cuda()
+    from paper_1306_4161_gb300 import autotune
+    path = os.path.join(autotune.TUNING_DIR, "heldout.npz")
+    if not (os.path.exists(path) and os.path.exists(autotune.MODEL_PATH)):
+        pytest.skip("no committed tuning data")
+    model = autotune.read_model()
+    held = autotune.load_heldout(path)
+    small = sorted(held, key=lambda h: h["M"] * h["N"] * h["K"] * max(h["S"], 1) ** 2)
+    chosen = [next(h for h in small if h["kind"] == k) for k in ("fp64", "int8", "bf16")]
+    chosen += [h for h in small if h not in chosen][:3]
+    timer = autotune.Timer()
+    ratios = []
+    for i, h in enumerate(chosen):
+        cfgs = [tuple(int(v) for v in c) for c in h["cfg"]]
+        j = autotune.pick(model, h["M"], h["N"], h["K"], h["kind"], h["S"], cfgs)
+        best = cfgs[int(np.argmin(h["ms"]))]
+        A, B, C = autotune.operands(h["M"], h["N"], h["K"], 900 + i)
+        autotune.time_config(timer, A, B, C, best, h["kind"], h["S"], reps=1)
+        t_pick = autotune.time_config(timer, A, B, C, cfgs[j], h["kind"], h["S"], reps=5)
+        t_best = autotune.time_config(timer, A, B, C, best, h["kind"], h["S"], reps=5)
+        ratios.append(t_pick / t_best)
+    print("RETIMED", [round(r, 3) for r in ratios])
+    assert max(ratios) <= 1.25
+    assert math.exp(np.mean(np.log(ratios))) <= 1.10
