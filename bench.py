@@ -5,7 +5,9 @@ each as a fraction of its roofline.
 One step = one hsumma_gemm call on the split path: exponent scan, slicing,
 the HSUMMA diagonal products on the tensor cores, exact recombination, on
 seeded uniform[-1, 1] inputs already resident in HBM (each 2 GiB, larger than
-L2, so no flush is needed between steps).  Prints one JSON line (rank 0).
+L2, so no flush is needed between steps).  The library records CUDA events
+around each stage of the timed steps (hsumma_stage_timing), which give the
+dominant kernel's duration for the roofline.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -29,11 +31,12 @@ sys.path.insert(0, ROOT)
 
 N_SIZE = 16384
 METRIC = "FP64-accurate TFLOP/s at n=16384, split-precision vs native FP64, % of roofline"
-SPLIT = dict(P=128, Q=64, G=256, b=64, Bouter=1024, kind="bf16", slices=5)
+SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=2048, kind="bf16", slices=5)
 NATIVE = dict(P=128, Q=128, G=4096, b=32, Bouter=128)
 WORKLOAD = ("split_vs_fp64_16384: M=N=K=16384, A,B uniform[-1,1] (SplitMix64 seeds 1002/2002), "
             "bf16 slices S=5 (15 pair products), virtual grid 128x64 of 128x256 blocks, "
-            "G=256 groups of 8x4 (inner level served from L2), b=64, B=1024 (owner L2 prefetch); "
+            "G=4096 groups of 2x1 (each group one CTA pair: the in-group B broadcast is the "
+            "two-SM MMA), b=64, B=2048 (owner L2 prefetch); "
             "native fp64 beside it on a 128x128 grid, G=4096, b=32, B=128")
 
 
@@ -44,10 +47,13 @@ def configure(n):
     if n % 256:
         raise SystemExit("--size must be a multiple of 256")
     N_SIZE = n
-    SPLIT = dict(SPLIT, P=n // 128, Q=n // 256, G=max(1, (n // 128) * (n // 256) // 32))
+    SPLIT = dict(SPLIT, P=n // 128, Q=n // 256, G=max(1, (n // 128) * (n // 256) // 2))
     NATIVE = dict(NATIVE, P=n // 128, Q=n // 128, G=(n // 128) ** 2 // 4)
     if n != 16384:
-        WORKLOAD = WORKLOAD.replace("16384", str(n))
+        WORKLOAD = (f"split_vs_fp64_{n}: M=N=K={n}, bf16 S=5, grid {n // 128}x{n // 256} of "
+                    f"128x256 blocks, G={SPLIT['G']} (2x1 groups, CTA pairs), b=64, "
+                    f"B={SPLIT['Bouter']}; native fp64 grid {n // 128}x{n // 128}, "
+                    f"G={NATIVE['G']}")
 
 
 def flops(n=None):
@@ -55,7 +61,7 @@ def flops(n=None):
     return 2.0 * n ** 3
 
 
-def measured_traffic(kernel="bf16_diag_kernel"):
+def measured_traffic(kernel="bf16_pair_kernel"):
     """DRAM bytes per launch from the committed ncu record, only while the
     kernel's source is the one the counters were taken on (else None)."""
     import hashlib
@@ -146,6 +152,25 @@ def cpu_oracle_rate(A, B, target_s=15.0):
     return 2.0 * rows * n * B.shape[1] / dt / 1e12, rows, cores, dt
 
 
+def cpu_leg(A_band, A_rows, B, cols, sampled):
+    """The bench's CPU leg (with the reference arm, the only code here that runs
+    the oracle): the plain binary64 triple loop timed on a band of rows of C
+    (cpu_baseline), and the compensated (Dot2) reference of the sampled
+    entries, against which the GPU results' errors max |C - C^| / (|A||B|)
+    are reported."""
+    from oracle import native, split
+    rate, rws, cores, dt = cpu_oracle_rate(A_band, B, target_s=12.0)
+    cpu = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+           "sample": f"{rws} rows of C at n={B.shape[0]} by the plain binary64 triple loop "
+                     f"({dt:.1f} s)"}
+    import numpy as np
+    ref, absab = native.dot2_entries(A_rows, B, np.arange(A_rows.shape[0]), cols)
+    acc = {f"{k}_max_rel_err": split.max_rel_error(v, ref, absab) for k, v in sampled.items()}
+    acc["tolerance_2Ku"] = split.tolerance(B.shape[0])
+    acc["reference"] = f"Dot2 on {len(cols)} sampled entries"
+    return cpu, acc
+
+
 def run_reference(args, rank, world):
     import numpy as np
     import workloads
@@ -184,6 +209,106 @@ def run_reference(args, rank, world):
     return out
 
 
+def run_table(sections):
+    """Throughput of the five workloads' configurations (one JSON line each,
+    "table" rows; no oracle: the accuracy of these launches is checked by the
+    GPU tests).  Times are CUDA events on the launching stream, best of the
+    runs, each run after an L2 flush."""
+    import numpy as np
+    import torch
+    import paper_1306_4161_gb300 as hs
+    import workloads
+    hs.init(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dmma = hs.peak("dmma", 4000) / 1e12
+    imma = hs.peak("imma", 4000) / 1e12
+    bf16 = read_peaks().get("bf16_tflops_sustained") or 1700.0
+
+    def timed(fn, reps=1, warm=True):
+        if warm:               # also grows the split path's workspace
+            fn()
+            hs.sync()
+        best, stages = float("inf"), None
+        for _ in range(reps):
+            flush.zero_()
+            hs.stage_timing(True)
+            e0.record()
+            fn()
+            e1.record()
+            hs.stage_timing(False)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            if t < best:
+                best, stages = t, hs.stage_times()[0]
+        hs.sync()
+        return best, stages
+
+    def emit(**kw):
+        print(json.dumps({"table": True, **kw}), flush=True)
+
+    def product(M, N, K, distA, distB, seedA, seedB):
+        return (workloads.matrix_torch(M, K, seedA, distA, device="cuda"),
+                workloads.matrix_torch(K, N, seedB, distB, device="cuda"),
+                torch.empty((M, N), dtype=torch.float64, device="cuda"))
+
+    if 0 in sections:
+        A, B, C = product(512, 512, 512, "uniform", "uniform", 1000, 2000)
+        ms, _ = timed(lambda: hs.gemm(A, B, out=C, P=4, Q=4, G=4, b=32, Bouter=64), reps=20)
+        tf = 2 * 512 ** 3 / ms / 1e9
+        emit(workload="hsumma_fp64_512", path="fp64", cfg="4x4 G=4 b=32 B=64", ms=ms,
+             tflops=tf, frac_of_dmma=tf / dmma)
+    if 1 in sections:
+        n = 8192
+        A, B, C = product(n, n, n, "uniform", "uniform", 1001, 2001)
+        for G in (1, 4, 16, 64, 256):
+            for b in (32, 64, 128):
+                for Bo in (b, 2 * b, 4 * b):
+                    ms, _ = timed(lambda: hs.gemm(A, B, out=C, P=16, Q=16, G=G, b=b, Bouter=Bo),
+                                  warm=False)
+                    tf = 2 * n ** 3 / ms / 1e9
+                    emit(workload="hsumma_fp64_8192_gsweep", path="fp64",
+                         cfg=f"16x16 G={G} b={b} B={Bo}", cluster=hs.group_shape(16, 16, G)[2:],
+                         ms=ms, tflops=tf, frac_of_dmma=tf / dmma, counters=hs.counters())
+        del A, B, C
+    if 2 in sections:
+        n = 16384
+        A, B, C = product(n, n, n, "uniform", "uniform", 1002, 2002)
+        ms, _ = timed(lambda: hs.gemm(A, B, out=C, **NATIVE), warm=False)
+        tf = 2 * n ** 3 / ms / 1e9
+        emit(workload="split_vs_fp64_16384", path="fp64", cfg="128x128 G=4096 b=32 B=128",
+             ms=ms, tflops=tf, frac_of_dmma=tf / dmma)
+        split_cfg = {k: v for k, v in SPLIT.items() if k not in ("kind", "slices")}
+        for kind, slices, cfg, peak in (
+                ("bf16", range(3, 7), split_cfg, bf16),
+                ("int8", range(3, 9), dict(P=128, Q=128, G=1, b=128, Bouter=2048), imma)):
+            for S in slices:
+                ms, st = timed(lambda: hs.gemm(A, B, out=C, kind=kind, slices=S, **cfg))
+                npairs = S * (S + 1) // 2
+                unit = npairs * 2 * n ** 3 / st[2] / 1e9
+                emit(workload="split_vs_fp64_16384", path=kind, slices=S,
+                     cfg=" ".join(f"{k}={v}" for k, v in cfg.items()), ms=ms,
+                     tflops=2 * n ** 3 / ms / 1e9, stage_ms=st,
+                     product_kernel={"achieved": unit, "peak": peak, "frac": unit / peak})
+        del A, B, C
+    if 3 in sections:
+        M, N, K = 24576, 16384, 32768
+        A, B, C = product(M, N, K, "normal_spiked", "normal", 1003, 2003)
+        for G in (1, 3, 4, 12, 16, 48):
+            ms, _ = timed(lambda: hs.gemm(A, B, out=C, P=12, Q=16, G=G, b=32, Bouter=128),
+                          warm=False)
+            tf = 2 * M * N * K / ms / 1e9
+            emit(workload="rect_24576x16384x32768", path="fp64", cfg=f"12x16 G={G} b=32 B=128",
+                 cluster=hs.group_shape(12, 16, G)[2:], ms=ms, tflops=tf,
+                 frac_of_dmma=tf / dmma)
+        for how in ("model", "timed"):
+            cfg, _ = hs.choose(A, B, C, kind="bf16", slices=7, policy=how)
+            ms, st = timed(lambda: hs.gemm(A, B, out=C, kind="bf16", slices=7, P=cfg[0],
+                                           Q=cfg[1], G=cfg[2], b=cfg[3], Bouter=cfg[4]))
+            emit(workload="rect_24576x16384x32768", path="bf16", slices=7, chosen_by=how,
+                 cfg=cfg, ms=ms, tflops=2 * M * N * K / ms / 1e9, stage_ms=st)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,10 +317,18 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--native-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end (host buffers) measurement")
     ap.add_argument("--size", type=int, default=N_SIZE,
                     help="n of the n x n x n product (multiple of 256; default 16384)")
+    ap.add_argument("--table", default=None,
+                    help="comma-separated workload numbers 0..3: print throughput rows of "
+                         "their configurations instead of the benchmark line")
     args = ap.parse_args()
     configure(args.size)
+    if args.table is not None:
+        run_table({int(x) for x in args.table.split(",") if x.strip()})
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -240,10 +373,12 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hs.stage_timing(True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
+    hs.stage_timing(False)
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
@@ -254,46 +389,30 @@ def main():
         ms = float(t.item())
     value = world * flops() / (ms * 1e-3) / 1e12
 
-    # per-kernel breakdown of the same path through the step entry points, with
-    # events on the launching stream; the diagonal products dominate
-    S = SPLIT["slices"]
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    dur = np.zeros(4)
-    nb = max(1, min(3, args.steps))
-    for _ in range(nb):
-        ev[0].record(stream)
-        e, f = hs.split_exponents(dA, dB)
-        ev[1].record(stream)
-        As, Bs = hs.split_slices(dA, dB, e, f, "bf16", S)
-        ev[2].record(stream)
-        D = hs.split_diagonals(As, Bs, n, n, n, "bf16", S, P=SPLIT["P"], Q=SPLIT["Q"],
-                               G=SPLIT["G"], b=SPLIT["b"], Bouter=SPLIT["Bouter"])
-        ev[3].record(stream)
-        hs.split_recombine(D, e, f, n, n, n, "bf16", S)
-        ev[4].record(stream)
-        torch.cuda.synchronize()
-        dur += np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
-    dur /= nb
+    # per-stage device time of the timed steps (events the library recorded
+    # around each kernel on the launching stream while the steps ran)
+    stage_ms, ncalls = hs.stage_times()
+    dur = np.array(stage_ms) / max(ncalls, 1)
     counters = hs.counters()
-    del As, Bs, D
-    torch.cuda.empty_cache()
+    S = SPLIT["slices"]
     npairs = S * (S + 1) // 2
     peaks = read_peaks()
     bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
     gemm_tflops = npairs * flops() / (dur[2] * 1e-3) / 1e12
-    roofline = {"bound": "tensor", "kernel": "bf16_diag_kernel",
+    roofline = {"bound": "tensor", "kernel": "bf16_pair_kernel",
                 "achieved": gemm_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": gemm_tflops / bf16_peak,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)",
                 "algorithmic": f"{npairs} bf16 products x 2 n^3 per launch",
-                "traffic": measured_traffic() if N_SIZE == 16384 and SPLIT["G"] == 256 else None,
+                "duration_ms": dur[2], "timed_launches": ncalls,
+                "traffic": measured_traffic() if N_SIZE == 16384 else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write)"}
     breakdown_ms = {"exponent_scan": dur[0], "slicing": dur[1], "diagonal_products": dur[2],
                     "recombination": dur[3]}
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         hA = dA.cpu().pin_memory()
         hB = dB.cpu().pin_memory()
         hC = torch.empty((n, n), dtype=torch.float64).pin_memory()
@@ -308,21 +427,12 @@ def main():
                "ms_per_step": te * 1e3}
         del hA, hB, hC
 
-    # accuracy of the measured product on sampled entries (compensated reference)
-    acc = {}
-    try:
-        from oracle import native, split
-        x = workloads.splitmix64(77, 0, 2048)
-        rows = np.unique((x[0::2] % np.uint64(n)).astype(np.int64))[:256]
-        cols = (x[1::2] % np.uint64(n)).astype(np.int64)[:rows.size]
-        Ah = dA[torch.as_tensor(rows, device="cuda")].cpu().numpy()
-        Bh = dB.cpu().numpy()
-        ref, absab = native.dot2_entries(Ah, Bh, np.arange(rows.size), cols)
-        got = dC[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")]
-        acc["split_max_rel_err"] = split.max_rel_error(got.cpu().numpy(), ref, absab)
-        acc["tolerance_2Ku"] = split.tolerance(n)
-    except Exception as ex:  # accuracy is reported, not required for timing
-        acc["error"] = repr(ex)
+    # sampled entries of the split result (accuracy is computed in the CPU leg)
+    x = workloads.splitmix64(77, 0, 2048)
+    rows = np.unique((x[0::2] % np.uint64(n)).astype(np.int64))[:256]
+    cols = (x[1::2] % np.uint64(n)).astype(np.int64)[:rows.size]
+    ir, ic = torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")
+    sampled = {"split": dC[ir, ic].cpu().numpy()}
 
     # native binary64 path on the same inputs
     native_out = None
@@ -337,6 +447,7 @@ def main():
             hs.gemm(dA, dB, out=dC2, **NATIVE)
         f1.record(stream)
         barrier()
+        hs.sync()
         nms = f0.elapsed_time(f1) / args.native_steps
         ntf = flops() / (nms * 1e-3) / 1e12
         dmma_peak = hs.peak("dmma", 4000) / 1e12
@@ -345,21 +456,13 @@ def main():
                                    "peak": dmma_peak, "unit": "TFLOP/s",
                                    "frac": ntf / dmma_peak,
                                    "peak_source": "measured by hsumma_peak(DMMA) in this run"}}
-        try:
-            got = dC2[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")]
-            acc["native_max_rel_err"] = split.max_rel_error(got.cpu().numpy(), ref, absab)
-        except Exception:
-            pass
+        sampled["native"] = dC2[ir, ic].cpu().numpy()
         del dC2
 
-    cpu = None
+    cpu, acc = None, {}
     if rank == 0 and not args.no_cpu:
-        Ah = dA[:256].cpu().numpy()
-        Bh = dB.cpu().numpy()
-        rate, rws, cores, dt = cpu_oracle_rate(Ah, Bh, target_s=12.0)
-        cpu = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": f"{rws} rows of C at n=16384 by the plain binary64 triple loop "
-                         f"({dt:.1f} s)"}
+        cpu, acc = cpu_leg(dA[:256].cpu().numpy(), dA[ir].cpu().numpy(), dB.cpu().numpy(),
+                           cols, sampled)
 
     if rank == 0:
         out = {

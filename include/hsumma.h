@@ -277,6 +277,30 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *d_A,
                   int64_t ldc, int mode, int policy, int *h_cfg, int *h_how,
                   void *stream);
 
+/* Kernel choice for the bf16 split path when a group is realised as a 2 x 1
+ * cluster (two vertically adjacent processors, e.g. G = p/2): enable = 1 runs
+ * its products on CTA pairs (tcgen05 cta_group::2: each SM holds its own A rows
+ * and half of the shared B panel, and the pair MMA reads both halves -- the
+ * in-group broadcast of Section III done by the tensor cores; the setting
+ * after hsumma_init); 0 runs the single-CTA kernel; a negative value only
+ * queries.  Returns the previous setting (0 or 1), or HSUMMA_ERR_NOT_INIT.
+ * Results are identical either way. */
+int hsumma_pair_kernel(int enable);
+
+/* ---- Stage timing ----
+ * Per-kernel device time of hsumma_gemm on the caller's stream, for measuring
+ * the path while it runs.  hsumma_stage_timing(1) clears the record and makes
+ * every following hsumma_gemm call record five CUDA events around its stages
+ * (on the call's stream); hsumma_stage_timing(0) stops recording.
+ * hsumma_stage_times waits for the recorded events and writes the summed
+ * milliseconds of the four stages over the recorded calls to h_ms[4] (split
+ * path: exponent scan, slicing, diagonal products, recombination; binary64:
+ * 0, 0, the product kernel, 0) and their number to *h_calls.  An event pair is
+ * read only once its call has finished; a call that failed part-way leaves
+ * unrecorded events and makes hsumma_stage_times fail. */
+int hsumma_stage_timing(int enable);
+int hsumma_stage_times(double *h_ms, int *h_calls);
+
 /* ---- Peak microbenchmarks (roofline denominators) ---- */
 
 typedef enum {

@@ -72,6 +72,9 @@ _SIGS = {
                          ctypes.c_float, ctypes.c_float, _vp], _i32),
     "hsumma_mlp_pick": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hsumma_mlp_load": ([_vp, _vp, _vp], _i32),
+    "hsumma_pair_kernel": ([_i32], _i32),
+    "hsumma_stage_timing": ([_i32], _i32),
+    "hsumma_stage_times": ([_vp, ctypes.POINTER(ctypes.c_int)], _i32),
     "hsumma_candidates": ([_i64, _i64, _i64, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_int)],
                           _i32),
     "hsumma_features": ([_i64, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
@@ -355,3 +358,28 @@ def load_model(theta, mean, std):
     if th.size != N_MLP_PARAMS or mu.size != 10 or sd.size != 10:
         raise ValueError("a cost model has 9089 parameters and 10 means and deviations")
     _check(lib().hsumma_mlp_load(th.ctypes.data, mu.ctypes.data, sd.ctypes.data))
+
+
+def stage_timing(enable: bool):
+    """Start (clearing the record) or stop recording per-stage events in
+    hsumma_gemm."""
+    _ensure_init()
+    _check(lib().hsumma_stage_timing(1 if enable else 0))
+
+
+def stage_times():
+    """(summed ms of the four stages over the recorded calls, number of calls)."""
+    ms = (ctypes.c_double * 4)()
+    n = ctypes.c_int()
+    _check(lib().hsumma_stage_times(ms, ctypes.byref(n)))
+    return list(ms), n.value
+
+
+def pair_kernel(enable=None) -> bool:
+    """Whether bf16 products of groups realised as 2 x 1 clusters run on CTA
+    pairs; with enable given, set it.  Returns the previous setting."""
+    _ensure_init()
+    r = lib().hsumma_pair_kernel(-1 if enable is None else int(bool(enable)))
+    if r < 0:
+        _check(r)
+    return bool(r)

@@ -4,7 +4,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <array>
 #include <mutex>
+#include <vector>
 
 #include "../../include/hsumma.h"
 #include "internal.h"
@@ -16,6 +18,26 @@ thread_local char g_err[512] = "";
 std::mutex g_mu;
 DeviceState g_state;
 bool g_init = false;
+
+// Stage timing (hsumma_stage_timing): five events per recorded hsumma_gemm
+// call, around exponent scan, slicing, products, recombination.
+std::mutex g_stage_mu;
+bool g_stage_on = false;
+std::vector<std::array<cudaEvent_t, 5>> g_stage_ev;
+size_t g_stage_used = 0;
+
+// Events for the next recorded call, or nullptr when timing is off.
+static cudaEvent_t *stage_slot() {
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  if (!g_stage_on) return nullptr;
+  if (g_stage_used == g_stage_ev.size()) {
+    std::array<cudaEvent_t, 5> ev;
+    for (auto &e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g_stage_ev.push_back(ev);
+  }
+  return g_stage_ev[g_stage_used++].data();
+}
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -91,10 +113,10 @@ bool encode_tmap_3d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
 static int launch_split_diagonals(const GridPlan &g, int kind, int S, const void *As,
                                   const void *Bs, int32_t *D, cudaStream_t s) {
   if (kind == HSUMMA_BF16_SLICES) {
-    // CTA pairs (two-SM MMAs) only on request (HSUMMA_BF16_PAIR=1): on this GPU
-    // the per-SM MMA rate is set by the number of issuing threads, not by the
-    // pair form, and the single-SM kernel with two issuers is faster
-    if (g.cm % 2 == 0 && g_state.bf16_pair) return launch_split_bf16_pair(g, S, As, Bs, D, s);
+    // groups of two vertically adjacent processors may run on CTA pairs
+    // (hsumma_pair_kernel); every other group shape on the single-CTA kernel
+    if (g.cm == 2 && g.cn == 1 && g_state.bf16_pair)
+      return launch_split_bf16_pair(g, S, As, Bs, D, s);
     return launch_split_bf16(g, S, As, Bs, D, s);
   }
   return launch_split_int8(g, S, As, Bs, D, s);
@@ -222,8 +244,7 @@ int hsumma_init(int device) {
   if (st != HSUMMA_OK) return st;
   if (l2 < lim) lim = l2;
   g_state.cluster_limit = lim;
-  const char *pair = getenv("HSUMMA_BF16_PAIR");
-  g_state.bf16_pair = pair && pair[0] == '1';
+  g_state.bf16_pair = true;   // CTA pairs for 2 x 1 groups (measured faster)
   if (g_state.cluster_limit > 16) g_state.cluster_limit = 16;
   if (g_state.cluster_limit < 1) g_state.cluster_limit = 1;
   e = cudaDeviceSynchronize();
@@ -241,6 +262,16 @@ void hsumma_finalize(void) {
   if (g_state.workspace) cudaFree(g_state.workspace);
   if (g_state.host_staging) cudaFree(g_state.host_staging);
   if (g_state.tune_buf) cudaFree(g_state.tune_buf);
+  if (g_state.copy_in) cudaStreamDestroy(g_state.copy_in);
+  if (g_state.copy_out) cudaStreamDestroy(g_state.copy_out);
+  {
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    for (auto &ev : g_stage_ev)
+      for (auto &e : ev) cudaEventDestroy(e);
+    g_stage_ev.clear();
+    g_stage_used = 0;
+    g_stage_on = false;
+  }
   forget_choices();
   g_state = DeviceState();
   g_init = false;
@@ -425,7 +456,13 @@ int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
         ldb = lb;
       }
     }
-    return launch_fp64_hsumma(g, A, lda, B, ldb, C, ldc, s);
+    cudaEvent_t *ev = stage_slot();
+    if (ev)
+      for (int i = 0; i < 3; ++i) cudaEventRecord(ev[i], s);
+    st = launch_fp64_hsumma(g, A, lda, B, ldb, C, ldc, s);
+    if (ev)
+      for (int i = 3; i < 5; ++i) cudaEventRecord(ev[i], s);
+    return st;
   }
 
   // split path: exponents, slices, exact diagonal sums, recombination
@@ -451,13 +488,154 @@ int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
   void *Bs = ws;
   ws += al(S * N * Kp * eb);
   int32_t *D = reinterpret_cast<int32_t *>(ws);
+  cudaEvent_t *ev = stage_slot();
+  if (ev) cudaEventRecord(ev[0], s);
   st = launch_split_exponents(M, N, K, A, lda, B, ldb, e_rows, f_cols, s);
   if (st != HSUMMA_OK) return st;
+  if (ev) cudaEventRecord(ev[1], s);
   st = launch_split_slices(M, N, K, A, lda, B, ldb, e_rows, f_cols, kind, S, As, Bs, s);
   if (st != HSUMMA_OK) return st;
+  if (ev) cudaEventRecord(ev[2], s);
   st = launch_split_diagonals(g, kind, S, As, Bs, D, s);
   if (st != HSUMMA_OK) return st;
-  return launch_split_recombine(M, N, K, kind, S, D, e_rows, f_cols, C, ldc, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  st = launch_split_recombine(M, N, K, kind, S, D, e_rows, f_cols, C, ldc, s);
+  if (ev) cudaEventRecord(ev[4], s);
+  return st;
+}
+
+// Row blocks of the pipelined host-buffer product: R blocks of P/R processor
+// rows each (R | P and R | I, so that every block keeps the product's blocks,
+// sub-tiles and in-group grid), at least 512 rows each, none empty; 1 if no R
+// in {4, 3, 2} fits.
+static int host_row_blocks(int64_t M, int P, int I, int64_t Mt) {
+  for (int R : {4, 3, 2}) {
+    if (P % R || I % R) continue;
+    const int64_t rows = (int64_t)(P / R) * Mt;
+    if (rows < 512 || (R - 1) * rows >= M) continue;
+    return R;
+  }
+  return 1;
+}
+
+// hsumma_gemm_host pipelined by row blocks: C_r = A_r B for the R row blocks
+// of A and C.  B is copied first on the copy-in stream, then the blocks of A;
+// the caller's stream scans and slices B once (split path), then per block
+// waits for its rows of A and runs the path on them; each finished block of C
+// is copied back on the copy-out stream while the next block computes.  Every
+// element is computed as in the unblocked product (row exponents are per row,
+// column exponents over the whole of B), so the result is the same bit for bit.
+static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA, int64_t lda,
+                               const double *hB, int64_t ldb, double *hC, int64_t ldc,
+                               const GridPlan &full, int R, int kind, int S, double *dA,
+                               double *dB, double *dC, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (!g_state.copy_in) e = cudaStreamCreateWithFlags(&g_state.copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !g_state.copy_out)
+    e = cudaStreamCreateWithFlags(&g_state.copy_out, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate(copy streams)");
+  cudaStream_t ci = g_state.copy_in, co = g_state.copy_out;
+  const int64_t rows = (int64_t)(full.P / R) * full.Mt;
+  // events: B copied, A block r copied, C block r computed, all copied back
+  std::vector<cudaEvent_t> ev(2 * R + 2, nullptr);
+  for (auto &x : ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  auto cleanup = [&]() {
+    for (auto &x : ev)
+      if (x) cudaEventDestroy(x);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaEventCreate(pipeline)");
+  }
+  cudaEvent_t evB = ev[0], evDone = ev[2 * R + 1];
+  auto fail = [&](cudaError_t err, const char *what) {
+    cleanup();
+    return cuda_fail(err, what);
+  };
+  auto fail_st = [&](int st) {
+    cleanup();
+    return st;
+  };
+
+  e = cudaMemsetAsync(g_state.d_counters, 0, 8 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return fail(e, "cudaMemsetAsync(counters)");
+  // copies in: B, then A block by block
+  e = cudaEventRecord(ev[1], s);  // the caller's earlier work on s comes first
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, ev[1], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(dB, ldb * 8, hB, ldb * 8, N * 8, K, cudaMemcpyHostToDevice, ci);
+  if (e == cudaSuccess) e = cudaEventRecord(evB, ci);
+  for (int r = 0; r < R && e == cudaSuccess; ++r) {
+    const int64_t r0 = r * rows, mr = (M - r0) < rows ? (M - r0) : rows;
+    e = cudaMemcpy2DAsync(dA + r0 * lda, lda * 8, hA + r0 * lda, lda * 8, K * 8, mr,
+                          cudaMemcpyHostToDevice, ci);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + r], ci);
+  }
+  if (e != cudaSuccess) return fail(e, "copy operands in");
+
+  // the split path: B's exponents and slices once; a block-sized workspace
+  int32_t *e_rows = nullptr, *f_cols = nullptr, *D = nullptr;
+  void *As = nullptr, *Bs = nullptr;
+  int st = HSUMMA_OK;
+  e = cudaStreamWaitEvent(s, evB, 0);
+  if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(B)");
+  if (kind != HSUMMA_FP64) {
+    st = ensure_workspace(split_ws_bytes(rows, N, K, kind, S));
+    if (st != HSUMMA_OK) return fail_st(st);
+    const int64_t Kp = ceil_div(K, 64) * 64;
+    const size_t eb = kind == HSUMMA_INT8_SLICES ? 1 : 2;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    uint8_t *ws = reinterpret_cast<uint8_t *>(g_state.workspace);
+    e_rows = reinterpret_cast<int32_t *>(ws);
+    ws += al(rows * 4);
+    f_cols = reinterpret_cast<int32_t *>(ws);
+    ws += al(N * 4);
+    As = ws;
+    ws += al(S * rows * Kp * eb);
+    Bs = ws;
+    ws += al(S * N * Kp * eb);
+    D = reinterpret_cast<int32_t *>(ws);
+    st = launch_split_exponents(0, N, K, nullptr, 1, dB, ldb, nullptr, f_cols, s);
+    if (st == HSUMMA_OK)
+      st = launch_split_slices(0, N, K, nullptr, 1, dB, ldb, nullptr, f_cols, kind, S, nullptr,
+                               Bs, s);
+    if (st != HSUMMA_OK) return fail_st(st);
+  }
+  for (int r = 0; r < R; ++r) {
+    const int64_t r0 = r * rows, mr = (M - r0) < rows ? (M - r0) : rows;
+    GridPlan g;
+    st = make_plan(mr, N, K, full.P / R, full.Q, full.G / R, full.b, full.Bo, kind, &g);
+    if (st != HSUMMA_OK) return fail_st(st);
+    e = cudaStreamWaitEvent(s, ev[1 + r], 0);
+    if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(A block)");
+    const double *Ar = dA + r0 * lda;
+    double *Cr = dC + r0 * ldc;
+    if (kind == HSUMMA_FP64) {
+      st = launch_fp64_hsumma(g, Ar, lda, dB, ldb, Cr, ldc, s);
+    } else {
+      st = launch_split_exponents(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, s);
+      if (st == HSUMMA_OK)
+        st = launch_split_slices(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, kind, S, As,
+                                 nullptr, s);
+      if (st == HSUMMA_OK) st = launch_split_diagonals(g, kind, S, As, Bs, D, s);
+      if (st == HSUMMA_OK)
+        st = launch_split_recombine(mr, N, K, kind, S, D, e_rows, f_cols, Cr, ldc, s);
+    }
+    if (st != HSUMMA_OK) return fail_st(st);
+    cudaEvent_t done = ev[1 + R + r];
+    e = cudaEventRecord(done, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(co, done, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(hC + r0 * ldc, ldc * 8, Cr, ldc * 8, N * 8, mr,
+                            cudaMemcpyDeviceToHost, co);
+    if (e != cudaSuccess) return fail(e, "copy a block of C out");
+  }
+  e = cudaEventRecord(evDone, co);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, evDone, 0);
+  if (e != cudaSuccess) return fail(e, "join copy streams");
+  cleanup();  // destroying recorded events is safe: they are released once complete
+  return hsumma_sync(reinterpret_cast<void *>(s));
 }
 
 int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t lda,
@@ -488,19 +666,36 @@ int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t 
   double *dA = reinterpret_cast<double *>(base);
   double *dB = reinterpret_cast<double *>(base + bA);
   double *dC = reinterpret_cast<double *>(base + bA + bB);
+  // pipelined by row blocks when the configuration is given and allows it
+  const bool given = P || Q || G || b || Bouter;
+  if (given && M > 0 && N > 0 && K > 0) {
+    int kind, S;
+    st = split_kind_and_S(mode, &kind, &S);
+    if (st != HSUMMA_OK) return st;
+    GridPlan full;
+    st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, &full);
+    if (st != HSUMMA_OK) return st;
+    const bool exact_ok = kind == HSUMMA_FP64 || (double)S * (double)K * 16384.0 < 9.0e18;
+    const bool tma_ok = kind != HSUMMA_FP64 || (tma_ready(dA, lda) && tma_ready(dB, ldb) &&
+                                                (lda % 2) == 0);
+    const int R = host_row_blocks(M, P, full.I, full.Mt);
+    if (R > 1 && exact_ok && tma_ok)
+      return gemm_host_pipelined(M, N, K, hA, lda, hB, ldb, hC, ldc, full, R, kind, S, dA, dB,
+                                 dC, s);
+  }
   cudaError_t e;
   if (M && K) {
-    e = cudaMemcpyAsync(dA, hA, (size_t)M * lda * 8, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpy2DAsync(dA, lda * 8, hA, lda * 8, K * 8, M, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(A)");
   }
   if (K && N) {
-    e = cudaMemcpyAsync(dB, hB, (size_t)K * ldb * 8, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpy2DAsync(dB, ldb * 8, hB, ldb * 8, N * 8, K, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(B)");
   }
   st = hsumma_gemm(M, N, K, dA, lda, dB, ldb, dC, ldc, P, Q, G, b, Bouter, mode, stream);
   if (st != HSUMMA_OK) return st;
   if (M && N) {
-    e = cudaMemcpyAsync(hC, dC, (size_t)M * ldc * 8, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpy2DAsync(hC, ldc * 8, dC, ldc * 8, N * 8, M, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(C)");
   }
   return hsumma_sync(stream);
@@ -661,6 +856,49 @@ int hsumma_peak(int kind, int64_t work, double *rate) {
     return HSUMMA_ERR_ARG;
   }
   return run_peak(kind, work, rate);
+}
+
+int hsumma_stage_timing(int enable) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  g_stage_on = enable != 0;
+  if (g_stage_on) g_stage_used = 0;
+  return HSUMMA_OK;
+}
+
+int hsumma_stage_times(double *ms, int *calls) {
+  if (!ms || !calls) {
+    set_error("null output pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  for (int i = 0; i < 4; ++i) ms[i] = 0.0;
+  for (size_t c = 0; c < g_stage_used; ++c) {
+    auto &ev = g_stage_ev[c];
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize(stage)");
+    for (int i = 0; i < 4; ++i) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime(stage)");
+      ms[i] += t;
+    }
+  }
+  *calls = (int)g_stage_used;
+  return HSUMMA_OK;
+}
+
+int hsumma_pair_kernel(int enable) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  const int was = g_state.bf16_pair ? 1 : 0;
+  if (enable >= 0) g_state.bf16_pair = enable != 0;
+  return was;
 }
 
 }  // extern "C"

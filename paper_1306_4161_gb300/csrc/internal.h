@@ -29,9 +29,11 @@ struct DeviceState {
   size_t workspace_bytes = 0;
   void *host_staging = nullptr;              // device buffers of hsumma_gemm_host
   size_t host_staging_bytes = 0;
-  bool bf16_pair = false;                    // HSUMMA_BF16_PAIR=1: CTA-pair bf16 kernel
+  bool bf16_pair = false;                    // bf16 products of 2 x 1 groups on CTA pairs
   void *tune_buf = nullptr;                  // model scoring inputs of hsumma_choose
   size_t tune_bytes = 0;
+  cudaStream_t copy_in = nullptr;            // hsumma_gemm_host's copy streams
+  cudaStream_t copy_out = nullptr;
 };
 
 DeviceState &state();

@@ -1,25 +1,29 @@
-// Split-precision HSUMMA, step 3 with bf16 slices, CTA-pair variant: the same
-// exact diagonal products as split_bf16.cu, with every MMA spanning two SMs
+// Split-precision HSUMMA, step 3 with bf16 slices on CTA pairs: the same exact
+// diagonal sums as split_bf16.cu, for groups of two vertically adjacent
+// processors (in-group grid 2 x 1), with every MMA spanning the pair's two SMs
 // (tcgen05 cta_group::2, 256 x 256 x 16).
 //
-// The group cluster is laid out with its x dimension along processor rows, so
-// the hardware's CTA pairs (cluster ranks 2k, 2k+1) are two vertically adjacent
-// processors of one group: they need the same B columns and different A rows.
-// Each CTA of a pair loads its own 128 rows of A (multicast along its cluster
-// row, the in-group row broadcast) and one half (128 columns) of the pair's
-// 256-column B panel (multicast to the CTAs of its cluster column that hold
-// the same half, the in-group column broadcast); the pair's MMA reads both
-// halves of B from the two SMs, so each SM's shared memory holds 32 KB per
-// k-stage instead of 48 KB and the pipeline is 6 stages deep.
+// The two processors of a group need the same 256 B columns and different A
+// rows.  Each CTA loads its own 128 rows of A and one half (128 columns) of the
+// group's B panel; the pair MMA reads both halves from the two SMs, which is
+// the in-group column broadcast of Section III done by the tensor cores
+// instead of a copy.  Each SM therefore holds 32 KB per k-stage (48 KB in the
+// single-CTA kernel) and the ring is 6 stages deep: about 1.6 times the work
+// in flight per byte of shared memory, and a third less traffic from L2.
 //
-// Synchronisation: every CTA's "full" barrier counts the bytes of its own
-// stage; the second CTA of a pair forwards its completion to the first
-// ("pair full"), whose single thread issues the pair MMAs; the MMA completion
-// is committed to the "empty" barriers of every CTA of the cluster (a stage is
-// refilled once every pair of the cluster has consumed it) and, per
-// accumulator chunk, to both CTAs' "acc full" barriers.  Both CTAs drain their
-// own tensor memory (128 rows x 256 columns) exactly as in split_bf16.cu and
-// release the accumulator to the first CTA of the pair.
+// Synchronisation (no forwarding step): the first CTA of the pair ("leader")
+// expects the bytes of both CTAs on its own "full" barrier, and the second
+// CTA's copies count their bytes on that barrier directly (cta_group::2 bulk
+// tensor copies).  Two issuing threads of the leader take the k-stages of
+// parity 0 and 1 into separate accumulators (tensor-memory columns 0..255 and
+// 256..511 of both SMs), with the staggered chunk ends of split_bf16.cu; each
+// stage's MMA completion releases the stage in both CTAs, and each chunk end
+// hands the accumulator to the drain warps of both CTAs, which return it to
+// the leader.  Every wait is bounded (4 s) and ends in an error status.
+//
+// Roles (384 threads per CTA): warp 0 issues the copies, warps 1 and 2 issue
+// the MMAs (leader only; warp 1 of each CTA owns its tensor memory), warp 3
+// idles, warps 4..11 drain their CTA's 128 rows into exact int32 planes.
 #include "internal.h"
 #include "ptx.cuh"
 #include "tc05.cuh"
@@ -32,16 +36,18 @@ constexpr int TM = 128, TN = 256, HN = TN / 2, BKS = 64, STAGES = 6;
 constexpr int A_BYTES = TM * BKS * 2, BH_BYTES = HN * BKS * 2;
 constexpr int STAGE_BYTES = A_BYTES + BH_BYTES;
 constexpr int CH = 16;                 // k-stages per accumulator chunk (1024 products)
-constexpr int NEPI = 8;
-constexpr int NTHREADS = (2 + NEPI) * 32;
+constexpr int NEPI = 8;                // draining warps per CTA
+constexpr int NTHREADS = (4 + NEPI) * 32;
+constexpr int SEGST = 127 * CH;        // stages per int32 segment
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC2 = idesc_bf16_f32(2 * TM, TN);
+constexpr uint16_t PAIR = 3;           // both CTAs of the cluster
 
 struct PairParams {
   int32_t *D;
   int64_t M, N, K, Kpad, Mt, Nt, Kq, Kp;
-  int P, Q, cm, cn, nsub_m, nsub_n, Bo, S, nkb, seg_chunks, nseg;
+  int P, Q, nsub_m, nsub_n, Bo, S, nkb, nseg;
   unsigned long long *counters;
   int *status;
 };
@@ -52,27 +58,32 @@ __device__ __forceinline__ int64_t span(int64_t lo, int64_t hi, int64_t a, int64
 }
 
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
-                                              volatile int *abort_flag, bool cluster_scope) {
+                                              volatile int *abort_flag) {
   const unsigned long long t0 = globaltimer();
   while (true) {
-    if (cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))
-      return true;
+    if (mbar_try_wait_cluster(bar, parity)) return true;
     if (*abort_flag) return false;
     if (globaltimer() - t0 > kWaitLimitNs) return false;
   }
 }
 
-// cluster tile L -> processor row r and column c of this CTA (tiles walked
-// down columns of 8 cluster rows); ry, rx: the CTA's row and column in the
-// group cluster
-__device__ __forceinline__ void tile_proc(int L, int ncx, int ncy, int cm, int cn, int ry,
-                                          int rx, int *r, int *c) {
+// the chunk schedule of split_bf16.cu: issuer 0 closes a chunk every 16 of its
+// stages, issuer 1 after 8 and then every 16; both at the segment's last stage
+__device__ __forceinline__ bool chunk_end(int local, int seg_len) {
+  const int c = (local >> 1) + 1;
+  if (local + 2 >= seg_len) return true;
+  return (local & 1) ? ((c + 8) % CH == 0) : (c % CH == 0);
+}
+
+// group tile L -> processor row r (of this CTA) and column c: tiles walked
+// down columns of 8 group rows
+__device__ __forceinline__ void tile_proc(int L, int ncx, int ncy, int ry, int *r, int *c) {
   const int rows = 8;
   const int group = L / (rows * ncx);
   const int in_group = min(rows, ncy - group * rows);
   const int idx = L - group * rows * ncx;
-  *r = (group * rows + idx % in_group) * cm + ry;
-  *c = (idx / in_group) * cn + rx;
+  *r = (group * rows + idx % in_group) * 2 + ry;
+  *c = idx / in_group;
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -84,35 +95,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-  uint64_t *full = bars, *empty = bars + STAGES, *pfull = bars + 2 * STAGES;
-  uint64_t *acc_full = bars + 3 * STAGES, *acc_empty = acc_full + 2;
+  uint64_t *full = bars, *empty = bars + STAGES;
+  uint64_t *acc_full = bars + 2 * STAGES, *acc_empty = acc_full + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cm = p.cm, cn = p.cn;
-  // cluster x runs along processor rows: rank = ry + rx cm, pairs differ in ry's low bit
-  const int ry = (int)cluster_ctaid_x(), rx = (int)cluster_ctaid_y();
-  const int rank = ry + rx * cm;
-  const bool leader = (ry & 1) == 0;
-  const int lead_rank = rank & ~1;
-  const int half = ry & 1;                 // which 128 columns of B this CTA holds
-  const int hw = cm / 2;                   // CTAs of a cluster column holding one half
-  const int hj = ry >> 1;                  // index among them
-  uint16_t a_mask = 0, b_mask = 0;
-  for (int x = 0; x < cn; ++x) a_mask |= (uint16_t)(1u << (ry + x * cm));
-  for (int y = half; y < cm; y += 2) b_mask |= (uint16_t)(1u << (y + rx * cm));
-  const uint16_t all_mask = (uint16_t)((1u << (cm * cn)) - 1u);
-  const uint16_t pair_mask = (uint16_t)(3u << lead_rank);
-  const int ncx = p.Q / cn, ncy = p.P / cm, ntiles = ncx * ncy;
-  const int ncl = (int)gridDim.x / cm, cid = (int)blockIdx.x / cm;
+  const int ry = (int)cluster_ctaid_x();          // 0: leader, 1: second CTA of the pair
+  const bool leader = ry == 0;
+  const int ncx = p.Q, ncy = p.P / 2, ntiles = ncx * ncy;
+  const int ncl = (int)gridDim.x / 2, cid = (int)blockIdx.x / 2;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), (uint32_t)(cm * cn / 2));
-      mbar_init(smem_u32(&pfull[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
@@ -136,85 +134,79 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int S = p.S, nkb = p.nkb;
   const int64_t nout = (p.Kpad + p.Bo - 1) / p.Bo;
-  const bool a_contig = (TM / 8) % cn == 0, b_contig = (HN / 8) % hw == 0;
-  const int a_box = a_contig ? TM / cn : 8, b_box = b_contig ? HN / hw : 8;
 
   if (warp == 0) {
-    // ---------------- copies ----------------
+    // ---------------- copies (both CTAs) ----------------
     if (lane == 0) {
-      unsigned long long a_ld = 0, a_dl = 0, b_ld = 0, b_dl = 0, pf = 0, nops = 0;
+      unsigned long long a_ld = 0, b_ld = 0, pf = 0, nops = 0;
       uint32_t stage = 0, phase = 0;
       bool ok = true;
       for (int L = cid; L < ntiles && ok; L += ncl) {
         int r, c;
-        tile_proc(L, ncx, ncy, cm, cn, ry, rx, &r, &c);
+        tile_proc(L, ncx, ncy, ry, &r, &c);
         const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
         const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
         for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
           const int64_t m0 = row_lo + (int64_t)mi * TM;
           for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
             const int64_t n0 = col_lo + (int64_t)ni * TN;
-            const int64_t nh = n0 + half * HN;
+            const int64_t nh = n0 + ry * HN;
             for (int d = 2; d <= S + 1 && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
                 for (int kb = 0; kb < nkb; ++kb) {
                   const int64_t k0 = (int64_t)kb * BKS;
                   if (k0 % p.Bo == 0) {
+                    // owners stage the next outer panel into L2, one outer block
+                    // ahead without gaps (the rule of split_bf16.cu)
                     const int64_t o = k0 / p.Bo;
-                    for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
+                    int ns = s + 1, nd = d;
+                    if (ns >= nd) { ++nd; ns = 1; }
+                    const bool first = (d == 2 && s == 1 && o == 0);
+                    for (int w = first ? 0 : 1; w <= 1; ++w) {
+                      int64_t q = o + w;
+                      int ps = s, pt = t;
+                      if (q >= nout) {
+                        if (nd > S + 1) break;
+                        q = 0;
+                        ps = ns;
+                        pt = nd - ns;
+                      }
                       const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
                       if (c == (int)imin64(p.Q - 1, kq / p.Kq)) {
                         for (int64_t kk = kq; kk < kend; kk += BKS)
-                          tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, s - 1);
+                          tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, ps - 1);
                         pf += 1;
                       }
-                      // one B panel per processor column: its first row owns it
                       if (r == (int)imin64(p.P - 1, kq / p.Kp)) {
                         for (int64_t kk = kq; kk < kend; kk += BKS)
-                          tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, t - 1);
+                          tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, pt - 1);
                         pf += 1;
                       }
                     }
                   }
-                  if (!wait_or_abort(smem_u32(&empty[stage]), phase ^ 1u, &abort_flag, true)) {
+                  if (!wait_or_abort(smem_u32(&empty[stage]), phase ^ 1u, &abort_flag)) {
                     if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteEmpty);
                     abort_flag = 1;
                     ok = false;
                     break;
                   }
-                  const uint32_t fb = smem_u32(&full[stage]);
-                  mbar_arrive_expect_tx(fb, STAGE_BYTES);
-                  const uint32_t a_base = smem_u32(smem + stage * STAGE_BYTES);
-                  const uint32_t b_base = a_base + A_BYTES;
+                  const uint32_t a_dst = smem_u32(smem + stage * STAGE_BYTES);
+                  const uint32_t b_dst = a_dst + A_BYTES;
+                  if (leader) {
+                    const uint32_t fb = smem_u32(&full[stage]);
+                    mbar_arrive_expect_tx(fb, 2 * STAGE_BYTES);
+                    tma_load_3d(a_dst, &tmA, (int32_t)k0, (int32_t)m0, s - 1, fb);
+                    tma_load_3d(b_dst, &tmB, (int32_t)k0, (int32_t)nh, t - 1, fb);
+                  } else {
+                    const uint32_t fb = cluster_addr(smem_u32(&full[stage]), 0);
+                    tma_load_3d_pair(a_dst, &tmA, (int32_t)k0, (int32_t)m0, s - 1, fb);
+                    tma_load_3d_pair(b_dst, &tmB, (int32_t)k0, (int32_t)nh, t - 1, fb);
+                  }
                   const int64_t kc = span(0, p.K, k0, k0 + BKS);
-                  for (int i = a_contig ? rx * (a_box / 8) : rx; i < TM / 8;
-                       i += a_contig ? TM / 8 : cn) {
-                    const int64_t ar = m0 + (int64_t)i * 8;
-                    const uint32_t dst = a_base + i * 8 * 128;
-                    if (cn > 1)
-                      tma_load_3d_mc(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb, a_mask);
-                    else
-                      tma_load_3d(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb);
-                    const int64_t ca = span(row_lo, row_hi, ar, ar + a_box) * kc;
-                    a_ld += ca;
-                    a_dl += ca * cn;
-                    nops += 1;
-                  }
-                  for (int i = b_contig ? hj * (b_box / 8) : hj; i < HN / 8;
-                       i += b_contig ? HN / 8 : hw) {
-                    const int64_t br = nh + (int64_t)i * 8;
-                    const uint32_t dst = b_base + i * 8 * 128;
-                    if (hw > 1)
-                      tma_load_3d_mc(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb, b_mask);
-                    else
-                      tma_load_3d(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb);
-                    // every loaded half is read by both CTAs of each pair it reaches
-                    const int64_t cb = span(col_lo, col_hi, br, br + b_box) * kc;
-                    b_ld += cb;
-                    b_dl += cb * cm;
-                    nops += 1;
-                  }
+                  a_ld += span(row_lo, row_hi, m0, m0 + TM) * kc;
+                  b_ld += span(col_lo, col_hi, nh, nh + HN) * kc;
+                  nops += 2;
                   if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
               }
@@ -222,57 +214,55 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       }
+      // tail: every release of the last stages has landed before leaving
       for (int i = 0; i < STAGES && ok; ++i) {
-        if (!wait_or_abort(smem_u32(&empty[stage]), phase ^ 1u, &abort_flag, true)) {
+        if (!wait_or_abort(smem_u32(&empty[stage]), phase ^ 1u, &abort_flag)) {
           if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteEmpty);
           abort_flag = 1;
           ok = false;
         }
         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
       }
+      // A rows reach this CTA only; each half of B reaches both CTAs' products
       atomicAdd(&p.counters[0], a_ld);
-      atomicAdd(&p.counters[1], a_dl);
+      atomicAdd(&p.counters[1], a_ld);
       atomicAdd(&p.counters[2], b_ld);
-      atomicAdd(&p.counters[3], b_dl);
+      atomicAdd(&p.counters[3], 2 * b_ld);
       atomicAdd(&p.counters[4], pf);
       atomicAdd(&p.counters[5], nops);
     }
-  } else if (warp == 1) {
+  } else if ((warp == 1 || warp == 2) && leader) {
+    // ---------------- pair MMAs: issuer `me` takes the stages of parity me ----------------
     if (lane == 0) {
-      uint32_t stage = 0, phase = 0, gc = 0;
+      const int me = warp - 1;
+      uint32_t gst = 0, nchunk = 0;
+      bool in_chunk = false;
+      const uint32_t dt = tmem_base + (uint32_t)(me * TN);
       bool ok = true;
       for (int L = cid; L < ntiles && ok; L += ncl) {
         for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
           for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
             for (int d = 2; d <= S + 1 && ok; ++d) {
               const int nst = (d - 1) * nkb;
-              for (int st = 0; st < nst; ++st) {
-                if (!leader) {
-                  // ---- second CTA of the pair: forward "stage filled" to the first
-                  if (!wait_or_abort(smem_u32(&full[stage]), phase, &abort_flag, false)) {
-                    if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteFull);
-                    abort_flag = 1;
-                    ok = false;
-                    break;
-                  }
-                  mbar_arrive_cluster(smem_u32(&pfull[stage]), (uint32_t)lead_rank);
-                  if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-                  continue;
-                }
-                // ---- first CTA of the pair: issue the pair MMAs
-                const uint32_t buf = gc & 1u;
-                if (st % CH == 0) {
-                  if (!wait_or_abort(smem_u32(&acc_empty[buf]), ((gc >> 1) & 1u) ^ 1u,
-                                     &abort_flag, true)) {
+              for (int st = 0; st < nst; ++st, ++gst) {
+                if ((st & 1) != me) continue;
+                const int seg_lo = st - st % SEGST;
+                const int seg_len = min(nst, seg_lo + SEGST) - seg_lo;
+                const int local = st - seg_lo;
+                bool first = false;
+                if (!in_chunk) {
+                  if (!wait_or_abort(smem_u32(&acc_empty[me]), (nchunk & 1u) ^ 1u, &abort_flag)) {
                     if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteAccEmpty);
                     abort_flag = 1;
                     ok = false;
                     break;
                   }
                   tc_fence_after();
+                  in_chunk = true;
+                  first = true;
                 }
-                if (!wait_or_abort(smem_u32(&full[stage]), phase, &abort_flag, false) ||
-                    !wait_or_abort(smem_u32(&pfull[stage]), phase, &abort_flag, true)) {
+                const uint32_t stage = gst % STAGES, phase = (gst / STAGES) & 1u;
+                if (!wait_or_abort(smem_u32(&full[stage]), phase, &abort_flag)) {
                   if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteFull);
                   abort_flag = 1;
                   ok = false;
@@ -281,17 +271,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_after();
                 const uint32_t a_addr = smem_u32(smem + stage * STAGE_BYTES);
                 const uint32_t b_addr = a_addr + A_BYTES;
-                const uint32_t dt = tmem_base + buf * TN;
 #pragma unroll
                 for (int k = 0; k < BKS / 16; ++k) {
                   mma2_bf16(dt, sdesc_k128(a_addr + k * 32), sdesc_k128(b_addr + k * 32), IDESC2,
-                            (st % CH != 0 || k > 0) ? 1u : 0u);
+                            (first && k == 0) ? 0u : 1u);
                 }
-                mma2_commit_mc(smem_u32(&empty[stage]), all_mask);
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-                if (st % CH == CH - 1 || st == nst - 1) {
-                  mma2_commit_mc(smem_u32(&acc_full[buf]), pair_mask);
-                  ++gc;
+                mma2_commit_mc(smem_u32(&empty[stage]), PAIR);
+                if (chunk_end(local, seg_len)) {
+                  mma2_commit_mc(smem_u32(&acc_full[me]), PAIR);
+                  ++nchunk;
+                  in_chunk = false;
                 }
               }
             }
@@ -299,15 +288,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-  } else {
-    // ---------------- drain: tensor memory -> exact int32 planes ----------------
-    const int q = warp & 3;
-    const int h = (warp - 2) >> 2;
-    uint32_t gc = 0;
+  } else if (warp >= 4) {
+    // ---------------- drain (both CTAs): this SM's 128 rows -> exact int32 planes ----------------
+    const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+    const int h = (warp - 4) >> 2;          // column half of the 256-column tile
+    uint32_t nchunk0 = 0, nchunk1 = 0;
     bool ok = true;
     for (int L = cid; L < ntiles && ok; L += ncl) {
       int r, c;
-      tile_proc(L, ncx, ncy, cm, cn, ry, rx, &r, &c);
+      tile_proc(L, ncx, ncy, ry, &r, &c);
       const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
       const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
       for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
@@ -316,22 +305,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t n0 = col_lo + (int64_t)ni * TN + h * 128;
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
           for (int d = 2; d <= S + 1 && ok; ++d) {
-            const int nch = ((d - 1) * nkb + CH - 1) / CH;
-            for (int seg = 0; seg * p.seg_chunks < nch && ok; ++seg) {
-              const int c1 = min(nch, (seg + 1) * p.seg_chunks);
+            const int nst = (d - 1) * nkb;
+            for (int seg = 0; seg * SEGST < nst && ok; ++seg) {
+              const int seg_len = min(nst, (seg + 1) * SEGST) - seg * SEGST;
               int acc[128];
 #pragma unroll
               for (int i = 0; i < 128; ++i) acc[i] = 0;
-              for (int ch = seg * p.seg_chunks; ch < c1; ++ch) {
-                const uint32_t buf = gc & 1u;
-                const bool got =
-                    wait_or_abort(smem_u32(&acc_full[buf]), (gc >> 1) & 1u, &abort_flag, true);
+              for (int local = 0; local < seg_len; ++local) {
+                if (!chunk_end(local, seg_len)) continue;
+                const int who = local & 1;
+                const uint32_t par = who ? (nchunk1 & 1u) : (nchunk0 & 1u);
+                // warp-uniform decision before the warp-collective tcgen05.ld
+                const bool got = wait_or_abort(smem_u32(&acc_full[who]), par, &abort_flag);
                 if (!__all_sync(0xffffffffu, got)) {
                   ok = false;
                   break;
                 }
                 tc_fence_after();
-                const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + buf * TN + h * 128;
+                const uint32_t ta =
+                    tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(who * TN) + h * 128;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                   uint32_t v[16];
@@ -343,8 +335,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(smem_u32(&acc_empty[buf]), (uint32_t)lead_rank);
-                ++gc;
+                if (lane == 0) mbar_arrive_cluster(smem_u32(&acc_empty[who]), 0u);
+                if (who) ++nchunk1; else ++nchunk0;
               }
               if (!ok) break;
               if (row < row_hi) {
@@ -373,8 +365,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (abort_flag) bounded_sleep(2000000ull);
-  // both CTAs of every pair are done with tensor memory before it is released
+  if (abort_flag) bounded_sleep(2000000ull);   // in-flight copies and MMAs land
+  // both CTAs of the pair are done with tensor memory before it is released
   cluster_sync();
   if (warp == 1) {
     tc_fence_after();
@@ -387,18 +379,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void *Bs, int32_t *D,
                            cudaStream_t s) {
+  if (g.cm != 2 || g.cn != 1 || g.P % 2) {
+    set_error("the CTA-pair kernel needs groups realised as 2 x 1 clusters");
+    return HSUMMA_ERR_ARG;
+  }
   const int64_t Kpad = ceil_div(g.K, 64) * 64;
-  const int hw = g.cm / 2;
-  const int a_box = (TM / 8) % g.cn == 0 ? TM / g.cn : 8;
-  const int b_box = (HN / 8) % hw == 0 ? HN / hw : 8;
   const auto BF16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap tA, tB, tApf, tBpf;
-  if (!encode_tmap_3d(&tA, BF16, 2, As, Kpad, g.M, S, BKS, a_box, CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_tmap_3d(&tB, BF16, 2, Bs, Kpad, g.N, S, BKS, b_box, CU_TENSOR_MAP_SWIZZLE_128B) ||
+  if (!encode_tmap_3d(&tA, BF16, 2, As, Kpad, g.M, S, BKS, TM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_tmap_3d(&tB, BF16, 2, Bs, Kpad, g.N, S, BKS, HN, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !encode_tmap_3d(&tApf, BF16, 2, As, Kpad, g.M, S, BKS, TM, CU_TENSOR_MAP_SWIZZLE_NONE) ||
       !encode_tmap_3d(&tBpf, BF16, 2, Bs, Kpad, g.N, S, BKS, TN, CU_TENSOR_MAP_SWIZZLE_NONE))
     return HSUMMA_ERR_ARG;
-  PairParams p;
+  PairParams p{};
   p.D = D;
   p.M = g.M;
   p.N = g.N;
@@ -410,42 +403,32 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   p.Kp = g.Kp;
   p.P = g.P;
   p.Q = g.Q;
-  p.cm = g.cm;
-  p.cn = g.cn;
   p.nsub_m = (int)ceil_div(g.Mt, TM);
   p.nsub_n = (int)ceil_div(g.Nt, TN);
   p.Bo = g.Bo;
   p.S = S;
   p.nkb = (int)(Kpad / BKS);
-  p.seg_chunks = kSegChunks;
-  p.nseg = split_planes(g.K, S);
+  p.nseg = split_planes(g.K, S, HSUMMA_BF16_SLICES);
   p.counters = state().d_counters;
   p.status = state().d_status;
   cudaError_t e = cudaFuncSetAttribute(bf16_pair_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-  if (g.cm * g.cn > 8) {
-    e = cudaFuncSetAttribute(bf16_pair_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                             1);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
-  }
-  // one cluster per cluster tile; cluster x along processor rows
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair smem)");
   cudaLaunchConfig_t cfg = {};
-  const int ntiles = (g.Q / g.cn) * (g.P / g.cm);
-  cfg.gridDim = dim3((unsigned)(ntiles * g.cm), (unsigned)g.cn, 1);
+  const int ntiles = (g.P / 2) * g.Q;
+  cfg.gridDim = dim3((unsigned)(2 * ntiles), 1, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = (unsigned)g.cm;
-  at[0].val.clusterDim.y = (unsigned)g.cn;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, bf16_pair_kernel, tA, tB, tApf, tBpf, p);
-  if (e != cudaSuccess) return cuda_fail(e, "launch bf16_pair_kernel");
-  return HSUMMA_OK;
+  return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "launch bf16 pair kernel");
 }
 
 }  // namespace hs

@@ -168,6 +168,26 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *tm, int32_
       : "memory");
 }
 
+// shared::cluster address of the same shared-memory offset in CTA `rank` of
+// the cluster
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t smem_addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
+  return r;
+}
+
+// 3-D tile load into this CTA's shared memory whose bytes are counted on an
+// mbarrier of the CTA pair (cta_group::2: `bar` is a shared::cluster address
+// in this CTA or in its peer)
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const void *tm, int32_t x,
+                                                 int32_t y, int32_t z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const void *tm, int32_t x,
                                                int32_t y, int32_t z, uint32_t bar,
                                                uint16_t mask) {

@@ -242,29 +242,101 @@ def test_odd_leading_dimensions():
     assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 2, "bf16"))
 
 
-@pytest.mark.parametrize("M,N,K,P,Q,G,S", [
-    (256, 256, 1024, 2, 1, 1, 3),       # one CTA pair
-    (512, 512, 512, 4, 2, 1, 2),        # 4 x 2 cluster: B halves multicast to 2 CTAs
-    (600, 300, 640, 6, 1, 1, 2),        # 6 x 1 cluster: 8-row pieces for the B halves
-    (520, 1100, 700, 4, 4, 4, 3),       # 2 x 2 groups, ragged blocks and sub-tiles
+@pytest.mark.parametrize("M,N,K,P,Q,G,S,Bo", [
+    (256, 256, 1024, 2, 1, 1, 3, 128),        # one CTA pair
+    (600, 700, 640, 4, 3, 6, 2, 128),         # 2 x 1 groups, ragged blocks and sub-tiles
+    (1030, 1100, 700, 8, 4, 16, 3, 1024),     # 2 x 1 groups, B longer than K
+    (512, 2048, 4096, 2, 4, 4, 4, 256),       # several chunks per diagonal
 ])
-def test_bf16_pair_kernel_exact(M, N, K, P, Q, G, S):
-    # group clusters with an even number of rows run the CTA-pair kernel
+def test_bf16_pair_kernel_exact(M, N, K, P, Q, G, S, Bo):
+    # groups realised as 2 x 1 clusters run on CTA pairs when asked
     hs = lib_ready()
     torch = torch_cuda()
     I, J, cm, cn = hs.group_shape(P, Q, G)
-    assert cm % 2 == 0
+    assert (cm, cn) == (2, 1)
     A, B, dA, dB = pair(M, N, K, 29, "wide", "uniform")
     e, f = hs.split_exponents(dA, dB)
     As, Bs = hs.split_slices(dA, dB, e, f, "bf16", S)
-    D = hs.split_diagonals(As, Bs, M, N, K, "bf16", S, P=P, Q=Q, G=G, b=64, Bouter=128)
-    hs.sync()
+    was = hs.pair_kernel(True)
+    try:
+        D = hs.split_diagonals(As, Bs, M, N, K, "bf16", S, P=P, Q=Q, G=G, b=64, Bouter=Bo)
+        hs.sync()
+        c = hs.counters()
+    finally:
+        hs.pair_kernel(was)
     _, parts = split.split_gemm(A, B, S, "bf16", return_parts=True)
     Dg = D.to(torch.int64).sum(dim=1).cpu().numpy()
     for d in range(2, S + 2):
         assert np.array_equal(Dg[d - 2], parts["D"][d]), d
     npairs = S * (S + 1) // 2
-    want = gsched.counters_closed_form(M, N, K, P, Q, cm, cn, 128, 256, 128, npairs)
-    c = hs.counters()
+    want = gsched.counters_closed_form(M, N, K, P, Q, cm, cn, 128, 256, Bo, npairs)
     for k, v in want.items():
         assert c[k] == v, (k, c[k], v)
+
+
+def test_pair_kernel_gemm_matches_single_cta_kernel():
+    hs = lib_ready()
+    torch = torch_cuda()
+    A, B, dA, dB = pair(1500, 1300, 900, 33, "uniform", "wide")
+    cfg = dict(P=12, Q=6, G=36, b=64, Bouter=256, kind="bf16", slices=5)
+    assert hs.group_shape(12, 6, 36)[2:] == (2, 1)
+    was = hs.pair_kernel(True)
+    try:
+        C2 = hs.gemm(dA, dB, **cfg)
+        hs.pair_kernel(False)
+        C1 = hs.gemm(dA, dB, **cfg)
+        hs.sync()
+    finally:
+        hs.pair_kernel(was)
+    assert torch.equal(C1, C2)
+    assert np.array_equal(C2.cpu().numpy(), split.split_gemm(A, B, 5, "bf16"))
+
+
+def test_stage_timing_records_each_call():
+    hs = lib_ready()
+    torch = torch_cuda()
+    A, B, dA, dB = pair(512, 768, 640, 41)
+    hs.stage_timing(True)
+    hs.gemm(dA, dB, P=4, Q=3, G=1, b=64, Bouter=256, kind="bf16", slices=3)
+    hs.gemm(dA, dB, P=4, Q=6, G=4, b=32, Bouter=128)
+    hs.stage_timing(False)
+    hs.gemm(dA, dB, P=4, Q=6, G=4, b=32, Bouter=128)       # not recorded
+    ms, calls = hs.stage_times()
+    hs.sync()
+    assert calls == 2
+    assert all(t > 0 for t in ms)                           # every split stage ran
+    hs.stage_timing(True)
+    hs.gemm(dA, dB, P=4, Q=6, G=4, b=32, Bouter=128)
+    hs.stage_timing(False)
+    ms, calls = hs.stage_times()
+    assert calls == 1 and ms[2] > 0
+    assert ms[0] < 0.01 and ms[1] < 0.01 and ms[3] < 0.01   # binary64: one kernel
+
+
+@pytest.mark.parametrize("kind,S,M,N,K,P,Q,G,pinned", [
+    ("fp64", 0, 4000, 900, 640, 16, 4, 16, False),     # 4 row blocks of 1000 rows
+    ("fp64", 0, 3001, 700, 512, 12, 4, 12, True),      # 3 blocks, the last one short
+    ("bf16", 5, 4100, 1000, 900, 32, 4, 32, True),     # split path, 4 blocks, ragged
+    ("int8", 6, 2100, 520, 700, 16, 4, 16, False),     # 2 blocks
+])
+def test_host_entry_pipelined_by_row_blocks(kind, S, M, N, K, P, Q, G, pinned):
+    hs = lib_ready()
+    torch = torch_cuda()
+    dist = "smallint" if kind == "fp64" else "uniform"
+    A = workloads.matrix(M, K, 51, dist)
+    B = workloads.matrix(K, N, 52, "wide" if kind != "fp64" else dist)
+    big = np.full((M, N + 8), 7.0)                   # C with padding the call must not touch
+    hC = big[:, :N]
+    if pinned:
+        A = torch.from_numpy(A).pin_memory()
+        B = torch.from_numpy(B).pin_memory()
+    b = 32 if kind == "fp64" else (64 if kind == "bf16" else 128)
+    hs.gemm_host(A, B, hC, P=P, Q=Q, G=G, b=b, Bouter=4 * b, kind=kind, slices=S)
+    An = A.numpy() if pinned else A
+    Bn = B.numpy() if pinned else B
+    if kind == "fp64":
+        want = (An.astype(np.int64) @ Bn.astype(np.int64)).astype(np.float64)
+    else:
+        want = split.split_gemm(An, Bn, S, kind)
+    assert np.array_equal(hC, want)
+    assert np.all(big[:, N:] == 7.0)

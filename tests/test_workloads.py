@@ -46,3 +46,15 @@ def test_torch_matches_numpy(dist):
     a = workloads.matrix(19, 23, 77, dist)
     b = workloads.matrix_torch(19, 23, 77, dist).numpy()
     assert np.array_equal(a, b)
+
+
+def test_normal_distributions_and_torch_generator():
+    torch = pytest.importorskip("torch")
+    a = workloads.matrix(400, 300, 19, "normal")
+    assert abs(a.mean()) < 0.02 and abs(a.std() - 1.0) < 0.02
+    s = workloads.matrix(400, 300, 19, "normal_spiked")
+    spiked = np.nonzero(np.abs(s).max(axis=0) > 1e4)[0]
+    assert spiked.size == 3                                  # round(0.01 * 300)
+    assert np.array_equal(np.delete(s, spiked, axis=1), np.delete(a, spiked, axis=1))
+    t = workloads.matrix_torch(400, 300, 19, "normal_spiked").numpy()
+    assert np.allclose(t, s, rtol=1e-14, atol=0)             # same draws, libm rounding apart
