@@ -103,27 +103,33 @@ __global__ void exponents_cols_kernel(const double *__restrict__ B, int64_t ldb,
   }
 }
 
-// RN(|x| 2^-e 2^(w s)) for s = 1..S as signed integers, then the digits.
-template <int W, int S_MAX>
-__device__ __forceinline__ void digits_of(double x, int e, int S, int (&t)[S_MAX]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const bool neg = (bits >> 63) != 0;
-  const int E = (int)((bits >> 52) & 0x7FF);
-  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
-  int lsb;  // binary exponent of m's least significant bit
-  if (E > 0) {
-    m |= 1ull << 52;
-    lsb = E - 1075;
-  } else {
-    lsb = -1074;
-  }
-  long long prev = 0;
-#pragma unroll
-  for (int s = 1; s <= S_MAX; ++s) {
-    if (s > S) {
-      t[s - 1] = 0;
-      continue;
+// The digits of one value, slice by slice: Y_s = RN(|x| 2^-e 2^(w s)) (ties to
+// even) as a signed integer, and digit s = Y_s - 2^w Y_(s-1).  The state holds
+// the significand, the exponent of its last bit, the sign and Y_(s-1), so no
+// table indexed by the (run-time) slice number is needed.
+struct DigitGen {
+  unsigned long long m;
+  int lsb;    // binary exponent of m's least significant bit
+  bool neg;
+  long long prev;
+
+  __device__ __forceinline__ void init(double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    neg = (bits >> 63) != 0;
+    const int E = (int)((bits >> 52) & 0x7FF);
+    m = bits & 0xFFFFFFFFFFFFFull;
+    if (E > 0) {
+      m |= 1ull << 52;
+      lsb = E - 1075;
+    } else {
+      lsb = -1074;
     }
+    prev = 0;
+  }
+
+  // digit s (1-based) of w-bit slices for the scale 2^-e
+  template <int W>
+  __device__ __forceinline__ int next(int s, int e) {
     // |x| 2^-e 2^(w s) = m 2^sh, rounded to nearest (ties to even):
     // RNE(m / 2^d) = (m + 2^(d-1) - 1 + ((m >> d) & 1)) >> d for 1 <= d <= 54
     const int sh = lsb - e + W * s;
@@ -139,63 +145,85 @@ __device__ __forceinline__ void digits_of(double x, int e, int S, int (&t)[S_MAX
       y = (m + ((1ull << (d - 1)) - 1ull) + ((m >> d) & 1ull)) >> d;
     }
     const long long Y = neg ? -(long long)y : (long long)y;
-    t[s - 1] = (int)(Y - prev * (1ll << W));
+    const int t = (int)(Y - prev * (1ll << W));
     prev = Y;
+    return t;
+  }
+};
+
+// Eight digits of one slice, stored at dst: bf16 (16 bytes) or int8 (8 bytes).
+template <int KIND>
+__device__ __forceinline__ void store8(void *dst, const int (&t)[8]) {
+  if (KIND == HSUMMA_INT8_SLICES) {
+    uint2 v;
+    v.x = (uint32_t)(uint8_t)t[0] | ((uint32_t)(uint8_t)t[1] << 8) |
+          ((uint32_t)(uint8_t)t[2] << 16) | ((uint32_t)(uint8_t)t[3] << 24);
+    v.y = (uint32_t)(uint8_t)t[4] | ((uint32_t)(uint8_t)t[5] << 8) |
+          ((uint32_t)(uint8_t)t[6] << 16) | ((uint32_t)(uint8_t)t[7] << 24);
+    *reinterpret_cast<uint2 *>(dst) = v;
+  } else {
+    uint4 v;
+    uint32_t *w = reinterpret_cast<uint32_t *>(&v);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      __nv_bfloat162 b = __floats2bfloat162_rn((float)t[2 * h], (float)t[2 * h + 1]);
+      w[h] = *reinterpret_cast<uint32_t *>(&b);
+    }
+    *reinterpret_cast<uint4 *>(dst) = v;
   }
 }
 
-constexpr int SMAX = 8;
-
-// A slices: As[s][i][k], k < Kp (zero beyond K); each thread 4 consecutive k
+// A slices: As[s][i][k], k < Kp (zero beyond K); each thread 8 consecutive k
 template <int KIND>
-__global__ void slices_rows_kernel(const double *__restrict__ A, int64_t lda, int64_t M,
-                                   int64_t K, int64_t Kp, const int32_t *__restrict__ e,
-                                   int S, void *__restrict__ out) {
+__global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restrict__ A,
+                                                          int64_t lda, int64_t M, int64_t K,
+                                                          int64_t Kp,
+                                                          const int32_t *__restrict__ e, int S,
+                                                          void *__restrict__ out) {
   constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
-  const int64_t groups = Kp / 4;
+  constexpr int EB = KIND == HSUMMA_INT8_SLICES ? 1 : 2;
+  const int64_t groups = Kp / 8;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= M * groups) return;
-  const int64_t i = gid / groups, k0 = (gid % groups) * 4;
+  const int64_t i = gid / groups, k0 = (gid % groups) * 8;
   const int ei = e[i];
-  int t[4][SMAX];
-  double x[4];
+  double x[8];
   const double *a = A + i * lda + k0;
-  if (k0 + 3 < K && (reinterpret_cast<uintptr_t>(a) & 15) == 0) {
-    const double2 v0 = reinterpret_cast<const double2 *>(a)[0];
-    const double2 v1 = reinterpret_cast<const double2 *>(a)[1];
-    x[0] = v0.x;
-    x[1] = v0.y;
-    x[2] = v1.x;
-    x[3] = v1.y;
+  if (k0 + 7 < K && (reinterpret_cast<uintptr_t>(a) & 15) == 0) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const double2 v = reinterpret_cast<const double2 *>(a)[h];
+      x[2 * h] = v.x;
+      x[2 * h + 1] = v.y;
+    }
   } else {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = k0 + u < K ? a[u] : 0.0;
+    for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? a[u] : 0.0;
   }
+  DigitGen g[8];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) digits_of<W, SMAX>(x[u], ei, S, t[u]);
-  for (int s = 0; s < S; ++s) {
-    const int64_t off = ((int64_t)s * M + i) * Kp + k0;
-    if (KIND == HSUMMA_INT8_SLICES) {
-      char4 v = make_char4((signed char)t[0][s], (signed char)t[1][s], (signed char)t[2][s],
-                           (signed char)t[3][s]);
-      *reinterpret_cast<char4 *>(reinterpret_cast<int8_t *>(out) + off) = v;
-    } else {
-      __nv_bfloat162 lo = __floats2bfloat162_rn((float)t[0][s], (float)t[1][s]);
-      __nv_bfloat162 hi = __floats2bfloat162_rn((float)t[2][s], (float)t[3][s]);
-      uint2 v;
-      v.x = *reinterpret_cast<uint32_t *>(&lo);
-      v.y = *reinterpret_cast<uint32_t *>(&hi);
-      *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(out) + off) = v;
-    }
+  for (int u = 0; u < 8; ++u) g[u].init(x[u]);
+  uint8_t *base = reinterpret_cast<uint8_t *>(out) + (i * Kp + k0) * EB;
+  const int64_t plane = M * Kp * EB;
+  for (int s = 1; s <= S; ++s) {
+    int t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = g[u].next<W>(s, ei);
+    store8<KIND>(base + (s - 1) * plane, t);
   }
 }
 
-// B slices, transposed: Bs[t][j][k]; a block transposes a 64 (k) x 64 (j) tile
+// B slices, transposed: Bs[t][j][k]; a block transposes a 64 (k) x 64 (j) tile,
+// each thread then forms 8 consecutive k of one column j (8 threads write one
+// 64-k row segment of Bs)
 template <int KIND>
-__global__ void slices_cols_kernel(const double *__restrict__ B, int64_t ldb, int64_t K,
-                                   int64_t N, int64_t Kp, const int32_t *__restrict__ f,
-                                   int S, void *__restrict__ out) {
+__global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restrict__ B,
+                                                          int64_t ldb, int64_t K, int64_t N,
+                                                          int64_t Kp,
+                                                          const int32_t *__restrict__ f, int S,
+                                                          void *__restrict__ out) {
   constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
+  constexpr int EB = KIND == HSUMMA_INT8_SLICES ? 1 : 2;
   __shared__ double tile[64][65];
   const int64_t k0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 64;
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 256 threads: 64 x 4
@@ -204,29 +232,22 @@ __global__ void slices_cols_kernel(const double *__restrict__ B, int64_t ldb, in
     tile[r][tx] = (k < K && j < N) ? B[k * ldb + j] : 0.0;
   }
   __syncthreads();
-  // thread -> (j = j0 + jj, k = k0 + 4 kk .. +3)
-  for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
-    const int jj = idx >> 4, kk = (idx & 15) * 4;
+  const int64_t plane = N * Kp * EB;
+  // thread -> (j = j0 + jj, k = k0 + kk .. kk + 7)
+  for (int idx = threadIdx.x; idx < 64 * 8; idx += 256) {
+    const int jj = idx >> 3, kk = (idx & 7) * 8;
     const int64_t j = j0 + jj;
     if (j >= N) continue;
     const int fj = f[j];
-    int t[4][SMAX];
+    DigitGen g[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) digits_of<W, SMAX>(tile[kk + u][jj], fj, S, t[u]);
-    for (int s = 0; s < S; ++s) {
-      const int64_t off = ((int64_t)s * N + j) * Kp + k0 + kk;
-      if (KIND == HSUMMA_INT8_SLICES) {
-        char4 v = make_char4((signed char)t[0][s], (signed char)t[1][s],
-                             (signed char)t[2][s], (signed char)t[3][s]);
-        *reinterpret_cast<char4 *>(reinterpret_cast<int8_t *>(out) + off) = v;
-      } else {
-        __nv_bfloat162 lo = __floats2bfloat162_rn((float)t[0][s], (float)t[1][s]);
-        __nv_bfloat162 hi = __floats2bfloat162_rn((float)t[2][s], (float)t[3][s]);
-        uint2 v;
-        v.x = *reinterpret_cast<uint32_t *>(&lo);
-        v.y = *reinterpret_cast<uint32_t *>(&hi);
-        *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(out) + off) = v;
-      }
+    for (int u = 0; u < 8; ++u) g[u].init(tile[kk + u][jj]);
+    uint8_t *base = reinterpret_cast<uint8_t *>(out) + (j * Kp + k0 + kk) * EB;
+    for (int s = 1; s <= S; ++s) {
+      int t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = g[u].next<W>(s, fj);
+      store8<KIND>(base + (s - 1) * plane, t);
     }
   }
 }
@@ -307,22 +328,55 @@ __device__ __forceinline__ double round_scaled(__int128 X, int k) {
 }
 
 // X = sum_d D_d 2^(w (S+1-d)) by Horner's rule (constant shifts), rounded once.
+// Each thread takes four consecutive columns of one row: 16-byte loads from
+// every plane when the rows are 16-byte aligned (N a multiple of 4), 16-byte
+// stores of C when its row allows, element by element otherwise.
 template <int W, int S>
-__global__ void recombine_kernel(const int32_t *__restrict__ D, int nseg, int64_t M, int64_t N,
-                                 const int32_t *__restrict__ e, const int32_t *__restrict__ f,
-                                 double *__restrict__ C, int64_t ldc) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) recombine_kernel(const int32_t *__restrict__ D, int nseg,
+                                                        int64_t M, int64_t N,
+                                                        const int32_t *__restrict__ e,
+                                                        const int32_t *__restrict__ f,
+                                                        double *__restrict__ C, int64_t ldc) {
+  const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   const int64_t i = blockIdx.y;
-  if (j >= N) return;
-  const int64_t plane = M * N, off = i * N + j;
-  __int128 X = 0;
+  if (j0 >= N) return;
+  const int64_t plane = M * N, off = i * N + j0;
+  const bool full = j0 + 3 < N;
+  const bool vec = full && (N & 3) == 0;
+  __int128 X[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int d = 2; d <= S + 1; ++d) {
-    long long Dd = 0;   // the segment planes of a diagonal sum exactly in 64 bits
-    for (int g = 0; g < nseg; ++g) Dd += __ldg(D + (int64_t)((d - 2) * nseg + g) * plane + off);
-    X = (X << W) + (__int128)Dd;
+    long long Dd[4] = {0, 0, 0, 0};   // the segment planes of a diagonal sum exactly in 64 bits
+    for (int g = 0; g < nseg; ++g) {
+      const int32_t *src = D + (int64_t)((d - 2) * nseg + g) * plane + off;
+      if (vec) {
+        const int4 v = __ldg(reinterpret_cast<const int4 *>(src));
+        Dd[0] += v.x;
+        Dd[1] += v.y;
+        Dd[2] += v.z;
+        Dd[3] += v.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j0 + u < N) Dd[u] += __ldg(src + u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) X[u] = (X[u] << W) + (__int128)Dd[u];
   }
-  C[i * ldc + j] = round_scaled(X, e[i] + f[j] - W * (S + 1));
+  const int k = e[i] - W * (S + 1);
+  double out[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) out[u] = j0 + u < N ? round_scaled(X[u], k + f[j0 + u]) : 0.0;
+  double *dst = C + i * ldc + j0;
+  if (full && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    reinterpret_cast<double2 *>(dst)[0] = make_double2(out[0], out[1]);
+    reinterpret_cast<double2 *>(dst)[1] = make_double2(out[2], out[3]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (j0 + u < N) dst[u] = out[u];
+  }
 }
 
 template <int W, int S>
@@ -369,7 +423,7 @@ int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
                         int kind, int S, void *As, void *Bs, cudaStream_t s) {
   const int64_t Kp = ceil_div(K, 64) * 64;
   if (Kp == 0) return HSUMMA_OK;
-  const int64_t nA = M * (Kp / 4);
+  const int64_t nA = M * (Kp / 8);
   if (nA > 0) {
     const unsigned blocks = (unsigned)ceil_div(nA, 256);
     if (kind == HSUMMA_INT8_SLICES)
@@ -396,7 +450,7 @@ int launch_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, con
   // r0 rows in: D, e and C advance by r0 rows, the plane stride stays M N
   for (int64_t r0 = 0; r0 < M; r0 += 65535) {
     const int64_t rows = (M - r0) < 65535 ? (M - r0) : 65535;
-    dim3 grid((unsigned)ceil_div(N, 256), (unsigned)rows);
+    dim3 grid((unsigned)ceil_div(ceil_div(N, 4), 256), (unsigned)rows);
     if (kind == HSUMMA_INT8_SLICES)
       recombine_dispatch<7>(S, grid, s, D + r0 * N, nseg, M, N, e + r0, f, C + r0 * ldc, ldc);
     else
