@@ -152,7 +152,7 @@ def cpu_oracle_rate(A, B, target_s=15.0):
     return 2.0 * rows * n * B.shape[1] / dt / 1e12, rows, cores, dt
 
 
-def cpu_leg(A_band, A_rows, B, cols, sampled):
+def cpu_leg(A_band, A_rows, B, ri, cj, sampled):
     """The bench's CPU leg (with the reference arm, the only code here that runs
     the oracle): the plain binary64 triple loop timed on a band of rows of C
     (cpu_baseline), and the compensated (Dot2) reference of the sampled
@@ -164,10 +164,11 @@ def cpu_leg(A_band, A_rows, B, cols, sampled):
            "sample": f"{rws} rows of C at n={B.shape[0]} by the plain binary64 triple loop "
                      f"({dt:.1f} s)"}
     import numpy as np
-    ref, absab = native.dot2_entries(A_rows, B, np.arange(A_rows.shape[0]), cols)
+    ref, absab = native.dot2_entries(A_rows, B, ri, cj)
     acc = {f"{k}_max_rel_err": split.max_rel_error(v, ref, absab) for k, v in sampled.items()}
     acc["tolerance_2Ku"] = split.tolerance(B.shape[0])
-    acc["reference"] = f"Dot2 on {len(cols)} sampled entries"
+    acc["reference"] = (f"Dot2 on {len(cj)} entries: every 128-tile border row and column "
+                        f"and seeded ones")
     return cpu, acc
 
 
@@ -427,12 +428,21 @@ def main():
                "ms_per_step": te * 1e3}
         del hA, hB, hC
 
-    # sampled entries of the split result (accuracy is computed in the CPU leg)
-    x = workloads.splitmix64(77, 0, 2048)
-    rows = np.unique((x[0::2] % np.uint64(n)).astype(np.int64))[:256]
-    cols = (x[1::2] % np.uint64(n)).astype(np.int64)[:rows.size]
+    # sampled entries of the split result (accuracy is computed in the CPU leg):
+    # every tile-border row and column (128 x 128 tiles) and seeded ones, their
+    # cross product column by column
+    x = workloads.splitmix64(77, 0, 192)
+    rows = set((x[:64] % np.uint64(n)).astype(np.int64).tolist())
+    cols = set((x[64:] % np.uint64(n)).astype(np.int64).tolist())
+    for b0 in range(0, n, 128):
+        rows.update((b0, min(n, b0 + 128) - 1))
+        cols.update((b0, min(n, b0 + 128) - 1))
+    rows = np.array(sorted(rows), dtype=np.int64)
+    cols = np.array(sorted(cols), dtype=np.int64)
+    ri = np.tile(np.arange(rows.size, dtype=np.int64), cols.size)
+    cj = np.repeat(cols, rows.size)
     ir, ic = torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")
-    sampled = {"split": dC[ir, ic].cpu().numpy()}
+    sampled = {"split": dC[ir][:, ic].cpu().numpy().T.ravel()}
 
     # native binary64 path on the same inputs
     native_out = None
@@ -456,13 +466,13 @@ def main():
                                    "peak": dmma_peak, "unit": "TFLOP/s",
                                    "frac": ntf / dmma_peak,
                                    "peak_source": "measured by hsumma_peak(DMMA) in this run"}}
-        sampled["native"] = dC2[ir, ic].cpu().numpy()
+        sampled["native"] = dC2[ir][:, ic].cpu().numpy().T.ravel()
         del dC2
 
     cpu, acc = None, {}
     if rank == 0 and not args.no_cpu:
         cpu, acc = cpu_leg(dA[:256].cpu().numpy(), dA[ir].cpu().numpy(), dB.cpu().numpy(),
-                           cols, sampled)
+                           ri, cj, sampled)
 
     if rank == 0:
         out = {

@@ -151,8 +151,9 @@ def collect(out_dir, n_samples=2000, per_shape=20, n_heldout=200, seed=4000, rep
         del A, B, C
         if (i + 1) % 10 == 0:
             log(f"train {i + 1} shapes, {len(rows)} samples, {time.time() - t0:.0f}s")
-    rows = np.array(rows, dtype=np.float64)
-    np.savez_compressed(os.path.join(out_dir, "samples.npz"), rows=rows)
+    if n_samples > 0:
+        rows = np.array(rows, dtype=np.float64)
+        np.savez_compressed(os.path.join(out_dir, "samples.npz"), rows=rows)
 
     shape_rows, offs, cfgs, mss, base_cfg, base_ms = [], [0], [], [], [], []
     for i, (M, N, K, kind, S) in enumerate(held_shapes):
@@ -233,13 +234,15 @@ def init_params(seed: int) -> np.ndarray:
     return theta.astype(np.float32)
 
 
-def train(X, y, steps=6000, lr=3e-3, seed=4003, log=print, X_val=None, y_val=None,
-          check_every=250):
+def train(X, y, steps=6000, lr=1e-3, seed=4003, log=print, X_val=None, y_val=None,
+          check_every=250, val_products=None):
     """Fit the network to ln t on the GPU: full-batch Adam (beta = 0.9, 0.999;
     eps = 1e-8) with the step size decayed on a cosine from lr to 0.  Features
-    and targets are standardised with the training set's statistics.  With a
-    validation set, the parameters of the checkpoint (every check_every steps)
-    with the smallest validation error are kept.  Returns the model dict."""
+    and targets are standardised with the training set's statistics.  Every
+    check_every steps a checkpoint is scored and the best one kept: by the
+    geometric mean of pick time over best time on val_products (products with
+    every candidate timed, as load_heldout returns them) when given, else by
+    the mean squared error on (X_val, y_val).  Returns the model dict."""
     import torch
     hs.init(0)
     lib = hs.lib()
@@ -261,6 +264,13 @@ def train(X, y, steps=6000, lr=3e-3, seed=4003, log=print, X_val=None, y_val=Non
     if X_val is not None:
         dXv, yv = dev((X_val - mean) / std), (np.asarray(y_val) - ym) / ys
         pv = torch.empty(len(yv), dtype=torch.float32, device="cuda")
+    if val_products:
+        Xp = np.concatenate([hs.features(h["M"], h["N"], h["K"],
+                                         [tuple(int(v) for v in c) for c in h["cfg"]],
+                                         h["kind"], h["S"]) for h in val_products])
+        dXp = dev((Xp - mean) / std)
+        pp = torch.empty(Xp.shape[0], dtype=torch.float32, device="cuda")
+        bounds = np.cumsum([0] + [len(h["ms"]) for h in val_products])
     for t in range(1, steps + 1):
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (t - 1) / steps))
         hs._check(lib.hsumma_mlp_backward(n, theta.data_ptr(), dX.data_ptr(), dy.data_ptr(),
@@ -271,18 +281,28 @@ def train(X, y, steps=6000, lr=3e-3, seed=4003, log=print, X_val=None, y_val=Non
         if t == 1 or t % 500 == 0 or t == steps:
             hist.append((t, float(loss.item())))
             log(f"step {t}: mse {hist[-1][1]:.5f}")
-        if X_val is not None and (t % check_every == 0 or t == steps):
-            hs._check(lib.hsumma_mlp_forward(len(yv), theta.data_ptr(), dXv.data_ptr(),
-                                             pv.data_ptr(), None, stream))
-            err = float(np.mean((pv.cpu().numpy().astype(np.float64) - yv) ** 2))
+        if (val_products or X_val is not None) and (t % check_every == 0 or t == steps):
+            if val_products:
+                hs._check(lib.hsumma_mlp_forward(Xp.shape[0], theta.data_ptr(), dXp.data_ptr(),
+                                                 pp.data_ptr(), None, stream))
+                pred = pp.cpu().numpy()
+                r = [h["ms"][int(np.argmin(pred[a:b]))] / np.min(h["ms"])
+                     for h, a, b in zip(val_products, bounds[:-1], bounds[1:])]
+                err = float(np.exp(np.mean(np.log(r))))
+            else:
+                hs._check(lib.hsumma_mlp_forward(len(yv), theta.data_ptr(), dXv.data_ptr(),
+                                                 pv.data_ptr(), None, stream))
+                err = float(np.mean((pv.cpu().numpy().astype(np.float64) - yv) ** 2))
             if err < best[0]:
                 best = (err, t, theta.cpu().numpy().copy())
     hs.sync()
     out = dict(theta=theta.cpu().numpy(), mean=mean, std=std, y_mean=np.float64(ym),
                y_std=np.float64(ys), history=np.array(hist))
     if best[2] is not None:
-        log(f"kept step {best[1]}: validation mse {best[0]:.5f}")
-        out.update(theta=best[2], val_mse=np.float64(best[0]), val_step=np.int64(best[1]))
+        what = "pick/best geomean" if val_products else "mse"
+        log(f"kept step {best[1]}: validation {what} {best[0]:.5f}")
+        out.update(theta=best[2], val_score=np.float64(best[0]), val_step=np.int64(best[1]),
+                   lr=np.float64(lr), steps=np.int64(steps))
     return out
 
 
@@ -362,8 +382,11 @@ def main(argv=None):
     t.add_argument("--data", default=TUNING_DIR)
     t.add_argument("--out", default=MODEL_PATH)
     t.add_argument("--steps", type=int, default=6000)
-    t.add_argument("--lr", type=float, default=3e-3)
+    t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--seed", type=int, default=4003)
+    t.add_argument("--val", default=os.path.join(TUNING_DIR, "validation.npz"),
+                   help="products with every candidate timed (heldout.npz format) that select "
+                        "the checkpoint; '' uses the training products' last 10 %% instead")
     e = sub.add_parser("evaluate")
     e.add_argument("--data", default=TUNING_DIR)
     e.add_argument("--model", default=MODEL_PATH)
@@ -374,10 +397,15 @@ def main(argv=None):
     elif a.cmd == "train":
         rows = np.load(os.path.join(a.data, "samples.npz"))["rows"]
         rows = rows[np.isfinite(rows[:, 10])]
-        tr, va = split_by_product(rows)
-        X, y = sample_features(tr)
-        Xv, yv = sample_features(va)
-        save_model(train(X, y, a.steps, a.lr, a.seed, X_val=Xv, y_val=yv), a.out)
+        if a.val:
+            X, y = sample_features(rows)
+            save_model(train(X, y, a.steps, a.lr, a.seed, val_products=load_heldout(a.val)),
+                       a.out)
+        else:
+            tr, va = split_by_product(rows)
+            X, y = sample_features(tr)
+            Xv, yv = sample_features(va)
+            save_model(train(X, y, a.steps, a.lr, a.seed, X_val=Xv, y_val=yv), a.out)
     else:
         hs.init(0)
         rep = evaluate(read_model(a.model), load_heldout(os.path.join(a.data, "heldout.npz")))

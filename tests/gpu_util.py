@@ -37,3 +37,22 @@ def sample_entries(M, N, n, seed):
     extra_r = [0, M - 1, 0, M - 1] + [min(M - 1, r) for r in (127, 128, 255, 256)]
     extra_c = [0, 0, N - 1, N - 1] + [min(N - 1, c) for c in (255, 256, 127, 128)]
     return np.concatenate([rows, extra_r]), np.concatenate([cols, extra_c])
+
+
+def border_grid(M, N, tm, tn, n_rows, n_cols, seed):
+    """Row and column sets of a sampled accuracy check: every tile-border row
+    (the first and last row of each tm-row block) and column (of each tn-column
+    block), plus n_rows / n_cols seeded ones; the entries are their cross
+    product, column by column (so the reference reads each column of B once)."""
+    x = workloads.splitmix64(seed, 0, n_rows + n_cols)
+    rows = set((x[:n_rows] % np.uint64(max(M, 1))).astype(np.int64).tolist())
+    cols = set((x[n_rows:] % np.uint64(max(N, 1))).astype(np.int64).tolist())
+    for b in range(0, M, tm):
+        rows.update((b, min(M, b + tm) - 1))
+    for b in range(0, N, tn):
+        cols.update((b, min(N, b + tn) - 1))
+    rows = np.array(sorted(rows), dtype=np.int64)
+    cols = np.array(sorted(cols), dtype=np.int64)
+    ri = np.tile(np.arange(rows.size, dtype=np.int64), cols.size)   # index into rows
+    cj = np.repeat(cols, rows.size)
+    return rows, cols, ri, cj

@@ -1,32 +1,38 @@
 """Accuracy of both paths at the full sizes, in the launch configurations the
 benchmark times (GPU): at n = 16384 for every slice count, on uniform and
 wide-range inputs, and the rectangular 24576 x 16384 x 32768 product whose A
-has 1 % of its columns scaled by 1e6.  Error max |C - C^| / (|A||B|) on seeded
-sampled entries against the compensated (Dot2) reference; bound 2 K u."""
+has 1 % of its columns scaled by 1e6.  Error max |C - C^| / (|A||B|) against
+the compensated (Dot2) reference on more than 65536 entries: every tile-border
+row and column and seeded ones; bound 2 K u."""
 import numpy as np
 import pytest
 
 import workloads
 from oracle import native, split
-from tests.gpu_util import lib_ready, torch_cuda
+from tests.gpu_util import border_grid, lib_ready, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
-BENCH_SPLIT = dict(P=128, Q=64, G=256, b=64, Bouter=1024)     # bench.py's split launch
+BENCH_SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=2048)    # bench.py's split launch
 BENCH_NATIVE = dict(P=128, Q=128, G=4096, b=32, Bouter=128)   # bench.py's binary64 launch
 INT8_FLAT = dict(P=128, Q=128, G=1, b=128, Bouter=2048)
 
 
-def sampled_reference(torch, dA, dB, count, seed):
-    """count seeded entries (distinct rows) and their Dot2 reference."""
+def sampled_reference(torch, dA, dB, n_rows, n_cols, seed):
+    """Every tile-border row and column (128 x 128 tiles, which include the
+    borders of the split path's 128 x 256 tiles) and seeded ones; the Dot2
+    reference of their cross product and a function that gathers the same
+    entries of a GPU result."""
     M, N = dA.shape[0], dB.shape[1]
-    x = workloads.splitmix64(seed, 0, 8 * count)
-    rows = np.unique((x[0::2] % np.uint64(M)).astype(np.int64))[:count]
-    cols = (x[1::2] % np.uint64(N)).astype(np.int64)[:rows.size]
+    rows, cols, ri, cj = border_grid(M, N, 128, 128, n_rows, n_cols, seed)
     ir, ic = torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")
-    ref, absab = native.dot2_entries(dA[ir].cpu().numpy(), dB.cpu().numpy(),
-                                     np.arange(rows.size), cols)
-    return ir, ic, ref, absab
+    ref, absab = native.dot2_entries(dA[ir].cpu().numpy(), dB.cpu().numpy(), ri, cj)
+
+    def gather(C):
+        return C[ir][:, ic].cpu().numpy().T.ravel()      # column by column, as ri / cj
+
+    assert ref.size >= 65536
+    return gather, ref, absab
 
 
 @pytest.mark.parametrize("dist", ["uniform", "wide"])
@@ -36,7 +42,7 @@ def test_error_per_slice_count_at_16384(dist):
     n = 16384
     dA = workloads.matrix_torch(n, n, 1002, dist, device="cuda")
     dB = workloads.matrix_torch(n, n, 2002, dist, device="cuda")
-    ir, ic, ref, absab = sampled_reference(torch, dA, dB, 256, 77)
+    gather, ref, absab = sampled_reference(torch, dA, dB, 64, 128, 77)
     tol = split.tolerance(n)
     C = torch.empty((n, n), dtype=torch.float64, device="cuda")
     errs = {}
@@ -44,11 +50,11 @@ def test_error_per_slice_count_at_16384(dist):
         for S in slices:
             hs.gemm(dA, dB, out=C, kind=kind, slices=S, **cfg)
             hs.sync()
-            errs[(kind, S)] = split.max_rel_error(C[ir, ic].cpu().numpy(), ref, absab)
+            errs[(kind, S)] = split.max_rel_error(gather(C), ref, absab)
     if dist == "uniform":
         hs.gemm(dA, dB, out=C, **BENCH_NATIVE)
         hs.sync()
-        errs[("fp64", 0)] = split.max_rel_error(C[ir, ic].cpu().numpy(), ref, absab)
+        errs[("fp64", 0)] = split.max_rel_error(gather(C), ref, absab)
     print("ERRORS", dist, {f"{k}{s}": f"{v:.3e}" for (k, s), v in errs.items()}, f"tol {tol:.3e}")
     for kind, top in (("bf16", 6), ("int8", 8)):
         for S in range(3, top):
@@ -65,15 +71,16 @@ def test_rectangular_spiked_columns_both_paths():
     M, N, K = 24576, 16384, 32768
     dA = workloads.matrix_torch(M, K, 1003, "normal_spiked", device="cuda")
     dB = workloads.matrix_torch(K, N, 2003, "normal", device="cuda")
-    ir, ic, ref, absab = sampled_reference(torch, dA, dB, 128, 78)
+    gather, ref, absab = sampled_reference(torch, dA, dB, 16, 64, 78)
     tol = split.tolerance(K)
     C = torch.empty((M, N), dtype=torch.float64, device="cuda")
     hs.gemm(dA, dB, out=C, P=12, Q=16, G=48, b=32, Bouter=128)      # the 12 x 16 grid
     hs.sync()
-    e_native = split.max_rel_error(C[ir, ic].cpu().numpy(), ref, absab)
-    hs.gemm(dA, dB, out=C, kind="bf16", slices=7, P=192, Q=64, G=1, b=64, Bouter=1024)
+    e_native = split.max_rel_error(gather(C), ref, absab)
+    # 2 x 1 groups on CTA pairs, as in the benchmark
+    hs.gemm(dA, dB, out=C, kind="bf16", slices=7, P=192, Q=64, G=6144, b=64, Bouter=2048)
     hs.sync()
-    e_split = split.max_rel_error(C[ir, ic].cpu().numpy(), ref, absab)
+    e_split = split.max_rel_error(gather(C), ref, absab)
     print("RECT", f"native {e_native:.3e} bf16 S=7 {e_split:.3e} tol {tol:.3e}")
     assert e_native <= tol
     assert e_split <= tol
