@@ -258,11 +258,40 @@ int hsumma_features(int64_t M, int64_t N, int64_t K, int mode,
 
 /* Choice policies and how a choice was made. */
 enum {
-  HSUMMA_CHOOSE_AUTO = 0,   /* cached, else the model, else timing */
-  HSUMMA_CHOOSE_MODEL = 1,  /* the loaded model (HSUMMA_ERR_UNSUPPORTED if none) */
-  HSUMMA_CHOOSE_TIMED = 2   /* exhaustive timing, always */
+  HSUMMA_CHOOSE_AUTO = 0,     /* cached, else the model, else timing */
+  HSUMMA_CHOOSE_MODEL = 1,    /* the loaded model (HSUMMA_ERR_UNSUPPORTED if none) */
+  HSUMMA_CHOOSE_TIMED = 2,    /* exhaustive timing, always */
+  HSUMMA_CHOOSE_ANALYTIC = 3  /* the fitted analytic model (hsumma_analytic_load) */
 };
-enum { HSUMMA_CHOSEN_CACHED = 0, HSUMMA_CHOSEN_MODEL = 1, HSUMMA_CHOSEN_TIMED = 2 };
+enum {
+  HSUMMA_CHOSEN_CACHED = 0,
+  HSUMMA_CHOSEN_MODEL = 1,
+  HSUMMA_CHOSEN_TIMED = 2,
+  HSUMMA_CHOSEN_ANALYTIC = 3
+};
+
+/* Section IV's cost model of HSUMMA with binomial broadcast trees, read for a
+ * P x Q grid of thread blocks with I x J groups (in-group grid (P/I) x (Q/J)),
+ * blocks Mt x Nt = ceil(M/P) x ceil(N/Q), K counted once per slice pair on the
+ * split paths (Ke = K or K S(S+1)/2) and W = ceil(PQ / SMs) waves.  Writes
+ * 5 terms per configuration to h_terms (n x 5, row-major):
+ *   [0] computation  W 2 Mt Nt Ke,
+ *   [1] latency      W (Ke/b (log2(Q/J) + log2(P/I)) + Ke/B (log2 J + log2 I)),
+ *   [2] bandwidth    W Ke (Mt (log2(Q/J) + log2 J) + Nt (log2(P/I) + log2 I)),
+ *   [3] slicing      (M + N) K S on the split paths (0 for FP64),
+ *   [4] 1 (per call).
+ * For P = Q and I = J, [1] and [2] are the latency factor
+ * log2(p/G) n/b + log2(G) n/B and the bandwidth factor
+ * (log2(p/G) + log2 G) n^2/sqrt(p) of Section IV (Table I) times W.
+ * The predicted time is the dot product with the coefficients (gamma, alpha,
+ * beta, slicing, overhead) loaded by hsumma_analytic_load.  Host only. */
+int hsumma_analytic_terms(int64_t M, int64_t N, int64_t K, int mode,
+                          const int *h_cfg, int n, double *h_terms);
+
+/* Coefficients of the analytic model, 5 per mode kind (FP64, INT8, BF16),
+ * h_coef[kind * 5 + term] (seconds per unit of each term); NULL unloads.
+ * Drops every cached choice. */
+int hsumma_analytic_load(const double *h_coef);
 
 /* The configuration hsumma_gemm runs with when P = Q = G = b = Bouter = 0:
  * written to h_cfg[5] with *h_how one of HSUMMA_CHOSEN_*.  The model scores

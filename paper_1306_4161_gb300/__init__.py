@@ -78,6 +78,8 @@ _SIGS = {
     "hsumma_candidates": ([_i64, _i64, _i64, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_int)],
                           _i32),
     "hsumma_features": ([_i64, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
+    "hsumma_analytic_terms": ([_i64, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
+    "hsumma_analytic_load": ([_vp], _i32),
     "hsumma_choose": ([_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _i32, _vp,
                        ctypes.POINTER(ctypes.c_int), _vp], _i32),
     "hsumma_peak": ([_i32, _i64, ctypes.POINTER(ctypes.c_double)], _i32),
@@ -300,8 +302,8 @@ def peak(kind: str, work: int) -> float:
 
 
 # ---- automatic configuration ----
-CHOOSE = {"auto": 0, "model": 1, "timed": 2}
-CHOSEN = {0: "cached", 1: "model", 2: "timed"}
+CHOOSE = {"auto": 0, "model": 1, "timed": 2, "analytic": 3}
+CHOSEN = {0: "cached", 1: "model", 2: "timed", 3: "analytic"}
 
 
 def candidates(M, N, K, kind="fp64", slices=0) -> list[tuple[int, int, int, int, int]]:
@@ -383,3 +385,23 @@ def pair_kernel(enable=None) -> bool:
     if r < 0:
         _check(r)
     return bool(r)
+
+
+def analytic_terms(M, N, K, cfgs, kind="fp64", slices=0):
+    """The analytic model's 5 terms (n x 5 float64) of configurations."""
+    import numpy as np
+    cfg = np.ascontiguousarray(np.asarray(cfgs, dtype=np.int32).reshape(-1, 5))
+    T = np.empty((cfg.shape[0], 5), dtype=np.float64)
+    _check(lib().hsumma_analytic_terms(M, N, K, mode_code(kind, slices), cfg.ctypes.data,
+                                       cfg.shape[0], T.ctypes.data))
+    return T
+
+
+def load_analytic(coef):
+    """Load the analytic model's coefficients (3 kinds x 5 terms); None unloads."""
+    import numpy as np
+    if coef is None:
+        _check(lib().hsumma_analytic_load(None))
+        return
+    c = np.ascontiguousarray(coef, dtype=np.float64).reshape(3, 5)
+    _check(lib().hsumma_analytic_load(c.ctypes.data))

@@ -318,10 +318,51 @@ def read_model(path=MODEL_PATH):
 
 def load_into_library(path=MODEL_PATH):
     """Load the trained model at path into the library (hsumma_gemm's automatic
-    choice then uses it)."""
+    choice then uses it), with the analytic model's coefficients when present."""
     m = read_model(path)
     hs.load_model(m["theta"], m["mean"], m["std"])
+    if "analytic" in m:
+        hs.load_analytic(m["analytic"])
     return m
+
+
+# ---------------------------------------------------------------- analytic model
+def fit_analytic(rows):
+    """Coefficients (3 kinds x 5 terms) of Section IV's model, read for this GPU
+    (hsumma_analytic_terms), fitted per kind by non-negative least squares on
+    the relative error sum_i ((model_i - t_i) / t_i)^2 of the training rows."""
+    from scipy.optimize import nnls
+    coef = np.zeros((3, 5))
+    for kc in range(3):
+        sel = rows[rows[:, 3] == kc]
+        if len(sel) == 0:
+            continue
+        T = np.stack([hs.analytic_terms(int(r[0]), int(r[1]), int(r[2]),
+                                        [tuple(int(v) for v in r[5:10])], KIND_NAME[kc],
+                                        int(r[4]))[0] for r in sel])
+        t = sel[:, 10] * 1e-3                      # seconds
+        A = T / t[:, None]
+        scale = np.maximum(np.abs(A).max(axis=0), 1e-300)   # column scaling for NNLS
+        x, _ = nnls(A / scale, np.ones(len(t)))
+        coef[kc] = x / scale
+    return coef
+
+
+def analytic_pick(coef, h) -> int:
+    """Index of the candidate with the smallest analytic time."""
+    cfgs = [tuple(int(v) for v in c) for c in h["cfg"]]
+    T = hs.analytic_terms(h["M"], h["N"], h["K"], cfgs, h["kind"], h["S"])
+    return int(np.argmin(T @ coef[KIND_CODE[h["kind"]]]))
+
+
+def sampled_pick(h) -> int:
+    """The paper's own tuning (Section V-A-1, Section VI): run a few group counts
+    and keep the fastest -- here every candidate group count of the grid of one
+    sub-tile per block, with b = B; index of the fastest by the timed table."""
+    cfgs = [tuple(int(v) for v in c) for c in h["cfg"]]
+    P0, Q0 = cfgs[0][:2]
+    idx = [i for i, c in enumerate(cfgs) if c[:2] == (P0, Q0) and c[3] == c[4]]
+    return min(idx, key=lambda i: h["ms"][i])
 
 
 # ---------------------------------------------------------------- evaluation
@@ -348,23 +389,29 @@ def _stats(r):
 
 
 def evaluate(model, heldout, picker=None):
-    """Ratios of the model's pick and of the paper's setting to the exhaustive
-    best (the fastest candidate), over the held-out products, overall and per
-    kind."""
+    """Ratios to the exhaustive best (the fastest candidate), over the held-out
+    products, overall and per kind, of: the model's pick ("model"), the paper's
+    static setting G = sqrt(p), b = B ("paper_rule"), the paper's tuning by a few
+    runs ("sampled") and, when the model carries its coefficients, the fitted
+    analytic model ("analytic")."""
     picker = picker or (lambda h: pick(model, h["M"], h["N"], h["K"], h["kind"], h["S"],
                                        [tuple(int(v) for v in c) for c in h["cfg"]]))
+    coef = model.get("analytic") if isinstance(model, dict) else None
     rows = []
     for h in heldout:
         ms = h["ms"]
         best = float(np.min(ms))
-        j = picker(h)
-        rows.append((h["kind"], ms[j] / best, h["base_ms"] / best))
-    out = {"model": _stats([r[1] for r in rows]), "paper_rule": _stats([r[2] for r in rows])}
-    for k in KIND_CODE:
-        sel = [r for r in rows if r[0] == k]
+        r = {"kind": h["kind"], "model": ms[picker(h)] / best, "paper_rule": h["base_ms"] / best,
+             "sampled": ms[sampled_pick(h)] / best}
+        if coef is not None:
+            r["analytic"] = ms[analytic_pick(coef, h)] / best
+        rows.append(r)
+    keys = [k for k in ("model", "analytic", "sampled", "paper_rule") if k in rows[0]]
+    out = {k: _stats([r[k] for r in rows]) for k in keys}
+    for kind in KIND_CODE:
+        sel = [r for r in rows if r["kind"] == kind]
         if sel:
-            out[k] = {"model": _stats([r[1] for r in sel]),
-                      "paper_rule": _stats([r[2] for r in sel])}
+            out[kind] = {k: _stats([r[k] for r in sel]) for k in keys}
     return out
 
 
@@ -399,13 +446,14 @@ def main(argv=None):
         rows = rows[np.isfinite(rows[:, 10])]
         if a.val:
             X, y = sample_features(rows)
-            save_model(train(X, y, a.steps, a.lr, a.seed, val_products=load_heldout(a.val)),
-                       a.out)
+            model = train(X, y, a.steps, a.lr, a.seed, val_products=load_heldout(a.val))
         else:
             tr, va = split_by_product(rows)
             X, y = sample_features(tr)
             Xv, yv = sample_features(va)
-            save_model(train(X, y, a.steps, a.lr, a.seed, X_val=Xv, y_val=yv), a.out)
+            model = train(X, y, a.steps, a.lr, a.seed, X_val=Xv, y_val=yv)
+        model["analytic"] = fit_analytic(rows)
+        save_model(model, a.out)
     else:
         hs.init(0)
         rep = evaluate(read_model(a.model), load_heldout(os.path.join(a.data, "heldout.npz")))

@@ -89,6 +89,43 @@ void features(int64_t M, int64_t N, int64_t K, int kind, int S, const Cand &c, f
 std::mutex g_mu;
 std::map<std::tuple<int64_t, int64_t, int64_t, int>, Cand> g_cache;
 
+// Section IV's cost of HSUMMA with binomial broadcast trees, read for a P x Q
+// grid of thread blocks with I x J groups (in-group grid (P/I) x (Q/J)):
+//   inner level: each b-wide step broadcasts an Mt x b piece of A along an
+//     in-group row (tree depth log2(Q/J)) and a b x Nt piece of B along an
+//     in-group column (depth log2(P/I));
+//   outer level: each B-wide step broadcasts Mt x B and B x Nt among the J
+//     (resp. I) groups of a row (column): depth log2 J (log2 I);
+//   computation: 2 Mt Nt K multiply-adds per block;
+// with K counted once per slice pair on the split paths, and every term times
+// the number of waves in which the grid's blocks run on the device's SMs.  For
+// P = Q, I = J the latency and bandwidth factors are the paper's
+// log2(p/G) n/b + log2(G) n/B and (log2(p/G) + log2(G)) n^2 / sqrt(p).  Terms:
+//   [0] computation, [1] latency (messages x depth), [2] bandwidth (words x
+//   depth), [3] slicing volume (M + N) K S (split paths), [4] one per call.
+constexpr int kAnalyticTerms = 5;
+double g_analytic[3][kAnalyticTerms];
+bool g_analytic_loaded = false;
+
+void analytic_terms(int64_t M, int64_t N, int64_t K, int kind, int S, const Cand &c,
+                    double *f) {
+  int I = 1, J = 1, cm = 1, cn = 1;
+  if (hsumma_group_shape(c.P, c.Q, c.G, &I, &J, &cm, &cn) != HSUMMA_OK) I = J = 1;
+  const double P = c.P, Q = c.Q, p = P * Q;
+  const int sms = state().sm_count > 0 ? state().sm_count : 152;
+  const double waves = std::ceil(p / sms);
+  const double Mt = std::ceil((double)M / P), Nt = std::ceil((double)N / Q);
+  const double pairs = kind == HSUMMA_FP64 ? 1.0 : S * (S + 1) / 2.0;
+  const double Ke = (double)K * pairs;
+  auto lg = [](double x) { return x > 1.0 ? std::log2(x) : 0.0; };
+  const double gi = P / I, gj = Q / J;
+  f[0] = waves * 2.0 * Mt * Nt * Ke;
+  f[1] = waves * (Ke / c.b * (lg(gj) + lg(gi)) + Ke / c.Bo * (lg(J) + lg(I)));
+  f[2] = waves * Ke * (Mt * (lg(gj) + lg(J)) + Nt * (lg(gi) + lg(I)));
+  f[3] = kind == HSUMMA_FP64 ? 0.0 : (double)(M + N) * (double)K * S;
+  f[4] = 1.0;
+}
+
 int decode_mode(int mode, int *kind, int *S) {
   *kind = mode & 0xff;
   *S = (mode >> 8) & 0xff;
@@ -266,7 +303,7 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
   int kind, S;
   int st = decode_mode(mode, &kind, &S);
   if (st != HSUMMA_OK) return st;
-  if (!cfg || !how || policy < 0 || policy > 2 || M < 0 || N < 0 || K < 0) {
+  if (!cfg || !how || policy < 0 || policy > 3 || M < 0 || N < 0 || K < 0) {
     set_error("bad arguments");
     return HSUMMA_ERR_ARG;
   }
@@ -294,6 +331,22 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
   if (M == 0 || N == 0 || K == 0) {
     bi = 0;  // nothing to compute: any candidate does
     *how = HSUMMA_CHOSEN_MODEL;
+  } else if (policy == HSUMMA_CHOOSE_ANALYTIC) {
+    if (!g_analytic_loaded) {
+      set_error("no analytic model loaded (hsumma_analytic_load)");
+      return HSUMMA_ERR_UNSUPPORTED;
+    }
+    double best_t = INFINITY;
+    for (size_t i = 0; i < cands.size(); ++i) {
+      double f[kAnalyticTerms], t = 0.0;
+      analytic_terms(M, N, K, kind, S, cands[i], f);
+      for (int k = 0; k < kAnalyticTerms; ++k) t += g_analytic[kind][k] * f[k];
+      if (t < best_t) {
+        best_t = t;
+        bi = (int)i;
+      }
+    }
+    *how = HSUMMA_CHOSEN_ANALYTIC;
   } else if (policy == HSUMMA_CHOOSE_MODEL || (policy == HSUMMA_CHOOSE_AUTO && have_model)) {
     st = pick_by_model(M, N, K, kind, S, cands, s, &bi);
     if (st != HSUMMA_OK) return st;
@@ -307,6 +360,41 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
   cfg[0] = c.P, cfg[1] = c.Q, cfg[2] = c.G, cfg[3] = c.b, cfg[4] = c.Bo;
   std::lock_guard<std::mutex> lock(g_mu);
   g_cache[key] = c;
+  return HSUMMA_OK;
+}
+
+int hsumma_analytic_terms(int64_t M, int64_t N, int64_t K, int mode, const int *cfg, int n,
+                          double *terms) {
+  int kind, S;
+  int st = decode_mode(mode, &kind, &S);
+  if (st != HSUMMA_OK) return st;
+  if (n < 0 || (n > 0 && (!cfg || !terms)) || M < 0 || N < 0 || K < 0) {
+    set_error("bad arguments");
+    return HSUMMA_ERR_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const Cand c{cfg[5 * i], cfg[5 * i + 1], cfg[5 * i + 2], cfg[5 * i + 3], cfg[5 * i + 4]};
+    if (c.P < 1 || c.Q < 1 || c.G < 1 || c.b < 1 || c.Bo < 1) {
+      set_error("bad configuration");
+      return HSUMMA_ERR_ARG;
+    }
+    analytic_terms(M, N, K, kind, S, c, terms + (size_t)i * kAnalyticTerms);
+  }
+  return HSUMMA_OK;
+}
+
+int hsumma_analytic_load(const double *coef) {
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!coef) {
+      g_analytic_loaded = false;
+    } else {
+      for (int k = 0; k < 3; ++k)
+        for (int t = 0; t < kAnalyticTerms; ++t) g_analytic[k][t] = coef[k * kAnalyticTerms + t];
+      g_analytic_loaded = true;
+    }
+  }
+  forget_choices();
   return HSUMMA_OK;
 }
 

@@ -1,9 +1,11 @@
 """Host logic of the automatic configuration (no GPU): the candidate sets
 follow the group rule of Section III as the oracle states it, the features are
 the stated logarithms, the seeded tuning shapes keep their ranges, the paper's
-standard setting picks G nearest sqrt(p) (Section IV), and -- once tuning data
+standard setting picks G nearest sqrt(p) (Section IV), the analytic policy's
+terms reduce to Section IV's Table I on square grids, and -- once tuning data
 is committed -- the committed model, evaluated by the float64 oracle network,
-stays within 10% of the exhaustive best on the held-out products."""
+stays within 10% of the exhaustive best on the held-out products, and the
+fitted analytic model beats the paper's static and sampled tunings."""
 import math
 import os
 
@@ -111,3 +113,74 @@ def test_committed_model_on_held_out_products_by_oracle_network():
     assert rep["model"]["n"] == 200
     assert rep["model"]["geomean"] <= 1.10
     assert rep["model"]["geomean"] < rep["paper_rule"]["geomean"]
+
+
+@pytest.mark.parametrize("n,P,G,b,B", [(4096, 16, 16, 64, 256), (8192, 16, 4, 32, 128),
+                                       (1024, 8, 64, 32, 32), (2048, 4, 1, 64, 512)])
+def test_analytic_terms_reduce_to_table_one_on_square_grids(n, P, G, b, B):
+    # Section IV, Table I (binomial trees): latency factor log2(p/G) n/b +
+    # log2(G) n/B, bandwidth factor (log2(p/G) + log2 G) n^2/sqrt(p), computation
+    # 2 n^3 / p -- each times the waves the grid needs on 152 SMs
+    I, J, _, _ = hs.group_shape(P, P, G)
+    assert I == J
+    T = hs.analytic_terms(n, n, n, [(P, P, G, b, B)], "fp64")[0]
+    p = P * P
+    W = math.ceil(p / 152)
+    t1 = cost_model.table1(n, p, G, b, B)["hsumma"]
+    assert T[0] == pytest.approx(W * t1["comp"], rel=1e-12)
+    assert T[1] == pytest.approx(W * (t1["lat_in"] + t1["lat_out"]), rel=1e-12)
+    assert T[2] == pytest.approx(W * (t1["band_in"] + t1["band_out"]), rel=1e-12)
+    assert T[3] == 0 and T[4] == 1
+    # the split paths count K once per slice pair and add the slicing volume
+    Ts = hs.analytic_terms(n, n, n, [(P, P, G, b, B)], "bf16", 5)[0]
+    assert Ts[0] == pytest.approx(15 * T[0], rel=1e-12)
+    assert Ts[3] == 2 * n * n * 5
+
+
+def test_analytic_terms_rectangular_restatement():
+    M, N, K = 3000, 5000, 1700
+    for P, Q, G, b, B in [(12, 20, 16, 64, 256), (24, 20, 480, 64, 1024), (6, 10, 1, 128, 512)]:
+        I, J, _, _ = hs.group_shape(P, Q, G)
+        T = hs.analytic_terms(M, N, K, [(P, Q, G, b, B)], "int8", 4)[0]
+        W = math.ceil(P * Q / 152)
+        Mt, Nt, Ke = math.ceil(M / P), math.ceil(N / Q), K * 10
+        lg = lambda x: math.log2(x) if x > 1 else 0.0
+        assert T[0] == pytest.approx(W * 2 * Mt * Nt * Ke)
+        assert T[1] == pytest.approx(W * (Ke / b * (lg(Q / J) + lg(P / I)) + Ke / B * (lg(J) + lg(I))))
+        assert T[2] == pytest.approx(W * Ke * (Mt * (lg(Q / J) + lg(J)) + Nt * (lg(P / I) + lg(I))))
+        assert T[3] == (M + N) * K * 4
+
+
+def test_analytic_fit_and_policies_on_committed_data():
+    path = os.path.join(autotune.TUNING_DIR, "heldout.npz")
+    if not os.path.exists(path):
+        pytest.skip("no committed tuning data")
+    rows = np.load(os.path.join(autotune.TUNING_DIR, "samples.npz"))["rows"]
+    coef = autotune.fit_analytic(rows)
+    assert coef.shape == (3, 5) and np.all(coef >= 0)
+    assert np.all(coef[:, 0] > 0)                       # every kind pays for computation
+    # the fitted model explains the training timings to within a factor ~1.3 (median)
+    ratios = []
+    for r in rows:
+        kc = int(r[3])
+        T = hs.analytic_terms(int(r[0]), int(r[1]), int(r[2]), [tuple(int(v) for v in r[5:10])],
+                              autotune.KIND_NAME[kc], int(r[4]))[0]
+        ratios.append(abs(math.log(T @ coef[kc] / (r[10] * 1e-3))))
+    assert math.exp(np.median(ratios)) < 1.3
+    # on the held-out products: the fitted model beats the paper's static and
+    # sampled tunings; the learned network is at least as good as the fitted model
+    model = autotune.read_model()
+    model["analytic"] = coef
+    held = autotune.load_heldout(path)
+
+    def picker(h):
+        cfgs = [tuple(int(v) for v in c) for c in h["cfg"]]
+        X = hs.features(h["M"], h["N"], h["K"], cfgs, h["kind"], h["S"]).astype(np.float64)
+        pred, _ = mlp.forward(model["theta"].astype(np.float64),
+                              (X - model["mean"].astype(np.float64)) / model["std"].astype(np.float64))
+        return int(np.argmin(pred))
+
+    rep = autotune.evaluate(model, held, picker=picker)
+    g = {k: rep[k]["geomean"] for k in ("model", "analytic", "sampled", "paper_rule")}
+    assert g["analytic"] < g["sampled"] < g["paper_rule"]
+    assert g["model"] <= g["analytic"] * 1.01

@@ -217,3 +217,26 @@ def test_model_pick_holds_when_retimed():
     print("RETIMED", [round(r, 3) for r in ratios])
     assert max(ratios) <= 1.25
     assert math.exp(np.mean(np.log(ratios))) <= 1.10
+
+
+def test_analytic_policy_picks_and_computes():
+    hs = lib_ready()
+    torch = torch_cuda()
+    from paper_1306_4161_gb300 import autotune
+    m = autotune.read_model()
+    if "analytic" not in m:
+        pytest.skip("no committed analytic coefficients")
+    hs.load_analytic(m["analytic"])
+    M, N, K = 1200, 900, 640
+    dA, dB, want = _exact_pair(torch, M, N, K, 95)
+    cfg, how = hs.choose(dA, dB, kind="fp64", policy="analytic")
+    assert how == "analytic" and cfg in hs.candidates(M, N, K, "fp64")
+    T = hs.analytic_terms(M, N, K, hs.candidates(M, N, K, "fp64"), "fp64")
+    assert hs.candidates(M, N, K, "fp64").index(cfg) == int(np.argmin(T @ m["analytic"][0]))
+    C = hs.gemm(dA, dB, P=cfg[0], Q=cfg[1], G=cfg[2], b=cfg[3], Bouter=cfg[4])
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), want)
+    hs.load_analytic(None)
+    with pytest.raises(hs.HsummaError):
+        hs.choose(dA, dB, kind="fp64", policy="analytic")
+    autotune.load_into_library()
