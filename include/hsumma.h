@@ -316,6 +316,14 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *d_A,
  * Results are identical either way. */
 int hsumma_pair_kernel(int enable);
 
+/* Self-test of the failure handling (the paper has no counterpart): launches
+ * one block that waits on a shared-memory barrier nothing arrives on, gives up
+ * after limit_ns (0 .. 1e9) of device time, and records HSUMMA_ERR_TIMEOUT in
+ * the device status word exactly as a GEMM kernel whose wait ran out would;
+ * the next hsumma_sync on the stream returns HSUMMA_ERR_TIMEOUT ("self-test
+ * wait") and clears the word.  Nothing faults or hangs. */
+int hsumma_selftest_timeout(long long limit_ns, void *stream);
+
 /* ---- Stage timing ----
  * Per-kernel device time of hsumma_gemm on the caller's stream, for measuring
  * the path while it runs.  hsumma_stage_timing(1) clears the record and makes

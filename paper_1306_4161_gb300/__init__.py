@@ -73,6 +73,7 @@ _SIGS = {
     "hsumma_mlp_pick": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hsumma_mlp_load": ([_vp, _vp, _vp], _i32),
     "hsumma_pair_kernel": ([_i32], _i32),
+    "hsumma_selftest_timeout": ([ctypes.c_longlong, _vp], _i32),
     "hsumma_stage_timing": ([_i32], _i32),
     "hsumma_stage_times": ([_vp, ctypes.POINTER(ctypes.c_int)], _i32),
     "hsumma_candidates": ([_i64, _i64, _i64, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_int)],

@@ -737,9 +737,9 @@ int hsumma_sync(void *stream) {
   if (h[0] != 0) {
     cudaMemset(g_state.d_status, 0, sizeof(h));
     static const char *sites[] = {"?", "stage fill", "stage release", "accumulator fill",
-                                  "accumulator drain", "non-finite input"};
+                                  "accumulator drain", "non-finite input", "self-test wait"};
     set_error("device error %d at %s (block %d)", h[0],
-              (h[1] >= 0 && h[1] <= 5) ? sites[h[1]] : "?", h[2]);
+              (h[1] >= 0 && h[1] <= 6) ? sites[h[1]] : "?", h[2]);
     return h[0];
   }
   return HSUMMA_OK;

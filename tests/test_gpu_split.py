@@ -340,3 +340,22 @@ def test_host_entry_pipelined_by_row_blocks(kind, S, M, N, K, P, Q, G, pinned):
         want = split.split_gemm(An, Bn, S, kind)
     assert np.array_equal(hC, want)
     assert np.all(big[:, N:] == 7.0)
+
+
+def test_a_wait_that_runs_out_is_reported_and_cleared():
+    # the bounded-wait machinery itself: a barrier nothing arrives on, a 2 ms
+    # limit, the status word read and cleared by hsumma_sync, the context usable
+    hs = lib_ready()
+    torch = torch_cuda()
+    hs._check(hs.lib().hsumma_selftest_timeout(2_000_000, None))
+    with pytest.raises(hs.HsummaError) as ei:
+        hs.sync(None)
+    assert ei.value.status == -4
+    assert "self-test wait" in str(ei.value)
+    hs.sync(None)                                   # cleared
+    with pytest.raises(hs.HsummaError):
+        hs._check(hs.lib().hsumma_selftest_timeout(2_000_000_000, None))   # limit too long
+    A, B, dA, dB = pair(200, 300, 700, 31, "uniform")
+    C = hs.gemm(dA, dB, P=2, Q=2, G=1, b=64, Bouter=128, kind="bf16", slices=3)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 3, "bf16"))
