@@ -339,7 +339,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(smem_u32(&acc_empty[who]), 0u);
+                // hand the accumulator back to the leader: the loads have completed
+                // and nothing was written, so no release ordering is needed
+                if (lane == 0) {
+                  if (leader)
+                    mbar_arrive(smem_u32(&acc_empty[who]));
+                  else
+                    mbar_arrive_cluster_relaxed(smem_u32(&acc_empty[who]), 0u);
+                }
                 if (who) ++nchunk1; else ++nchunk0;
               }
               if (!ok) break;
