@@ -113,9 +113,9 @@ bool encode_tmap_3d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
 static int launch_split_diagonals(const GridPlan &g, int kind, int S, const void *As,
                                   const void *Bs, int32_t *D, cudaStream_t s) {
   if (kind == HSUMMA_BF16_SLICES) {
-    // groups of two vertically adjacent processors may run on CTA pairs
-    // (hsumma_pair_kernel); every other group shape on the single-CTA kernel
-    if (g.cm == 2 && g.cn == 1 && g_state.bf16_pair)
+    // groups of 2 x 1 and 2 x 2 processors may run on CTA pairs (clusters of
+    // one or two pairs, hsumma_pair_kernel); every other shape on one CTA each
+    if (g.cm == 2 && (g.cn == 1 || g.cn == 2) && g_state.bf16_pair)
       return launch_split_bf16_pair(g, S, As, Bs, D, s);
     return launch_split_bf16(g, S, As, Bs, D, s);
   }

@@ -1,7 +1,10 @@
 // Split-precision HSUMMA, step 3 with bf16 slices on CTA pairs: the same exact
 // diagonal sums as split_bf16.cu, for groups of two vertically adjacent
 // processors (in-group grid 2 x 1), with every MMA spanning the pair's two SMs
-// (tcgen05 cta_group::2, 256 x 256 x 16).
+// (tcgen05 cta_group::2, 256 x 256 x 16), and for groups of 2 x 2 processors
+// as clusters of two such pairs (the three-level hierarchy: owners stage outer
+// panels in L2, the cluster multicasts A along each processor row, the pair
+// shares B through its MMA).
 //
 // The two processors of a group need the same 256 B columns and different A
 // rows.  Each CTA loads its own 128 rows of A and one half (128 columns) of the
@@ -20,6 +23,12 @@
 // stage's MMA completion releases the stage in both CTAs, and each chunk end
 // hands the accumulator to the drain warps of both CTAs, which return it to
 // the leader.  Every wait is bounded (4 s) and ends in an error status.
+//
+// 2 x 2 groups: the two CTAs of a processor row each load one half (64 rows)
+// of the row's A tile and multicast it to both (cta_group::2 copies that count
+// the bytes on each destination's pair leader); a stage is released in all
+// four CTAs once both pairs' MMAs have read it (the commits of both leaders,
+// multicast to the cluster).
 //
 // Roles (384 threads per CTA): warp 0 issues the copies, warps 1 and 2 issue
 // the MMAs (leader only; warp 1 of each CTA owns its tensor memory), warp 3
@@ -42,7 +51,6 @@ constexpr int SEGST = 127 * CH;        // stages per int32 segment
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC2 = idesc_bf16_f32(2 * TM, TN);
-constexpr uint16_t PAIR = 3;           // both CTAs of the cluster
 
 struct PairParams {
   int32_t *D;
@@ -75,17 +83,21 @@ __device__ __forceinline__ bool chunk_end(int local, int seg_len) {
   return (local & 1) ? ((c + 8) % CH == 0) : (c % CH == 0);
 }
 
-// group tile L -> processor row r (of this CTA) and column c: tiles walked
+// group tile L -> processor row r and column c of the CTA that is member `ry`
+// of pair `px` of the group's cluster (CN pairs side by side): tiles walked
 // down columns of 8 group rows
-__device__ __forceinline__ void tile_proc(int L, int ncx, int ncy, int ry, int *r, int *c) {
+template <int CN>
+__device__ __forceinline__ void tile_proc(int L, int ncx, int ncy, int ry, int px, int *r,
+                                          int *c) {
   const int rows = 8;
   const int group = L / (rows * ncx);
   const int in_group = min(rows, ncy - group * rows);
   const int idx = L - group * rows * ncx;
   *r = (group * rows + idx % in_group) * 2 + ry;
-  *c = idx / in_group;
+  *c = (idx / in_group) * CN + px;
 }
 
+template <int CN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     bf16_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB,
@@ -101,16 +113,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ry = (int)cluster_ctaid_x();          // 0: leader, 1: second CTA of the pair
+  // cluster rank = 2 px + ry: pair px (the group's column), member ry (its row)
+  const int rank = (int)cluster_ctarank();
+  const int ry = rank & 1, px = rank >> 1;
   const bool leader = ry == 0;
-  const int ncx = p.Q, ncy = p.P / 2, ntiles = ncx * ncy;
-  const int ncl = (int)gridDim.x / 2, cid = (int)blockIdx.x / 2;
+  const int lead = rank & ~1;                     // this pair's first CTA
+  const uint16_t all_mask = (uint16_t)((1u << (2 * CN)) - 1u);
+  const uint16_t pair_mask = (uint16_t)(3u << lead);
+  const uint16_t row_mask = CN == 2 ? (uint16_t)((1u << ry) | (1u << (ry + 2))) : (uint16_t)1u;
+  const int ncx = p.Q / CN, ncy = p.P / 2, ntiles = ncx * ncy;
+  const int ncl = (int)gridDim.x / (2 * CN), cid = (int)blockIdx.x / (2 * CN);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&empty[s]), CN);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
@@ -138,16 +156,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ---------------- copies (both CTAs) ----------------
     if (lane == 0) {
-      unsigned long long a_ld = 0, b_ld = 0, pf = 0, nops = 0;
+      unsigned long long a_ld = 0, a_dl = 0, b_ld = 0, pf = 0, nops = 0;
       uint32_t stage = 0, phase = 0;
       bool ok = true;
       for (int L = cid; L < ntiles && ok; L += ncl) {
         int r, c;
-        tile_proc(L, ncx, ncy, ry, &r, &c);
+        tile_proc<CN>(L, ncx, ncy, ry, px, &r, &c);
         const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
         const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
         for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
           const int64_t m0 = row_lo + (int64_t)mi * TM;
+          const int64_t am0 = m0 + (CN == 2 ? px * (TM / 2) : 0);   // this CTA's A rows
           for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
             const int64_t n0 = col_lo + (int64_t)ni * TN;
             const int64_t nh = n0 + ry * HN;
@@ -193,18 +212,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   }
                   const uint32_t a_dst = smem_u32(smem + stage * STAGE_BYTES);
                   const uint32_t b_dst = a_dst + A_BYTES;
-                  if (leader) {
-                    const uint32_t fb = smem_u32(&full[stage]);
-                    mbar_arrive_expect_tx(fb, 2 * STAGE_BYTES);
+                  // the pair leader's barrier counts the stage's bytes of both CTAs
+                  const uint32_t fb = cluster_addr(smem_u32(&full[stage]), (uint32_t)lead);
+                  if (leader) mbar_arrive_expect_tx(smem_u32(&full[stage]), 2 * STAGE_BYTES);
+                  if (CN == 2) {
+                    // half of the row's A tile, to both CTAs of the processor row
+                    tma_load_3d_pair_mc(a_dst + px * (A_BYTES / 2), &tmA, (int32_t)k0,
+                                        (int32_t)am0, s - 1, fb, row_mask);
+                  } else if (leader) {
                     tma_load_3d(a_dst, &tmA, (int32_t)k0, (int32_t)m0, s - 1, fb);
-                    tma_load_3d(b_dst, &tmB, (int32_t)k0, (int32_t)nh, t - 1, fb);
                   } else {
-                    const uint32_t fb = cluster_addr(smem_u32(&full[stage]), 0);
                     tma_load_3d_pair(a_dst, &tmA, (int32_t)k0, (int32_t)m0, s - 1, fb);
-                    tma_load_3d_pair(b_dst, &tmB, (int32_t)k0, (int32_t)nh, t - 1, fb);
                   }
+                  if (leader)
+                    tma_load_3d(b_dst, &tmB, (int32_t)k0, (int32_t)nh, t - 1, fb);
+                  else
+                    tma_load_3d_pair(b_dst, &tmB, (int32_t)k0, (int32_t)nh, t - 1, fb);
                   const int64_t kc = span(0, p.K, k0, k0 + BKS);
-                  a_ld += span(row_lo, row_hi, m0, m0 + TM) * kc;
+                  const int64_t ca = span(row_lo, row_hi, am0, am0 + TM / CN) * kc;
+                  a_ld += ca;
+                  a_dl += ca * CN;
                   b_ld += span(col_lo, col_hi, nh, nh + HN) * kc;
                   nops += 2;
                   if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -223,9 +250,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
       }
-      // A rows reach this CTA only; each half of B reaches both CTAs' products
+      // A rows reach the CN CTAs of their processor row in the cluster; each
+      // half of B reaches both CTAs' products
       atomicAdd(&p.counters[0], a_ld);
-      atomicAdd(&p.counters[1], a_ld);
+      atomicAdd(&p.counters[1], a_dl);
       atomicAdd(&p.counters[2], b_ld);
       atomicAdd(&p.counters[3], 2 * b_ld);
       atomicAdd(&p.counters[4], pf);
@@ -276,9 +304,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   mma2_bf16(dt, sdesc_k128(a_addr + k * 32), sdesc_k128(b_addr + k * 32), IDESC2,
                             (first && k == 0) ? 0u : 1u);
                 }
-                mma2_commit_mc(smem_u32(&empty[stage]), PAIR);
+                mma2_commit_mc(smem_u32(&empty[stage]), all_mask);
                 if (chunk_end(local, seg_len)) {
-                  mma2_commit_mc(smem_u32(&acc_full[me]), PAIR);
+                  mma2_commit_mc(smem_u32(&acc_full[me]), pair_mask);
                   ++nchunk;
                   in_chunk = false;
                 }
@@ -296,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool ok = true;
     for (int L = cid; L < ntiles && ok; L += ncl) {
       int r, c;
-      tile_proc(L, ncx, ncy, ry, &r, &c);
+      tile_proc<CN>(L, ncx, ncy, ry, px, &r, &c);
       const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
       const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
       for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
@@ -345,7 +373,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   if (leader)
                     mbar_arrive(smem_u32(&acc_empty[who]));
                   else
-                    mbar_arrive_cluster_relaxed(smem_u32(&acc_empty[who]), 0u);
+                    mbar_arrive_cluster_relaxed(smem_u32(&acc_empty[who]), (uint32_t)lead);
                 }
                 if (who) ++nchunk1; else ++nchunk0;
               }
@@ -390,14 +418,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void *Bs, int32_t *D,
                            cudaStream_t s) {
-  if (g.cm != 2 || g.cn != 1 || g.P % 2) {
-    set_error("the CTA-pair kernel needs groups realised as 2 x 1 clusters");
+  if (g.cm != 2 || (g.cn != 1 && g.cn != 2) || g.P % 2 || g.Q % g.cn) {
+    set_error("the CTA-pair kernel needs groups realised as 2 x 1 or 2 x 2 clusters");
     return HSUMMA_ERR_ARG;
   }
+  const int CN = g.cn;
   const int64_t Kpad = ceil_div(g.K, 64) * 64;
   const auto BF16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap tA, tB, tApf, tBpf;
-  if (!encode_tmap_3d(&tA, BF16, 2, As, Kpad, g.M, S, BKS, TM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+  if (!encode_tmap_3d(&tA, BF16, 2, As, Kpad, g.M, S, BKS, TM / CN,
+                      CU_TENSOR_MAP_SWIZZLE_128B) ||
       !encode_tmap_3d(&tB, BF16, 2, Bs, Kpad, g.N, S, BKS, HN, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !encode_tmap_3d(&tApf, BF16, 2, As, Kpad, g.M, S, BKS, TM, CU_TENSOR_MAP_SWIZZLE_NONE) ||
       !encode_tmap_3d(&tBpf, BF16, 2, Bs, Kpad, g.N, S, BKS, TN, CU_TENSOR_MAP_SWIZZLE_NONE))
@@ -422,23 +452,24 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   p.nseg = split_planes(g.K, S, HSUMMA_BF16_SLICES);
   p.counters = state().d_counters;
   p.status = state().d_status;
-  cudaError_t e = cudaFuncSetAttribute(bf16_pair_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  auto kern = CN == 2 ? bf16_pair_kernel<2> : bf16_pair_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair smem)");
   cudaLaunchConfig_t cfg = {};
-  const int ntiles = (g.P / 2) * g.Q;
-  cfg.gridDim = dim3((unsigned)(2 * ntiles), 1, 1);
+  const int ntiles = (g.P / 2) * (g.Q / CN);
+  cfg.gridDim = dim3((unsigned)(2 * CN * ntiles), 1, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.x = (unsigned)(2 * CN);
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, bf16_pair_kernel, tA, tB, tApf, tBpf, p);
+  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
   return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "launch bf16 pair kernel");
 }
 

@@ -188,6 +188,19 @@ __device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const void *tm, i
       : "memory");
 }
 
+// 3-D tile load multicast to the CTAs in `mask`, whose bytes are counted, for
+// each destination CTA, on the mbarrier at `bar`'s offset in the first CTA of
+// that destination's CTA pair (cta_group::2)
+__device__ __forceinline__ void tma_load_3d_pair_mc(uint32_t dst, const void *tm, int32_t x,
+                                                    int32_t y, int32_t z, uint32_t bar,
+                                                    uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster.cta_group::2 [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const void *tm, int32_t x,
                                                int32_t y, int32_t z, uint32_t bar,
                                                uint16_t mask) {

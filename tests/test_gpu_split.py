@@ -247,13 +247,17 @@ def test_odd_leading_dimensions():
     (600, 700, 640, 4, 3, 6, 2, 128),         # 2 x 1 groups, ragged blocks and sub-tiles
     (1030, 1100, 700, 8, 4, 16, 3, 1024),     # 2 x 1 groups, B longer than K
     (512, 2048, 4096, 2, 4, 4, 4, 256),       # several chunks per diagonal
+    (256, 512, 640, 2, 2, 1, 3, 128),         # one 2 x 2 group: two pairs, A multicast
+    (600, 1100, 700, 4, 4, 4, 3, 256),        # 2 x 2 groups, ragged blocks and sub-tiles
+    (1030, 1000, 900, 8, 4, 8, 2, 1024),      # 2 x 2 groups, B longer than K
+    (512, 1024, 4096, 2, 2, 1, 4, 512),       # 2 x 2, several chunks per diagonal
 ])
 def test_bf16_pair_kernel_exact(M, N, K, P, Q, G, S, Bo):
-    # groups realised as 2 x 1 clusters run on CTA pairs when asked
+    # groups realised as 2 x 1 or 2 x 2 clusters run on CTA pairs when asked
     hs = lib_ready()
     torch = torch_cuda()
     I, J, cm, cn = hs.group_shape(P, Q, G)
-    assert (cm, cn) == (2, 1)
+    assert (cm, cn) in ((2, 1), (2, 2))
     A, B, dA, dB = pair(M, N, K, 29, "wide", "uniform")
     e, f = hs.split_exponents(dA, dB)
     As, Bs = hs.split_slices(dA, dB, e, f, "bf16", S)
