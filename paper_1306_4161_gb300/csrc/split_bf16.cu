@@ -371,14 +371,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_after();
                 const uint32_t ta =
                     tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(who * TN) + h * 128;
+                // two 16-column loads in flight per wait: four round trips
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                  uint32_t v[16];
+                for (int j = 0; j < 8; j += 2) {
+                  uint32_t v[16], w[16];
                   tmem_ld16(ta + j * 16, v);
+                  tmem_ld16(ta + j * 16 + 16, w);
                   tmem_ld_wait();
 #pragma unroll
-                  for (int i = 0; i < 16; ++i)
+                  for (int i = 0; i < 16; ++i) {
                     acc[j * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
+                    acc[j * 16 + 16 + i] += __float2int_rn(__uint_as_float(w[i]));
+                  }
                 }
                 tc_fence_before();
                 __syncwarp();
