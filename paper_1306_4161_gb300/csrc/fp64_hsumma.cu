@@ -112,9 +112,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int64_t m0 = row_lo + (int64_t)mi * TM;
         for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
           const int64_t n0 = col_lo + (int64_t)ni * TN;
+          int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
           for (int64_t kt = 0; kt < nk; ++kt) {
             const int64_t k0 = kt * BK;
-            if (k0 % p.Bo == 0) {
+            const bool outer = rem == 0;
+            for (rem += BK; rem >= p.Bo;) rem -= p.Bo;
+            if (outer) {
               // outer step o: stage outer panel o (first step) and o + 1 into L2;
               // the owner of an outer block is the processor whose own block of
               // A (columns) / B (rows) contains its first index

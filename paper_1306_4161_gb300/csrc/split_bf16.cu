@@ -175,9 +175,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int d = 2; d <= S + 1 && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
+                int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
                 for (int kb = 0; kb < nkb; ++kb) {
                   const int64_t k0 = (int64_t)kb * BKS;
-                  if (k0 % p.Bo == 0) {
+                  const bool outer = rem == 0;
+                  for (rem += BKS; rem >= p.Bo;) rem -= p.Bo;
+                  if (outer) {
                     // outer step o of pair (s, t): the owners stage the next outer
                     // panel into L2 -- panel o + 1 of this pair, or, at the last
                     // outer step, panel 0 of the next pair of the sub-tile -- so the

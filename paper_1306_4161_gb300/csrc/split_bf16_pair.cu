@@ -173,9 +173,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int d = 2; d <= S + 1 && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
+                int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
                 for (int kb = 0; kb < nkb; ++kb) {
                   const int64_t k0 = (int64_t)kb * BKS;
-                  if (k0 % p.Bo == 0) {
+                  const bool outer = rem == 0;
+                  for (rem += BKS; rem >= p.Bo;) rem -= p.Bo;
+                  if (outer) {
                     // owners stage the next outer panel into L2, one outer block
                     // ahead without gaps (the rule of split_bf16.cu)
                     const int64_t o = k0 / p.Bo;

@@ -112,9 +112,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int d = 2; d <= S + 1 && ok; ++d) {
             for (int s = 1; s < d && ok; ++s) {
               const int t = d - s;
+              int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
               for (int kb = 0; kb < nkb; ++kb) {
                 const int64_t k0 = (int64_t)kb * BKS;
-                if (k0 % p.Bo == 0) {
+                const bool outer = rem == 0;
+                for (rem += BKS; rem >= p.Bo;) rem -= p.Bo;
+                if (outer) {
                   const int64_t o = k0 / p.Bo;
                   for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
                     const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
