@@ -212,7 +212,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           const uint8_t *a_base = sA + stage * A_STAGE;
           const uint8_t *b_base = sB + stage * B_STAGE;
-#pragma unroll
+          // not unrolled: the unrolled loop's hoisted fragment loads spill
+          // registers at the 168-per-thread limit of a 9-warp block
+#pragma unroll 1
           for (int kk = 0; kk < BK / 4; ++kk) {
             const int k = kk * 4 + t;
             double af[4][2], bf[4];
