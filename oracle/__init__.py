@@ -14,9 +14,11 @@ generator (workloads.py), which holds none of the method's arithmetic.
 Modules
   native        binary64 triple-loop GEMM and Dot2 compensated entries (plain C)
   split         Ozaki-style slicing, exact pair products, exact recombination
-  hsumma_sim    distributed SUMMA / HSUMMA simulation with broadcast counters
+  hsumma_sim    distributed SUMMA / HSUMMA simulation with broadcast counters,
+                block-checkerboard and block-cyclic distributions
   cost_model    the paper's Hockney-model costs (Section IV)
-  gpu_schedule  group resolution and the GPU panel-load counter model
+  gpu_schedule  group resolution and the GPU panel-load counter model (block
+                and block-cyclic layouts)
   mlp           float64 MLP forward / backward / Adam
 
 Parity status: every function above is pinned by tests that do not reuse its

@@ -16,6 +16,15 @@ Nt = ceil(N/Q), which it sweeps in tm x tn sub-tiles in a fixed order.
   * outer, between-group broadcast (Figure 3): at each outer step the group that
     owns the outer block (Algorithm 1's Pivot_group_col / Pivot_group_row)
     prefetches the next outer panels into L2, from where every group reads them.
+
+Block-cyclic layout (Section VI's future-work distribution, here with the
+sub-tile as the distribution block): CTA (r, c) sweeps the sub-tiles of tile
+rows r, r + P, r + 2P, ... and tile columns c, c + Q, ...; every CTA sweeps the
+nominal ceil(ceil(M/tm)/P) x ceil(ceil(N/tn)/Q) sub-tiles in lockstep with its
+cluster, and skips a sub-tile when its whole cluster lies outside the matrix
+(the cluster's first tile row at or past M, or its first tile column at or
+past N).  The owner of outer block o is processor column o mod Q (A) and
+processor row o mod P (B).
 """
 from __future__ import annotations
 
@@ -53,7 +62,42 @@ def ceil_div(a, b):
     return -(-a // b)
 
 
-def counters_closed_form(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs=1):
+def _active_steps(T, P, cm, r):
+    """Sub-steps i of processor row r (block-cyclic layout) whose cluster,
+    with first row r - r % cm, holds a tile row r - r % cm + i P < T."""
+    r0 = r - r % cm
+    return ceil_div(T - r0, P) if r0 < T else 0
+
+
+def _owned_outer(nout, q, who):
+    """Outer blocks o < nout with o mod q == who."""
+    return ceil_div(nout - who, q) if who < nout else 0
+
+
+def counters_closed_form_cyclic(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs=1):
+    """Panel-load counters of one launch in the block-cyclic layout.
+
+    With Tm = ceil(M/tm), Tn = ceil(N/tn) tiles and act_m(r), act_n(c) the
+    sub-steps a CTA row / column does not skip, every tile row is swept once
+    per active column step, so
+      a_delivered = npairs * M * K * sum_c act_n(c),  a_loaded = a_delivered / cn
+      b_delivered = npairs * K * N * sum_r act_m(r),  b_loaded = b_delivered / cm
+      l2_prefetch = npairs * sum_{r,c} act_m(r) act_n(c) (own_Q(c) + own_P(r))
+    with own_Q(c) the outer blocks o with o mod Q = c."""
+    Tm, Tn = ceil_div(M, tm), ceil_div(N, tn)
+    nout = ceil_div(K, Bo) if K else 0
+    am = [_active_steps(Tm, P, cm, r) for r in range(P)]
+    an = [_active_steps(Tn, Q, cn, c) for c in range(Q)]
+    sm, sn = sum(am), sum(an)
+    assert sm % cm == 0 and sn % cn == 0
+    pf = (sm * sum(an[c] * _owned_outer(nout, Q, c) for c in range(Q))
+          + sn * sum(am[r] * _owned_outer(nout, P, r) for r in range(P)))
+    return dict(a_loaded=npairs * M * K * sn // cn, a_delivered=npairs * M * K * sn,
+                b_loaded=npairs * K * N * sm // cm, b_delivered=npairs * K * N * sm,
+                l2_prefetch=npairs * pf)
+
+
+def counters_closed_form(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs=1, cyclic=False):
     """Panel-load counters of one launch, in elements.
 
     a_loaded    = npairs * (Q / cn) * nsub_n * M * K   (one load per cluster row)
@@ -63,7 +107,10 @@ def counters_closed_form(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs=1):
     l2_prefetch = npairs * nsub_m * nsub_n * ceil(K / Bo) * (P + Q)
     with nsub_m = ceil(ceil(M/P) / tm), nsub_n = ceil(ceil(N/Q) / tn) sub-tiles
     per CTA (every CTA sweeps the nominal count so that a cluster runs in
-    lockstep; rows and columns outside its block are not counted)."""
+    lockstep; rows and columns outside its block are not counted).
+    cyclic=True: the block-cyclic layout (counters_closed_form_cyclic)."""
+    if cyclic:
+        return counters_closed_form_cyclic(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs)
     Mt, Nt = ceil_div(M, P), ceil_div(N, Q)
     nsm, nsn = ceil_div(Mt, tm), ceil_div(Nt, tn)
     nout = ceil_div(K, Bo) if K else 0
@@ -76,12 +123,15 @@ def counters_closed_form(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs=1):
     )
 
 
-def counters_enumerated(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs=1):
+def counters_enumerated(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs=1, cyclic=False):
     """The same counters by walking every CTA and sub-tile: the CTA at cluster
     column rank x issues the rows [x*tm/cn, (x+1)*tm/cn) of each A sub-tile panel
     (multicast to its cluster row); the CTA at cluster row rank y issues the
     columns [y*tn/cm, (y+1)*tn/cm) of each B sub-tile panel; only elements
-    inside the CTA's block and the matrix count."""
+    inside the CTA's block and the matrix count.  cyclic=True walks the
+    block-cyclic layout, sub-tile by sub-tile and outer block by outer block."""
+    if cyclic:
+        return _counters_enumerated_cyclic(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs)
     Mt, Nt = ceil_div(M, P), ceil_div(N, Q)
     nsm, nsn = ceil_div(Mt, tm), ceil_div(Nt, tn)
     out = dict(a_loaded=0, a_delivered=0, b_loaded=0, b_delivered=0, l2_prefetch=0)
@@ -106,6 +156,38 @@ def counters_enumerated(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs=1):
     # outer step: one A panel prefetch per processor row and one B panel
     # prefetch per processor column, per sub-tile and outer step
     out["l2_prefetch"] = npairs * nsm * nsn * nout * (P + Q)
+    return out
+
+
+def _counters_enumerated_cyclic(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs):
+    Tm, Tn = ceil_div(M, tm), ceil_div(N, tn)
+    nsm, nsn = ceil_div(Tm, P), ceil_div(Tn, Q)
+    nout = ceil_div(K, Bo) if K else 0
+    out = dict(a_loaded=0, a_delivered=0, b_loaded=0, b_delivered=0, l2_prefetch=0)
+    for r in range(P):
+        for c in range(Q):
+            x, y = c % cn, r % cm
+            r0, c0 = r - y, c - x                 # the cluster's first row and column
+            for mi in range(nsm):
+                if (r0 + mi * P) * tm >= M:       # no row of the cluster in the matrix
+                    continue
+                m0 = (r + mi * P) * tm
+                rlo, rhi = m0, min(M, m0 + tm)
+                for ni in range(nsn):
+                    if (c0 + ni * Q) * tn >= N:
+                        continue
+                    n0 = (c + ni * Q) * tn
+                    clo, chi = n0, min(N, n0 + tn)
+                    a0, a1 = m0 + x * tm // cn, m0 + (x + 1) * tm // cn
+                    arows = max(0, min(a1, rhi) - max(a0, rlo))
+                    out["a_loaded"] += npairs * arows * K
+                    out["a_delivered"] += npairs * cn * arows * K
+                    b0, b1 = n0 + y * tn // cm, n0 + (y + 1) * tn // cm
+                    bcols = max(0, min(b1, chi) - max(b0, clo))
+                    out["b_loaded"] += npairs * bcols * K
+                    out["b_delivered"] += npairs * cm * bcols * K
+                    for o in range(nout):         # the owners of outer block o prefetch
+                        out["l2_prefetch"] += npairs * ((o % Q == c) + (o % P == r))
     return out
 
 

@@ -27,6 +27,18 @@ holder of the outer A block sends its b-wide slice along the in-group row
 (row_comm), the holder of the outer B block along the in-group column (col_comm);
 then the local update.
 
+Block-cyclic distribution (the extension the paper's conclusion names as
+future work, Section VI): the rows of A and C are cut into blocks of mb rows
+dealt round robin to the P processor rows (row block t to processor row
+t mod P), the columns of B and C into blocks of nb dealt to the Q processor
+columns, and the k index into blocks of B (= Bouter) dealt to the processor
+columns (A) and rows (B), so that every outer block has one owner: outer block o
+of A is held by processor column o mod Q, of B by processor row o mod P.  The
+block-checkerboard distribution above is the special case mb = M/P, nb = N/Q
+and k blocks K/Q (A) and K/P (B): one block per processor.  The broadcasts and
+the local update are the same; only the owners (the roots of the outer
+broadcasts) and the rows and columns a processor holds change.
+
 Readings of garbled indices: the outer A broadcast runs
 over the J group columns (the text's range 1..I is read as 1..J) and the inner
 one over the Q/J in-group columns; B swaps the roles; Algorithm 1's tests on
@@ -65,6 +77,48 @@ class BcastStats:
 class SimResult:
     C: np.ndarray
     stats: dict = field(default_factory=dict)   # (level, matrix) -> BcastStats
+    # roots of the outer broadcasts (SUMMA: of every step): "A" -> processor
+    # column of each step's A owner, "B" -> processor row of each B owner
+    roots: dict = field(default_factory=dict)
+
+
+DISTS = ("block", "cyclic")
+
+
+@dataclass(frozen=True)
+class Layout:
+    """Distribution blocks: rows of A and C (mb), columns of B and C (nb), the
+    k index of A (ka, dealt over the Q processor columns) and of B (kb, dealt
+    over the P processor rows)."""
+    mb: int
+    nb: int
+    ka: int
+    kb: int
+
+
+def owned(n: int, owners: int, blk: int, who: int) -> np.ndarray:
+    """The indices in [0, n) that owner `who` of `owners` holds when blocks of
+    `blk` consecutive indices are dealt round robin (block t to owner
+    t mod owners; the last block is clipped at n), ascending."""
+    nblk = -(-n // blk) if n else 0
+    parts = [np.arange(t * blk, min(n, (t + 1) * blk)) for t in range(who, nblk, owners)]
+    return np.concatenate(parts) if parts else np.zeros(0, dtype=np.int64)
+
+
+def make_layout(dist, M, N, K, P, Q, kblk, mb=None, nb=None) -> Layout:
+    """"block": one block per processor (Algorithm 1's block-checkerboard
+    distribution; needs P | M, Q | N, P | K, Q | K).  "cyclic": blocks of mb
+    rows and nb columns, k blocks of `kblk` (the outer width B) for A and B."""
+    if dist == "block":
+        _check_shapes(M, N, K, P, Q)
+        return Layout(M // P, N // Q, K // Q, K // P)
+    if dist == "cyclic":
+        if not (mb and nb and mb > 0 and nb > 0):
+            raise ValueError("the block-cyclic distribution needs block sizes mb, nb >= 1")
+        if K % kblk:
+            raise ValueError("the block-cyclic distribution needs whole k blocks: B | K")
+        return Layout(mb, nb, kblk, kblk)
+    raise ValueError(f"unknown distribution {dist!r}")
 
 
 def _rounds_flat(q, root):
@@ -164,13 +218,40 @@ def _check_shapes(M, N, K, P, Q):
         raise ValueError("block distribution needs P | M, Q | N, P | K, Q | K")
 
 
-def distribute(A, B, P, Q):
-    M, K = A.shape
-    N = B.shape[1]
-    Mt, Nt, Kq, Kp = M // P, N // Q, K // Q, K // P
-    Al = [[A[r * Mt:(r + 1) * Mt, c * Kq:(c + 1) * Kq].copy() for c in range(Q)] for r in range(P)]
-    Bl = [[B[r * Kp:(r + 1) * Kp, c * Nt:(c + 1) * Nt].copy() for c in range(Q)] for r in range(P)]
-    return Al, Bl
+class Distributed:
+    """Every processor's own blocks of A, B and C under a Layout: processor
+    (r, c) holds A[rows[r]][:, acols[c]], B[brows[r]][:, cols[c]] and
+    C[rows[r]][:, cols[c]]."""
+
+    def __init__(self, A, B, P, Q, L: Layout):
+        M, K = A.shape
+        N = B.shape[1]
+        self.P, self.Q, self.L, self.M, self.N = P, Q, L, M, N
+        self.rows = [owned(M, P, L.mb, r) for r in range(P)]
+        self.cols = [owned(N, Q, L.nb, c) for c in range(Q)]
+        self.acols = [owned(K, Q, L.ka, c) for c in range(Q)]
+        self.brows = [owned(K, P, L.kb, r) for r in range(P)]
+        self.Al = [[A[np.ix_(self.rows[r], self.acols[c])] for c in range(Q)] for r in range(P)]
+        self.Bl = [[B[np.ix_(self.brows[r], self.cols[c])] for c in range(Q)] for r in range(P)]
+        self.Cl = [[np.zeros((len(self.rows[r]), len(self.cols[c]))) for c in range(Q)]
+                   for r in range(P)]
+
+    def owner_a(self, k0):
+        """(processor column, local column offset) of the A column k0."""
+        t = k0 // self.L.ka
+        return t % self.Q, (t // self.Q) * self.L.ka + k0 % self.L.ka
+
+    def owner_b(self, k0):
+        """(processor row, local row offset) of the B row k0."""
+        t = k0 // self.L.kb
+        return t % self.P, (t // self.P) * self.L.kb + k0 % self.L.kb
+
+    def gather(self):
+        C = np.zeros((self.M, self.N))
+        for r in range(self.P):
+            for c in range(self.Q):
+                C[np.ix_(self.rows[r], self.cols[c])] = self.Cl[r][c]
+        return C
 
 
 def _local_update(Cl, a, b):
@@ -179,32 +260,30 @@ def _local_update(Cl, a, b):
         Cl += np.multiply.outer(a[:, k], b[k, :])
 
 
-def _gather(Cl, P, Q):
-    return np.block([[Cl[r][c] for c in range(Q)] for r in range(P)])
-
-
-def summa(A, B, P, Q, b, tree="binomial") -> SimResult:
-    """SUMMA (Section II-A) with block width b."""
+def summa(A, B, P, Q, b, tree="binomial", dist="block", mb=None, nb=None) -> SimResult:
+    """SUMMA (Section II-A) with block width b; under the block-cyclic
+    distribution the k blocks are b wide (one pivot block per step)."""
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
     M, K = A.shape
     N = B.shape[1]
-    _check_shapes(M, N, K, P, Q)
-    Mt, Nt, Kq, Kp = M // P, N // Q, K // Q, K // P
-    if Kq % b or Kp % b:
+    L = make_layout(dist, M, N, K, P, Q, b, mb, nb)
+    if L.ka % b or L.kb % b:
         raise ValueError("each pivot block must have one owner: b | K/Q and b | K/P")
-    Al, Bl = distribute(A, B, P, Q)
-    Cl = [[np.zeros((Mt, Nt)) for _ in range(Q)] for _ in range(P)]
+    D = Distributed(A, B, P, Q, L)
     sA, sB = BcastStats(), BcastStats()
+    roots = {"A": [], "B": []}
     for step in range(K // b):
         k0 = step * b
-        c0, off_a = divmod(k0, Kq)
-        r0, off_b = divmod(k0, Kp)
+        c0, off_a = D.owner_a(k0)
+        r0, off_b = D.owner_b(k0)
+        roots["A"].append(c0)
+        roots["B"].append(r0)
         recvA, recvB = {}, {}
         crit_r, crit_w = 0, 0
         per_step = BcastStats()
         for r in range(P):      # row broadcasts of the A pivot column, in parallel
-            got, st = broadcast(tree, Al[r][c0][:, off_a:off_a + b], Q, c0)
+            got, st = broadcast(tree, D.Al[r][c0][:, off_a:off_a + b], Q, c0)
             for c in range(Q):
                 recvA[r, c] = got[c]
             per_step.add(st)
@@ -217,7 +296,7 @@ def summa(A, B, P, Q, b, tree="binomial") -> SimResult:
         crit_r, crit_w = 0, 0
         per_step = BcastStats()
         for c in range(Q):      # column broadcasts of the B pivot row
-            got, st = broadcast(tree, Bl[r0][c][off_b:off_b + b, :], P, r0)
+            got, st = broadcast(tree, D.Bl[r0][c][off_b:off_b + b, :], P, r0)
             for r in range(P):
                 recvB[r, c] = got[r]
             per_step.add(st)
@@ -229,8 +308,8 @@ def summa(A, B, P, Q, b, tree="binomial") -> SimResult:
         sB.crit_words += crit_w
         for r in range(P):
             for c in range(Q):
-                _local_update(Cl[r][c], recvA[r, c], recvB[r, c])
-    return SimResult(_gather(Cl, P, Q), {("summa", "A"): sA, ("summa", "B"): sB})
+                _local_update(D.Cl[r][c], recvA[r, c], recvB[r, c])
+    return SimResult(D.gather(), {("summa", "A"): sA, ("summa", "B"): sB}, roots)
 
 
 def _acc(dst: BcastStats, parallel: list):
@@ -245,37 +324,40 @@ def _acc(dst: BcastStats, parallel: list):
         dst.crit_words += max(st.crit_words for st in parallel)
 
 
-def hsumma(A, B, P, Q, I, J, b, Bo, tree="binomial", outer_tree=None) -> SimResult:
+def hsumma(A, B, P, Q, I, J, b, Bo, tree="binomial", outer_tree=None, dist="block",
+           mb=None, nb=None) -> SimResult:
     """HSUMMA (Section III, Algorithm 1) with I x J groups, inner width b and
-    outer width Bo (b <= Bo, b | Bo)."""
+    outer width Bo (b <= Bo, b | Bo), under the block-checkerboard ("block")
+    or the block-cyclic ("cyclic", blocks mb x nb, k blocks Bo) distribution."""
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
     outer_tree = outer_tree or tree
     M, K = A.shape
     N = B.shape[1]
-    _check_shapes(M, N, K, P, Q)
     if P % I or Q % J:
         raise ValueError("groups must tile the grid: I | P and J | Q")
     if b > Bo or Bo % b:
         raise ValueError("inner block b must divide the outer block B (b <= B)")
-    Mt, Nt, Kq, Kp = M // P, N // Q, K // Q, K // P
-    if Kq % Bo or Kp % Bo:
+    L = make_layout(dist, M, N, K, P, Q, Bo, mb, nb)
+    if L.ka % Bo or L.kb % Bo:
         raise ValueError("each outer block must have one owner: B | K/Q and B | K/P")
     pi, qj = P // I, Q // J        # in-group grid (s/I) x (t/J)
-    Al, Bl = distribute(A, B, P, Q)
-    Cl = [[np.zeros((Mt, Nt)) for _ in range(Q)] for _ in range(P)]
+    D = Distributed(A, B, P, Q, L)
     stats = {(lv, m): BcastStats() for lv in ("outer", "inner") for m in ("A", "B")}
+    roots = {"A": [], "B": []}
     for ko in range(K // Bo):
         k0 = ko * Bo
-        c0, off_a = divmod(k0, Kq)     # owner processor column of the outer A block
+        c0, off_a = D.owner_a(k0)      # owner processor column of the outer A block
         y0, j0 = divmod(c0, qj)        # its group column and in-group column
-        r0, off_b = divmod(k0, Kp)     # owner processor row of the outer B block
+        r0, off_b = D.owner_b(k0)      # owner processor row of the outer B block
         x0, i0 = divmod(r0, pi)
+        roots["A"].append(c0)
+        roots["B"].append(r0)
         # outer A: for every processor row r, among the J processors
         # P_(x, y)(i, j0), y = 0..J-1 (group_row_comm), root y0
         outerA, par = {}, []
         for r in range(P):
-            got, st = broadcast(outer_tree, Al[r][c0][:, off_a:off_a + Bo], J, y0)
+            got, st = broadcast(outer_tree, D.Al[r][c0][:, off_a:off_a + Bo], J, y0)
             for y in range(J):
                 outerA[r, y * qj + j0] = got[y]
             par.append(st)
@@ -284,7 +366,7 @@ def hsumma(A, B, P, Q, I, J, b, Bo, tree="binomial", outer_tree=None) -> SimResu
         # P_(x, y)(i0, j), x = 0..I-1 (group_col_comm), root x0
         outerB, par = {}, []
         for c in range(Q):
-            got, st = broadcast(outer_tree, Bl[r0][c][off_b:off_b + Bo, :], I, x0)
+            got, st = broadcast(outer_tree, D.Bl[r0][c][off_b:off_b + Bo, :], I, x0)
             for x in range(I):
                 outerB[x * pi + i0, c] = got[x]
             par.append(st)
@@ -311,8 +393,8 @@ def hsumma(A, B, P, Q, I, J, b, Bo, tree="binomial", outer_tree=None) -> SimResu
             _acc(stats["inner", "B"], par)
             for r in range(P):
                 for c in range(Q):
-                    _local_update(Cl[r][c], recvA[r, c], recvB[r, c])
-    return SimResult(_gather(Cl, P, Q), stats)
+                    _local_update(D.Cl[r][c], recvA[r, c], recvB[r, c])
+    return SimResult(D.gather(), stats, roots)
 
 
 def log2c(q: int) -> int:

@@ -106,3 +106,45 @@ def test_identity_with_paper_volumes(P, Q, G):
         assert c["b_delivered"] - c["b_loaded"] == v["b_inner"]
     else:       # flat: every processor loads what SUMMA broadcasts to it
         assert c["a_loaded"] == n * n + v["a_outer"] + v["a_inner"]
+
+
+# ---- block-cyclic layout (sub-tile blocks dealt round robin over the grid) ----
+
+@pytest.mark.parametrize("M,N,K,P,Q,cm,cn,tm,tn,Bo", [
+    (1152, 700, 96, 5, 4, 1, 2, 128, 128, 64),
+    (130, 900, 64, 4, 6, 2, 2, 128, 128, 64),          # cluster rows wholly outside M
+    (9, 10, 5, 4, 4, 2, 4, 128, 128, 16),
+    (4000, 4000, 1024, 6, 8, 2, 1, 128, 256, 512),
+    (3000, 2000, 640, 12, 5, 1, 1, 128, 128, 128),
+])
+def test_cyclic_counters_enumeration_equals_closed_form(M, N, K, P, Q, cm, cn, tm, tn, Bo):
+    for npairs in (1, 15):
+        e = gs.counters_enumerated(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs, cyclic=True)
+        c = gs.counters_closed_form(M, N, K, P, Q, cm, cn, tm, tn, Bo, npairs, cyclic=True)
+        assert e == c
+
+
+def test_cyclic_counts_worked_by_hand():
+    # M = 520 rows over P = 4 processor rows, 128-row sub-tiles, one tile column,
+    # K = 128, B = 64 (two outer blocks).  Block: Mt = 130, so every processor
+    # sweeps two sub-tiles (128 + 2 rows): 8 sub-tiles, each reading the 128 x 256
+    # B panel.  Block-cyclic: 5 tile rows (4 full + 8 rows) dealt 2, 1, 1, 1:
+    # 5 sub-tiles.  Owners of the two outer blocks: column 0 (Q = 1) for A,
+    # rows 0 and 1 for B, so the prefetches are
+    # row 0: 2 sub-tiles x (2 + 1), row 1: 1 x (2 + 1), rows 2, 3: 1 x 2 each = 13.
+    blk = gs.counters_closed_form(520, 256, 128, 4, 1, 1, 1, 128, 256, 64)
+    cyc = gs.counters_closed_form(520, 256, 128, 4, 1, 1, 1, 128, 256, 64, cyclic=True)
+    assert blk["b_loaded"] == 8 * 128 * 256 and cyc["b_loaded"] == 5 * 128 * 256
+    assert blk["a_loaded"] == cyc["a_loaded"] == 520 * 128
+    # block: 2 sub-tile steps x 2 outer blocks x (4 A owners + 1 B owner)
+    assert blk["l2_prefetch"] == 2 * 2 * (4 + 1) and cyc["l2_prefetch"] == 13
+
+
+@pytest.mark.parametrize("P,Q,cm,cn", [(4, 4, 2, 2), (4, 4, 1, 1), (6, 2, 3, 1), (2, 8, 2, 4)])
+def test_cyclic_equals_block_with_one_aligned_sub_tile_per_cta(P, Q, cm, cn):
+    # M = P tm, N = Q tn: both layouts give every CTA the same single sub-tile
+    tm, tn = 128, 256
+    for K, Bo in ((512, 64), (640, 128)):
+        blk = gs.counters_closed_form(P * tm, Q * tn, K, P, Q, cm, cn, tm, tn, Bo)
+        cyc = gs.counters_closed_form(P * tm, Q * tn, K, P, Q, cm, cn, tm, tn, Bo, cyclic=True)
+        assert blk == cyc

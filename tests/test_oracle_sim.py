@@ -163,3 +163,104 @@ def test_closed_form_helper_matches_simulation():
                 for m in "AB":
                     cf = hs.closed_form(lv, m, M, N, K, P, Q, I, J, b, Bo, tree)
                     assert vars(cf) == vars(r.stats[lv, m]), (tree, I, J, lv, m)
+
+
+# ---- block-cyclic distribution (Section VI names it as future work) ----
+
+def test_owned_indices_worked_by_hand():
+    # blocks of blk indices dealt round robin: block t to owner t mod owners
+    assert hs.owned(5, 2, 2, 0).tolist() == [0, 1, 4]
+    assert hs.owned(5, 2, 2, 1).tolist() == [2, 3]
+    assert hs.owned(7, 3, 1, 2).tolist() == [2, 5]
+    assert hs.owned(3, 4, 1, 3).tolist() == []
+    assert hs.owned(12, 3, 4, 1).tolist() == [4, 5, 6, 7]        # one block each
+    assert hs.owned(10, 3, 3, 0).tolist() == [0, 1, 2, 9]        # last block clipped
+
+
+@pytest.mark.parametrize("tree", hs.TREES)
+def test_cyclic_equals_oracle_ragged(tree):
+    # rows and columns that do not divide into whole blocks per processor
+    P, Q, M, N, K = 2, 4, 22, 26, 32
+    A = workloads.matrix(M, K, 111, "uniform")
+    B = workloads.matrix(K, N, 112, "wide")
+    C0 = native.dgemm(A, B)
+    for I, J in divisor_pairs(P, Q):
+        res = hs.hsumma(A, B, P, Q, I, J, b=2, Bo=4, tree=tree, dist="cyclic", mb=3, nb=2)
+        assert np.array_equal(res.C, C0), (I, J)
+    assert np.array_equal(hs.summa(A, B, P, Q, 4, tree, dist="cyclic", mb=5, nb=3).C, C0)
+
+
+def test_cyclic_integers_exact():
+    P, Q, M, N, K = 3, 2, 13, 9, 24
+    A = workloads.matrix(M, K, 113, "smallint")
+    B = workloads.matrix(K, N, 114, "smallint")
+    exact = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    for I, J in divisor_pairs(P, Q):
+        res = hs.hsumma(A, B, P, Q, I, J, b=4, Bo=8, dist="cyclic", mb=2, nb=4)
+        assert np.array_equal(res.C, exact)
+
+
+def test_outer_roots_rotate_under_cyclic():
+    # 4 x 4 grid, K = 32, B = 4: eight outer blocks.  Block distribution: A's
+    # columns 8c..8c+7 live on processor column c, so the owners run
+    # 0 0 1 1 2 2 3 3; block-cyclic: outer block o on column o mod 4.
+    A = workloads.matrix(16, 32, 115, "uniform")
+    B = workloads.matrix(32, 16, 116, "uniform")
+    blk = hs.hsumma(A, B, 4, 4, 2, 2, b=2, Bo=4)
+    cyc = hs.hsumma(A, B, 4, 4, 2, 2, b=2, Bo=4, dist="cyclic", mb=2, nb=2)
+    assert blk.roots["A"] == [0, 0, 1, 1, 2, 2, 3, 3] == blk.roots["B"]
+    assert cyc.roots["A"] == [0, 1, 2, 3, 0, 1, 2, 3] == cyc.roots["B"]
+    assert np.array_equal(blk.C, cyc.C)
+    # on a 2 x 4 grid the B owners cycle over the two processor rows
+    cyc2 = hs.hsumma(A, B, 2, 4, 1, 2, b=2, Bo=4, dist="cyclic", mb=2, nb=2)
+    assert cyc2.roots["B"] == [0, 1] * 4 and cyc2.roots["A"] == [0, 1, 2, 3] * 2
+
+
+@pytest.mark.parametrize("tree", hs.TREES)
+def test_cyclic_moves_the_same_data_when_blocks_are_even(tree):
+    # P mb | M and Q nb | N: every processor holds M/P rows and N/Q columns, so
+    # each broadcast carries as much as under the block distribution; only the
+    # roots move.  Counts equal the block distribution's and Tables I / II.
+    P = Q = 4
+    n = 32
+    A = workloads.matrix(n, n, 117, "uniform")
+    B = workloads.matrix(n, n, 118, "uniform")
+    for I, J in divisor_pairs(P, Q):
+        if I != J:
+            continue
+        blk = hs.hsumma(A, B, P, Q, I, J, b=2, Bo=4, tree=tree)
+        cyc = hs.hsumma(A, B, P, Q, I, J, b=2, Bo=4, tree=tree, dist="cyclic", mb=2, nb=4)
+        for key in blk.stats:
+            assert vars(cyc.stats[key]) == vars(blk.stats[key]), (I, key)
+        for lv in ("outer", "inner"):
+            for m in ("A", "B"):
+                want = hs.closed_form(lv, m, n, n, n, P, Q, I, J, 2, 4, tree)
+                assert vars(cyc.stats[lv, m]) == vars(want), (I, lv, m)
+
+
+def test_cyclic_G1_reduces_to_summa():
+    # one group: the outer level is empty and the inner broadcasts are SUMMA's,
+    # with the same rotating owners when B = b
+    P, Q, M, N, K = 2, 4, 12, 20, 16
+    A = workloads.matrix(M, K, 119, "uniform")
+    B = workloads.matrix(K, N, 120, "uniform")
+    for tree in ("flat", "binomial"):
+        s = hs.summa(A, B, P, Q, 2, tree, dist="cyclic", mb=3, nb=2)
+        g1 = hs.hsumma(A, B, P, Q, 1, 1, b=2, Bo=2, tree=tree, dist="cyclic", mb=3, nb=2)
+        assert vars(g1.stats["inner", "A"]) == vars(s.stats["summa", "A"])
+        assert vars(g1.stats["inner", "B"]) == vars(s.stats["summa", "B"])
+        assert g1.stats["outer", "A"].broadcasts == 0
+        assert g1.roots == s.roots == {"A": [k % Q for k in range(8)],
+                                       "B": [k % P for k in range(8)]}
+        assert np.array_equal(g1.C, s.C)
+
+
+def test_cyclic_argument_checks():
+    A = np.zeros((8, 12))
+    B = np.zeros((12, 8))
+    with pytest.raises(ValueError):
+        hs.hsumma(A, B, 2, 2, 1, 1, b=2, Bo=8, dist="cyclic", mb=2, nb=2)   # B does not divide K
+    with pytest.raises(ValueError):
+        hs.hsumma(A, B, 2, 2, 1, 1, b=2, Bo=4, dist="cyclic")               # no block sizes
+    with pytest.raises(ValueError):
+        hs.hsumma(A, B, 2, 2, 1, 1, b=2, Bo=4, dist="diagonal", mb=2, nb=2)
