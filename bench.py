@@ -308,6 +308,36 @@ def run_table(sections):
                                            Q=cfg[1], G=cfg[2], b=cfg[3], Bouter=cfg[4]))
             emit(workload="rect_24576x16384x32768", path="bf16", slices=7, chosen_by=how,
                  cfg=cfg, ms=ms, tflops=2 * M * N * K / ms / 1e9, stage_ms=st)
+    if 4 in sections:
+        # the two layouts of the grid at the same P x Q: block-checkerboard
+        # (Algorithm 1) and block-cyclic (sub-tiles dealt round robin); aligned
+        # grids do the same work in both, ragged ones sweep partial sub-tiles
+        # in every block of the former and only at the matrix edge in the latter
+        n = 16384
+        A, B, C = product(n, n, n, "uniform", "uniform", 1002, 2002)
+        for P, Q, G, note in ((128, 64, 4096, "aligned"), (120, 60, 3600, "ragged, many waves"),
+                              (12, 12, 72, "ragged, one wave")):
+            for layout in ("block", "cyclic"):
+                cfg = dict(P=P, Q=Q, G=G, b=64, Bouter=512, kind="bf16", slices=5, layout=layout)
+                ms, st = timed(lambda: hs.gemm(A, B, out=C, **cfg), reps=2)
+                unit = 15 * 2 * n ** 3 / st[2] / 1e9
+                emit(workload="layout_bf16_16384", layout=layout, grid=f"{P}x{Q}", G=G, note=note,
+                     cluster=hs.group_shape(P, Q, G)[2:], ms=ms, tflops=2 * n ** 3 / ms / 1e9,
+                     stage_ms=st, counters=hs.counters(),
+                     product_kernel={"achieved": unit, "peak": bf16, "frac": unit / bf16})
+        del A, B, C
+        n = 8192
+        A, B, C = product(n, n, n, "uniform", "uniform", 1001, 2001)
+        for P, Q, G, note in ((16, 16, 16, "aligned"), (24, 24, 144, "ragged"),
+                              (20, 20, 400, "ragged, flat")):
+            for layout in ("block", "cyclic"):
+                ms, _ = timed(lambda: hs.gemm(A, B, out=C, P=P, Q=Q, G=G, b=32, Bouter=128,
+                                              layout=layout), warm=False)
+                tf = 2 * n ** 3 / ms / 1e9
+                emit(workload="layout_fp64_8192", layout=layout, grid=f"{P}x{Q}", G=G, note=note,
+                     cluster=hs.group_shape(P, Q, G)[2:], ms=ms, tflops=tf,
+                     frac_of_dmma=tf / dmma, counters=hs.counters())
+        del A, B, C
 
 
 def main():
@@ -323,8 +353,9 @@ def main():
     ap.add_argument("--size", type=int, default=N_SIZE,
                     help="n of the n x n x n product (multiple of 256; default 16384)")
     ap.add_argument("--table", default=None,
-                    help="comma-separated workload numbers 0..3: print throughput rows of "
-                         "their configurations instead of the benchmark line")
+                    help="comma-separated workload numbers 0..3 (4: block against "
+                         "block-cyclic layout): print throughput rows of their "
+                         "configurations instead of the benchmark line")
     args = ap.parse_args()
     configure(args.size)
     if args.table is not None:

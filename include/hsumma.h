@@ -60,6 +60,20 @@ typedef enum {
 
 #define HSUMMA_MODE(kind, slices) ((int)(kind) | ((int)(slices) << 8))
 
+/* Layout of the virtual grid, or-ed into the mode argument (bit 16; other bits
+ * above 15 are rejected with HSUMMA_ERR_ARG).  Without it the grid is
+ * block-checkerboard (Algorithm 1): processor (r, c) owns the C block of rows
+ * [r ceil(M/P), (r+1) ceil(M/P)) and columns [c Nt, (c+1) Nt), swept in
+ * sub-tiles, and outer block o of A (B) is owned by the processor column
+ * (row) whose share of K holds it.  With it the grid is block-cyclic, the
+ * distribution Section VI leaves to future work: the sub-tiles (128 rows;
+ * 128 columns for FP64 and INT8, 256 for BF16) are dealt round robin, tile row
+ * t to processor row t mod P and tile column u to processor column u mod Q,
+ * and outer block o is owned by processor column o mod Q (A) and row o mod P
+ * (B).  Every element is the same k-ascending sum in both layouts, so C is the
+ * same bit for bit; the counters follow the layout. */
+#define HSUMMA_LAYOUT_CYCLIC 0x10000
+
 /* Panel-load counters of the last hsumma_gemm launch, in matrix elements
  * (slice elements for the split kinds, counted once per slice pair).  They
  * are the GPU counterparts of the broadcast volumes of Section IV-B: with one

@@ -19,6 +19,8 @@ HEADER = os.path.join(ROOT, "include", "hsumma.h")
 
 FP64, INT8_SLICES, BF16_SLICES = 0, 1, 2
 KINDS = {"fp64": FP64, "int8": INT8_SLICES, "bf16": BF16_SLICES}
+LAYOUT_CYCLIC = 0x10000          # mode bit: block-cyclic layout of the virtual grid
+LAYOUTS = {"block": 0, "cyclic": LAYOUT_CYCLIC}
 PEAKS = {"dfma": 0, "dmma": 1, "imma": 2, "hmma_bf16": 3, "tc05_bf16": 4, "copy": 5,
          "tc05_bf16_pair": 6}
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_UNSUPPORTED", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
@@ -161,9 +163,10 @@ def finalize():
     _inited = None
 
 
-def mode_code(kind: str | int, slices: int = 0) -> int:
+def mode_code(kind: str | int, slices: int = 0, layout: str = "block") -> int:
+    """The mode argument: kind in bits 0..7, slices in 8..15, the layout bit."""
     k = KINDS[kind] if isinstance(kind, str) else int(kind)
-    return k | (int(slices) << 8)
+    return k | (int(slices) << 8) | LAYOUTS[layout]
 
 
 def group_shape(P: int, Q: int, G: int):
@@ -188,10 +191,11 @@ def _check_f64(t, name):
 
 
 def gemm(A, B, *, P=0, Q=0, G=0, b=0, Bouter=0, kind="fp64", slices=0, out=None,
-         stream=_DEFAULT):
+         layout="block", stream=_DEFAULT):
     """C = A x B by HSUMMA on a virtual P x Q grid with G groups (torch tensors on
     the GPU, float64, row-major).  P = Q = G = b = Bouter = 0 (the default) lets
-    the library choose them (see choose())."""
+    the library choose them (see choose()).  layout: "block" (block-checkerboard,
+    Algorithm 1) or "cyclic" (sub-tiles dealt round robin over the grid)."""
     import torch
     _check_f64(A, "A")
     _check_f64(B, "B")
@@ -206,11 +210,13 @@ def gemm(A, B, *, P=0, Q=0, G=0, b=0, Bouter=0, kind="fp64", slices=0, out=None,
     ldb = B.stride(0) if (K and N) else max(N, 1)
     ldc = C.stride(0) if (M and N) else max(N, 1)
     _check(lib().hsumma_gemm(M, N, K, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(), ldc,
-                             P, Q, G, b, Bouter, mode_code(kind, slices), _stream_ptr(stream)))
+                             P, Q, G, b, Bouter, mode_code(kind, slices, layout),
+                             _stream_ptr(stream)))
     return C
 
 
-def gemm_host(A, B, C, *, P, Q, G, b, Bouter, kind="fp64", slices=0, stream=_DEFAULT):
+def gemm_host(A, B, C, *, P, Q, G, b, Bouter, kind="fp64", slices=0, layout="block",
+              stream=_DEFAULT):
     """The same product from host memory (numpy or CPU torch float64 arrays,
     row-major); C is written in place."""
     def ptr_ld(x):
@@ -222,7 +228,7 @@ def gemm_host(A, B, C, *, P, Q, G, b, Bouter, kind="fp64", slices=0, stream=_DEF
     N = B.shape[1]
     _ensure_init()
     _check(lib().hsumma_gemm_host(M, N, K, pa, la, pb, lb, pc, lc, P, Q, G, b, Bouter,
-                                  mode_code(kind, slices), _stream_ptr(stream)))
+                                  mode_code(kind, slices, layout), _stream_ptr(stream)))
     return C
 
 

@@ -129,6 +129,10 @@ void analytic_terms(int64_t M, int64_t N, int64_t K, int kind, int S, const Cand
 int decode_mode(int mode, int *kind, int *S) {
   *kind = mode & 0xff;
   *S = (mode >> 8) & 0xff;
+  if (mode & ~(0xffff | HSUMMA_LAYOUT_CYCLIC)) {
+    set_error("bad mode %#x", mode);
+    return HSUMMA_ERR_ARG;
+  }
   if (*kind == HSUMMA_FP64) return HSUMMA_OK;
   if ((*kind == HSUMMA_INT8_SLICES && *S >= 1 && *S <= 8) ||
       (*kind == HSUMMA_BF16_SLICES && *S >= 1 && *S <= 7))

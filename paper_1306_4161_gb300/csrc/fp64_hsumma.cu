@@ -60,6 +60,8 @@ __device__ __forceinline__ int64_t clamp_count(int64_t lo, int64_t hi, int64_t a
   return y > x ? y - x : 0;
 }
 
+// CYC: block-cyclic layout of the grid, else block-checkerboard
+template <bool CYC>
 __global__ void __launch_bounds__(NTHREADS, 1)
     fp64_hsumma_kernel(const __grid_constant__ CUtensorMap tmA,
                        const __grid_constant__ CUtensorMap tmB,
@@ -97,8 +99,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   cluster_sync();
 
-  const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
-  const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
+  const int r0 = r - cy, c0 = c - cx;           // the cluster's first processor row / column
+  // the block of a processor in the block-checkerboard layout (the epilogue
+  // reads these; formed once here they cost the k loop no registers)
+  const int64_t blk_row_lo = (int64_t)r * p.Mt, blk_row_hi = imin64(p.M, blk_row_lo + p.Mt);
+  const int64_t blk_col_lo = (int64_t)c * p.Nt, blk_col_hi = imin64(p.N, blk_col_lo + p.Nt);
+  constexpr bool cyc = CYC;
   const int64_t nk = (p.K + BK - 1) / BK;
   const int64_t nout = p.K > 0 ? (p.K + p.Bo - 1) / p.Bo : 0;
 
@@ -109,9 +115,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t stage = 0, phase = 0;
       bool ok = true;
       for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-        const int64_t m0 = row_lo + (int64_t)mi * TM;
+        if (tile_skipped(cyc, r0, mi, p.P, TM, p.M)) continue;
+        int64_t m0, row_lo, row_hi;
+        tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
         for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-          const int64_t n0 = col_lo + (int64_t)ni * TN;
+          if (tile_skipped(cyc, c0, ni, p.Q, TN, p.N)) continue;
+          int64_t n0, col_lo, col_hi;
+          tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
           int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
           for (int64_t kt = 0; kt < nk; ++kt) {
             const int64_t k0 = kt * BK;
@@ -120,17 +130,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (outer) {
               // outer step o: stage outer panel o (first step) and o + 1 into L2;
               // the owner of an outer block is the processor whose own block of
-              // A (columns) / B (rows) contains its first index
+              // A (columns) / B (rows) contains its first index (block-cyclic:
+              // the processor column / row q mod Q / q mod P)
               const int64_t o = k0 / p.Bo;
               for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
                 const int64_t kq = q * p.Bo;
                 const int64_t kend = imin64(p.K, kq + p.Bo);
-                if (c == (int)imin64(p.Q - 1, kq / p.Kq)) {
+                if (c == outer_owner(cyc, q, kq, p.Kq, p.Q)) {
                   for (int64_t kk = kq; kk < kend; kk += PF_K)
                     tma_prefetch_2d(&tmApf, (int32_t)kk, (int32_t)m0);
                   pf += 1;
                 }
-                if (r == (int)imin64(p.P - 1, kq / p.Kp)) {
+                if (r == outer_owner(cyc, q, kq, p.Kp, p.P)) {
                   for (int64_t kk = kq; kk < kend; kk += PF_K)
                     tma_prefetch_2d(&tmBpf, (int32_t)n0, (int32_t)kk);
                   pf += 1;
@@ -192,9 +203,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t stage = 0, phase = 0;
     bool ok = true;
     for (int mi = 0; mi < p.nsub_m; ++mi) {
-      const int64_t m0 = row_lo + (int64_t)mi * TM;
+      if (tile_skipped(cyc, r0, mi, p.P, TM, p.M)) continue;
       for (int ni = 0; ni < p.nsub_n; ++ni) {
-        const int64_t n0 = col_lo + (int64_t)ni * TN;
+        if (tile_skipped(cyc, c0, ni, p.Q, TN, p.N)) continue;
         double acc[4][4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -246,7 +257,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
-        // epilogue: C := the block's sub-tile (beta = 0), rows/cols inside the block
+        // epilogue: C := the sub-tile (beta = 0), rows/cols inside the block
+        // (block-cyclic: inside the tile and the matrix)
+        int64_t m0, row_lo, row_hi, n0, col_lo, col_hi;
+        if (cyc) {
+          tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
+          tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
+        } else {
+          m0 = blk_row_lo + (int64_t)mi * TM, row_hi = blk_row_hi;
+          n0 = blk_col_lo + (int64_t)ni * TN, col_hi = blk_col_hi;
+        }
 #pragma unroll
         for (int mt = 0; mt < 4; ++mt) {
 #pragma unroll
@@ -284,10 +304,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }  // namespace
 
 int fp64_cluster_limit(int *limit) {
-  cudaError_t e = cudaFuncSetAttribute(fp64_hsumma_kernel,
+  cudaError_t e = cudaFuncSetAttribute(fp64_hsumma_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-  e = cudaFuncSetAttribute(fp64_hsumma_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  e = cudaFuncSetAttribute(fp64_hsumma_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16, 1, 1);
@@ -301,7 +321,7 @@ int fp64_cluster_limit(int *limit) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  e = cudaOccupancyMaxPotentialClusterSize(&n, fp64_hsumma_kernel, &cfg);
+  e = cudaOccupancyMaxPotentialClusterSize(&n, fp64_hsumma_kernel<false>, &cfg);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxPotentialClusterSize");
   *limit = n;
   return HSUMMA_OK;
@@ -330,16 +350,17 @@ int launch_fp64_hsumma(const GridPlan &g, const double *A, int64_t lda, const do
   p.Q = g.Q;
   p.cm = g.cm;
   p.cn = g.cn;
-  p.nsub_m = (int)ceil_div(g.Mt, TM);
-  p.nsub_n = (int)ceil_div(g.Nt, TN);
+  p.nsub_m = (int)(g.cyc ? ceil_div(ceil_div(g.M, TM), g.P) : ceil_div(g.Mt, TM));
+  p.nsub_n = (int)(g.cyc ? ceil_div(ceil_div(g.N, TN), g.Q) : ceil_div(g.Nt, TN));
   p.Bo = g.Bo;
   p.counters = state().d_counters;
   p.status = state().d_status;
-  cudaError_t e = cudaFuncSetAttribute(fp64_hsumma_kernel,
+  auto kern = g.cyc ? fp64_hsumma_kernel<true> : fp64_hsumma_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
   if (g.cm * g.cn > 8) {
-    e = cudaFuncSetAttribute(fp64_hsumma_kernel,
+    e = cudaFuncSetAttribute(kern,
                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   }
@@ -355,7 +376,7 @@ int launch_fp64_hsumma(const GridPlan &g, const double *A, int64_t lda, const do
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, fp64_hsumma_kernel, tA, tB, tApf, tBpf, p);
+  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch fp64_hsumma_kernel");
   return HSUMMA_OK;
 }

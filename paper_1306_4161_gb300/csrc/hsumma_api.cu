@@ -291,6 +291,10 @@ int hsumma_group_shape(int P, int Q, int G, int *I, int *J, int *cluster_m, int 
 static int split_kind_and_S(int mode, int *kind, int *S) {
   *kind = mode & 0xff;
   *S = (mode >> 8) & 0xff;
+  if (mode & ~(0xffff | HSUMMA_LAYOUT_CYCLIC)) {
+    set_error("unknown mode bits %#x", mode);
+    return HSUMMA_ERR_ARG;
+  }
   if (*kind == HSUMMA_FP64) return HSUMMA_OK;
   if (*kind == HSUMMA_INT8_SLICES) {
     if (*S < 1 || *S > 8) {
@@ -351,7 +355,7 @@ static int ensure_workspace(size_t bytes) {
 }
 
 static int make_plan(int64_t M, int64_t N, int64_t K, int P, int Q, int G, int b, int Bo,
-                     int kind, GridPlan *g) {
+                     int kind, bool cyc, GridPlan *g) {
   if (P > 65535 || Q > 65535) {
     set_error("P and Q must be at most 65535");
     return HSUMMA_ERR_ARG;
@@ -391,6 +395,7 @@ static int make_plan(int64_t M, int64_t N, int64_t K, int P, int Q, int G, int b
   g->nsub_n = 0;
   g->b = b;
   g->Bo = Bo;
+  g->cyc = cyc;
   if (g->Kq < 1) g->Kq = 1;
   if (g->Kp < 1) g->Kp = 1;
   return HSUMMA_OK;
@@ -420,7 +425,7 @@ int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
                        mode, stream);
   }
   GridPlan g;
-  st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, &g);
+  st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, (mode & HSUMMA_LAYOUT_CYCLIC) != 0, &g);
   if (st != HSUMMA_OK) return st;
   cudaError_t e = cudaMemsetAsync(g_state.d_counters, 0, 8 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
@@ -506,8 +511,9 @@ int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
 
 // Row blocks of the pipelined host-buffer product: R blocks of P/R processor
 // rows each (R | P and R | I, so that every block keeps the product's blocks,
-// sub-tiles and in-group grid), at least 512 rows each, none empty; 1 if no R
-// in {4, 3, 2} fits.
+// sub-tiles and in-group grid; in the block-cyclic layout each block's tiles
+// are dealt over its own P/R processor rows), at least 512 rows each, none
+// empty; 1 if no R in {4, 3, 2} fits.
 static int host_row_blocks(int64_t M, int P, int I, int64_t Mt) {
   for (int R : {4, 3, 2}) {
     if (P % R || I % R) continue;
@@ -605,7 +611,8 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   for (int r = 0; r < R; ++r) {
     const int64_t r0 = r * rows, mr = (M - r0) < rows ? (M - r0) : rows;
     GridPlan g;
-    st = make_plan(mr, N, K, full.P / R, full.Q, full.G / R, full.b, full.Bo, kind, &g);
+    st = make_plan(mr, N, K, full.P / R, full.Q, full.G / R, full.b, full.Bo, kind, full.cyc,
+                   &g);
     if (st != HSUMMA_OK) return fail_st(st);
     e = cudaStreamWaitEvent(s, ev[1 + r], 0);
     if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(A block)");
@@ -673,7 +680,8 @@ int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t 
     st = split_kind_and_S(mode, &kind, &S);
     if (st != HSUMMA_OK) return st;
     GridPlan full;
-    st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, &full);
+    st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, (mode & HSUMMA_LAYOUT_CYCLIC) != 0,
+                   &full);
     if (st != HSUMMA_OK) return st;
     const bool exact_ok = kind == HSUMMA_FP64 || (double)S * (double)K * 16384.0 < 9.0e18;
     const bool tma_ok = kind != HSUMMA_FP64 || (tma_ready(dA, lda) && tma_ready(dB, ldb) &&
@@ -813,7 +821,7 @@ int hsumma_split_diagonals(int64_t M, int64_t N, int64_t K, int kind, int S, con
     return HSUMMA_ERR_ARG;
   }
   GridPlan g;
-  st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, &g);
+  st = make_plan(M, N, K, P, Q, G, b, Bouter, kind, false, &g);
   if (st != HSUMMA_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(g_state.d_counters, 0, 8 * sizeof(unsigned long long), s);

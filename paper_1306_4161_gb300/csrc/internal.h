@@ -17,6 +17,8 @@ struct GridPlan {
   int64_t Kq, Kp;        // ceil(K/Q), ceil(K/P): owner ranges of outer panels
   int nsub_m, nsub_n;    // sub-tiles per block
   int b, Bo;             // inner / outer panel widths
+  bool cyc;              // block-cyclic layout (sub-tiles dealt round robin), else
+                         // block-checkerboard (one block per processor)
 };
 
 struct DeviceState {

@@ -247,6 +247,46 @@ __device__ __forceinline__ void raster_proc(int cm, int cn, int cy, int cx, int 
   *c = gx * cn + cx;
 }
 
+// Layouts of the virtual grid.  Sub-tile i (of T rows) of processor row r
+// starts at row *org; the rows of it that the processor owns and the matrix
+// has are [org, org + T) ∩ [*lo, *hi).
+//  block-checkerboard (Algorithm 1): the processor's block [r Mt, (r+1) Mt)
+//    swept in tiles of T: org = r Mt + i T, [lo, hi) = the block;
+//  block-cyclic (the distribution Section VI leaves to future work, with the
+//    sub-tile as the distribution block): tile row r + i P, so
+//    org = (r + i P) T and [lo, hi) = the tile.
+// Columns use the same rule with (c, Q, Nt, N).
+__device__ __forceinline__ void tile_rows(bool cyc, int r, int i, int P, int64_t Mt, int T,
+                                          int64_t M, int64_t *org, int64_t *lo, int64_t *hi) {
+  if (cyc) {
+    *org = ((int64_t)r + (int64_t)i * P) * T;
+    *lo = *org;
+    *hi = *org + T < M ? *org + T : M;
+  } else {
+    *lo = (int64_t)r * Mt;
+    *org = *lo + (int64_t)i * T;
+    *hi = *lo + Mt < M ? *lo + Mt : M;
+  }
+}
+
+// Whether the CTAs of a cluster whose first processor row is r0 all skip
+// sub-step i: in the block-cyclic layout, when the cluster's first tile row
+// lies at or past the end of the matrix (every later row of it does too).  The
+// test depends on the cluster only, so a cluster skips in lockstep.
+__device__ __forceinline__ bool tile_skipped(bool cyc, int r0, int i, int P, int T, int64_t M) {
+  return cyc && ((int64_t)r0 + (int64_t)i * P) * T >= M;
+}
+
+// Owner of outer block q (starting at k index kq) among n processors: the
+// processor column of the A block (n = Q) or row of the B block (n = P).
+// Block-checkerboard: the processor whose k range [x Kblk, (x+1) Kblk) holds
+// kq (Algorithm 1's pivot); block-cyclic: q mod n.
+__device__ __forceinline__ int outer_owner(bool cyc, int64_t q, int64_t kq, int64_t Kblk, int n) {
+  if (cyc) return (int)(q % n);
+  const int64_t x = kq / Kblk;
+  return x < n - 1 ? (int)x : n - 1;
+}
+
 // Byte offset of 16-byte chunk `chunk` (0..7) of row `row` inside a 128-byte
 // swizzled tile (CU_TENSOR_MAP_SWIZZLE_128B): chunk index XOR (row mod 8).
 __device__ __forceinline__ uint32_t swz128(uint32_t row, uint32_t byte_in_row) {

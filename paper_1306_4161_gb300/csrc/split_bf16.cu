@@ -97,6 +97,8 @@ __device__ __forceinline__ void tile_proc(int L, int ncx, int ncy, int cm, int c
   *c = (idx / in_group) * cn + cx;
 }
 
+// CYC: block-cyclic layout of the grid, else block-checkerboard
+template <bool CYC>
 __global__ void __launch_bounds__(NTHREADS, 1)
     bf16_diag_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB,
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   cluster_sync();
 
   const int S = p.S, nkb = p.nkb;
+  constexpr bool cyc = CYC;
   const int64_t nout = (p.Kpad + p.Bo - 1) / p.Bo;
   // rows per TMA box: the CTA's contiguous share of a tile when the cluster
   // width divides the tile's 8-row pieces, else single 8-row pieces
@@ -166,12 +169,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int L = cid; L < ntiles && ok; L += ncl) {
         int r, c;
         tile_proc(L, ncx, ncy, cm, cn, cy, cx, &r, &c);
-        const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
-        const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
         for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-          const int64_t m0 = row_lo + (int64_t)mi * TM;
+          if (tile_skipped(cyc, r - cy, mi, p.P, TM, p.M)) continue;
+          int64_t m0, row_lo, row_hi;
+          tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
           for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-            const int64_t n0 = col_lo + (int64_t)ni * TN;
+            if (tile_skipped(cyc, c - cx, ni, p.Q, TN, p.N)) continue;
+            int64_t n0, col_lo, col_hi;
+            tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
             for (int d = 2; d <= S + 1 && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
@@ -200,12 +205,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         pt = nd - ns;
                       }
                       const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
-                      if (c == (int)imin64(p.Q - 1, kq / p.Kq)) {
+                      if (c == outer_owner(cyc, q, kq, p.Kq, p.Q)) {
                         for (int64_t kk = kq; kk < kend; kk += BKS)
                           tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, ps - 1);
                         pf += 1;
                       }
-                      if (r == (int)imin64(p.P - 1, kq / p.Kp)) {
+                      if (r == outer_owner(cyc, q, kq, p.Kp, p.P)) {
                         for (int64_t kk = kq; kk < kend; kk += BKS)
                           tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, pt - 1);
                         pf += 1;
@@ -285,8 +290,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t dt = tmem_base + (uint32_t)(me * TN);
       bool ok = true;
       for (int L = cid; L < ntiles && ok; L += ncl) {
+        int r, c;
+        tile_proc(L, ncx, ncy, cm, cn, cy, cx, &r, &c);
         for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
+          if (tile_skipped(cyc, r - cy, mi, p.P, TM, p.M)) continue;
           for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
+            if (tile_skipped(cyc, c - cx, ni, p.Q, TN, p.N)) continue;
             for (int d = 2; d <= S + 1 && ok; ++d) {
               const int nst = (d - 1) * nkb;
               for (int st = 0; st < nst; ++st, ++gst) {
@@ -347,12 +356,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int L = cid; L < ntiles && ok; L += ncl) {
       int r, c;
       tile_proc(L, ncx, ncy, cm, cn, cy, cx, &r, &c);
-      const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
-      const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
       for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-        const int64_t row = row_lo + (int64_t)mi * TM + q * 32 + lane;
+        if (tile_skipped(cyc, r - cy, mi, p.P, TM, p.M)) continue;
+        int64_t m0, row_lo, row_hi;
+        tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
+        const int64_t row = m0 + q * 32 + lane;
         for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-          const int64_t n0 = col_lo + (int64_t)ni * TN + h * 128;
+          if (tile_skipped(cyc, c - cx, ni, p.Q, TN, p.N)) continue;
+          int64_t t0, col_lo, col_hi;
+          tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &t0, &col_lo, &col_hi);
+          const int64_t n0 = t0 + h * 128;
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
           for (int d = 2; d <= S + 1 && ok; ++d) {
             const int nst = (d - 1) * nkb;
@@ -430,10 +443,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }  // namespace
 
 int bf16_cluster_limit(int *limit) {
-  cudaError_t e = cudaFuncSetAttribute(bf16_diag_kernel,
+  cudaError_t e = cudaFuncSetAttribute(bf16_diag_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-  e = cudaFuncSetAttribute(bf16_diag_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  e = cudaFuncSetAttribute(bf16_diag_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16, 1, 1);
@@ -447,7 +460,7 @@ int bf16_cluster_limit(int *limit) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  e = cudaOccupancyMaxPotentialClusterSize(&n, bf16_diag_kernel, &cfg);
+  e = cudaOccupancyMaxPotentialClusterSize(&n, bf16_diag_kernel<false>, &cfg);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxPotentialClusterSize");
   *limit = n;
   return HSUMMA_OK;
@@ -479,8 +492,8 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
   p.Q = g.Q;
   p.cm = g.cm;
   p.cn = g.cn;
-  p.nsub_m = (int)ceil_div(g.Mt, TM);
-  p.nsub_n = (int)ceil_div(g.Nt, TN);
+  p.nsub_m = (int)(g.cyc ? ceil_div(ceil_div(g.M, TM), g.P) : ceil_div(g.Mt, TM));
+  p.nsub_n = (int)(g.cyc ? ceil_div(ceil_div(g.N, TN), g.Q) : ceil_div(g.Nt, TN));
   p.Bo = g.Bo;
   p.S = S;
   p.nkb = (int)(Kpad / BKS);
@@ -488,11 +501,12 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
   p.nseg = split_planes(g.K, S);
   p.counters = state().d_counters;
   p.status = state().d_status;
-  cudaError_t e = cudaFuncSetAttribute(bf16_diag_kernel,
+  auto kern = g.cyc ? bf16_diag_kernel<true> : bf16_diag_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
   if (g.cm * g.cn > 8) {
-    e = cudaFuncSetAttribute(bf16_diag_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed,
                              1);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   }
@@ -512,7 +526,7 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, bf16_diag_kernel, tA, tB, tApf, tBpf, p);
+  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch bf16_diag_kernel");
   return HSUMMA_OK;
 }

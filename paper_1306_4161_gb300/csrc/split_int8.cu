@@ -57,6 +57,8 @@ __device__ __forceinline__ void imma(int (&c)[4], const uint32_t (&a)[4], uint32
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// CYC: block-cyclic layout of the grid, else block-checkerboard
+template <bool CYC>
 __global__ void __launch_bounds__(NTHREADS, 1)
     int8_diag_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB,
@@ -92,8 +94,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   cluster_sync();
 
-  const int64_t row_lo = (int64_t)r * p.Mt, row_hi = imin64(p.M, row_lo + p.Mt);
-  const int64_t col_lo = (int64_t)c * p.Nt, col_hi = imin64(p.N, col_lo + p.Nt);
+  const int r0 = r - cy, c0 = c - cx;           // the cluster's first processor row / column
+  constexpr bool cyc = CYC;
   const int S = p.S, nkb = p.nkb;
   const int64_t nout = (p.Kpad + p.Bo - 1) / p.Bo;
   const bool a_contig = (TM / 8) % cn == 0, b_contig = (TN / 8) % cm == 0;
@@ -106,9 +108,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t stage = 0, phase = 0;
       bool ok = true;
       for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-        const int64_t m0 = row_lo + (int64_t)mi * TM;
+        if (tile_skipped(cyc, r0, mi, p.P, TM, p.M)) continue;
+        int64_t m0, row_lo, row_hi;
+        tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
         for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-          const int64_t n0 = col_lo + (int64_t)ni * TN;
+          if (tile_skipped(cyc, c0, ni, p.Q, TN, p.N)) continue;
+          int64_t n0, col_lo, col_hi;
+          tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
           for (int d = 2; d <= S + 1 && ok; ++d) {
             for (int s = 1; s < d && ok; ++s) {
               const int t = d - s;
@@ -121,12 +127,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   const int64_t o = k0 / p.Bo;
                   for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
                     const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
-                    if (c == (int)imin64(p.Q - 1, kq / p.Kq)) {
+                    if (c == outer_owner(cyc, q, kq, p.Kq, p.Q)) {
                       for (int64_t kk = kq; kk < kend; kk += BKS)
                         tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, s - 1);
                       pf += 1;
                     }
-                    if (r == (int)imin64(p.P - 1, kq / p.Kp)) {
+                    if (r == outer_owner(cyc, q, kq, p.Kp, p.P)) {
                       for (int64_t kk = kq; kk < kend; kk += BKS)
                         tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, t - 1);
                       pf += 1;
@@ -192,9 +198,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t stage = 0, phase = 0;
     bool ok = true;
     for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-      const int64_t m0 = row_lo + (int64_t)mi * TM;
+      if (tile_skipped(cyc, r0, mi, p.P, TM, p.M)) continue;
+      int64_t m0, row_lo, row_hi;
+      tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
       for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-        const int64_t n0 = col_lo + (int64_t)ni * TN;
+        if (tile_skipped(cyc, c0, ni, p.Q, TN, p.N)) continue;
+        int64_t n0, col_lo, col_hi;
+        tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
         for (int d = 2; d <= S + 1 && ok; ++d) {
           const int nst = (d - 1) * nkb;
           for (int seg = 0; seg * SEG_STAGES < nst && ok; ++seg) {
@@ -283,10 +293,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }  // namespace
 
 int int8_cluster_limit(int *limit) {
-  cudaError_t e = cudaFuncSetAttribute(int8_diag_kernel,
+  cudaError_t e = cudaFuncSetAttribute(int8_diag_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-  e = cudaFuncSetAttribute(int8_diag_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  e = cudaFuncSetAttribute(int8_diag_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16, 1, 1);
@@ -300,7 +310,7 @@ int int8_cluster_limit(int *limit) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  e = cudaOccupancyMaxPotentialClusterSize(&n, int8_diag_kernel, &cfg);
+  e = cudaOccupancyMaxPotentialClusterSize(&n, int8_diag_kernel<false>, &cfg);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxPotentialClusterSize");
   *limit = n;
   return HSUMMA_OK;
@@ -332,19 +342,20 @@ int launch_split_int8(const GridPlan &g, int S, const void *As, const void *Bs, 
   p.Q = g.Q;
   p.cm = g.cm;
   p.cn = g.cn;
-  p.nsub_m = (int)ceil_div(g.Mt, TM);
-  p.nsub_n = (int)ceil_div(g.Nt, TN);
+  p.nsub_m = (int)(g.cyc ? ceil_div(ceil_div(g.M, TM), g.P) : ceil_div(g.Mt, TM));
+  p.nsub_n = (int)(g.cyc ? ceil_div(ceil_div(g.N, TN), g.Q) : ceil_div(g.Nt, TN));
   p.Bo = g.Bo;
   p.S = S;
   p.nkb = (int)ceil_div(Kpad, BKS);
   p.nseg = split_planes(g.K, S, HSUMMA_INT8_SLICES);
   p.counters = state().d_counters;
   p.status = state().d_status;
-  cudaError_t e = cudaFuncSetAttribute(int8_diag_kernel,
+  auto kern = g.cyc ? int8_diag_kernel<true> : int8_diag_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
   if (g.cm * g.cn > 8) {
-    e = cudaFuncSetAttribute(int8_diag_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed,
                              1);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   }
@@ -360,7 +371,7 @@ int launch_split_int8(const GridPlan &g, int S, const void *As, const void *Bs, 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, int8_diag_kernel, tA, tB, tApf, tBpf, p);
+  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch int8_diag_kernel");
   return HSUMMA_OK;
 }

@@ -74,3 +74,15 @@ def test_errors_before_init(lib):
 def test_mode_encoding():
     assert hs.mode_code("bf16", 5) == 2 | (5 << 8)
     assert hs.mode_code("fp64") == 0
+    assert hs.mode_code("int8", 6, "cyclic") == 1 | (6 << 8) | 0x10000
+
+
+def test_layout_bit_accepted_and_other_high_bits_rejected(lib):
+    import ctypes
+    out = ctypes.c_size_t()
+    bf5 = hs.mode_code("bf16", 5)
+    assert lib.hsumma_workspace_size(300, 520, 700, bf5 | 0x10000, ctypes.byref(out)) == 0
+    assert out.value == hs.workspace_size(300, 520, 700, "bf16", 5)   # the layout adds none
+    for bad in (0x20000, 0x40000000, 0x10000 | 0x100000):
+        assert lib.hsumma_workspace_size(300, 520, 700, bf5 | bad, ctypes.byref(out)) == -1
+        assert "mode" in hs.last_error()
