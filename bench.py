@@ -32,23 +32,24 @@ sys.path.insert(0, ROOT)
 N_SIZE = 16384
 METRIC = "FP64-accurate TFLOP/s at n=16384, split-precision vs native FP64, % of roofline"
 SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=512, kind="bf16", slices=5)
-NATIVE = dict(P=128, Q=128, G=4096, b=32, Bouter=128)
+NATIVE = dict(P=128, Q=128, G=8192, b=32, Bouter=128)
 WORKLOAD = ("split_vs_fp64_16384: M=N=K=16384, A,B uniform[-1,1] (SplitMix64 seeds 1002/2002), "
             "bf16 slices S=5 (15 pair products), virtual grid 128x64 of 128x256 blocks, "
             "G=4096 groups of 2x1 (each group one CTA pair: the in-group B broadcast is the "
             "two-SM MMA), b=64, B=512 (owner L2 prefetch); "
-            "native fp64 beside it on a 128x128 grid, G=4096, b=32, B=128")
+            "native fp64 beside it on a 128x128 grid, G=8192 groups of 2x1 (2-CTA clusters), "
+            "b=32, B=128")
 
 
 def configure(n):
     """Grids for an n x n x n product: 128 x 256 blocks (split) and 128 x 128
-    blocks (binary64), groups of 2 x 2 processors."""
+    blocks (binary64), groups of 2 x 1 processors."""
     global N_SIZE, SPLIT, NATIVE, WORKLOAD
     if n % 256:
         raise SystemExit("--size must be a multiple of 256")
     N_SIZE = n
     SPLIT = dict(SPLIT, P=n // 128, Q=n // 256, G=max(1, (n // 128) * (n // 256) // 2))
-    NATIVE = dict(NATIVE, P=n // 128, Q=n // 128, G=(n // 128) ** 2 // 4)
+    NATIVE = dict(NATIVE, P=n // 128, Q=n // 128, G=max(1, (n // 128) ** 2 // 2))
     if n != 16384:
         WORKLOAD = (f"split_vs_fp64_{n}: M=N=K={n}, bf16 S=5, grid {n // 128}x{n // 256} of "
                     f"128x256 blocks, G={SPLIT['G']} (2x1 groups, CTA pairs), b=64, "
@@ -277,8 +278,9 @@ def run_table(sections):
         A, B, C = product(n, n, n, "uniform", "uniform", 1002, 2002)
         ms, _ = timed(lambda: hs.gemm(A, B, out=C, **NATIVE), warm=False)
         tf = 2 * n ** 3 / ms / 1e9
-        emit(workload="split_vs_fp64_16384", path="fp64", cfg="128x128 G=4096 b=32 B=128",
-             ms=ms, tflops=tf, frac_of_dmma=tf / dmma)
+        emit(workload="split_vs_fp64_16384", path="fp64",
+             cfg=" ".join(f"{k}={v}" for k, v in NATIVE.items()), ms=ms, tflops=tf,
+             frac_of_dmma=tf / dmma)
         split_cfg = {k: v for k, v in SPLIT.items() if k not in ("kind", "slices")}
         for kind, slices, cfg, peak in (
                 ("bf16", range(3, 7), split_cfg, bf16),

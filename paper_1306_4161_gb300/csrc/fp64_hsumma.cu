@@ -19,10 +19,15 @@
 // the k-ascending binary64 sum of its products, so integer inputs give exact
 // results for any G, b and Bouter.
 //
-// Roles: warps 0..7 compute (2 x 4 warps, 64 x 32 each); warp 8 issues the
-// copies.  A 4-stage ring of 32 KB stages; "full" barriers count the bytes of a
-// stage, "empty" barriers collect one release from every CTA that the stage's
-// producers deliver to (its cluster row and column).
+// Roles: warps 0..7 compute (2 x 4 warps, 64 x 32 each); thread 0 also
+// issues every copy: after each stage's release it refills whatever ring slots
+// every receiving CTA has released (without waiting), and it waits only when
+// the stage about to be multiplied has not been issued yet.  Eight warps put two on each SM
+// sub-partition, which leaves a thread up to 255 registers (a ninth, copy-only
+// warp would cap them at 168 and poll the barriers beside two compute warps).
+// A 4-stage ring of 32 KB stages; "full" barriers count the bytes of a stage,
+// "empty" barriers collect one release from every CTA that the stage's
+// copies deliver to (its cluster row and column).
 #include "internal.h"
 #include "ptx.cuh"
 #include "../../include/hsumma.h"
@@ -33,8 +38,7 @@ namespace {
 constexpr int TM = 128, TN = 128, BK = 16, STAGES = 4;
 constexpr int A_STAGE = TM * BK * 8;          // 16 KB: 16 pieces of 8 rows x 128 B
 constexpr int B_STAGE = BK * TN * 8;          // 16 KB: 8 n-boxes x 2 pieces
-constexpr int NCONS = 256;
-constexpr int NTHREADS = NCONS + 32;
+constexpr int NTHREADS = 256;
 constexpr int SMEM_BYTES = STAGES * (A_STAGE + B_STAGE) + 2 * STAGES * 8 + 1024;
 constexpr int PF_K = 32;                      // k extent of one prefetch box
 
@@ -59,6 +63,17 @@ __device__ __forceinline__ int64_t clamp_count(int64_t lo, int64_t hi, int64_t a
   int64_t x = a > lo ? a : lo, y = b < hi ? b : hi;
   return y > x ? y - x : 0;
 }
+
+// The copy cursor of thread 0: the next k-stage of the sub-tile sweep to load
+// into the ring, the ring slot it goes to, and the panel-load counters.
+struct CopyCursor {
+  int tile;                 // linear sub-tile index mi * nsub_n + ni (nsub_m * nsub_n: done)
+  int64_t kt;               // k-stage within the sub-tile
+  int rem;                  // k0 mod B, kept without a 64-bit division per stage
+  int64_t m0, row_lo, row_hi, n0, col_lo, col_hi;
+  uint32_t stage, phase;
+  unsigned long long a_ld, a_dl, b_ld, b_dl, pf, nops;
+};
 
 // CYC: block-cyclic layout of the grid, else block-checkerboard
 template <bool CYC>
@@ -93,7 +108,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     fence_mbar_init();
   }
-  if (threadIdx.x == NCONS) {
+  if (threadIdx.x == 32) {
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
   }
@@ -107,190 +122,223 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr bool cyc = CYC;
   const int64_t nk = (p.K + BK - 1) / BK;
   const int64_t nout = p.K > 0 ? (p.K + p.Bo - 1) / p.Bo : 0;
+  const int ntile = p.nsub_m * p.nsub_n;
 
-  if (warp == NCONS / 32) {
-    // ---------------- producer: one thread issues every copy ----------------
-    if (lane == 0) {
-      unsigned long long a_ld = 0, a_dl = 0, b_ld = 0, b_dl = 0, pf = 0, nops = 0;
-      uint32_t stage = 0, phase = 0;
-      bool ok = true;
-      for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
-        if (tile_skipped(cyc, r0, mi, p.P, TM, p.M)) continue;
-        int64_t m0, row_lo, row_hi;
-        tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
-        for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
-          if (tile_skipped(cyc, c0, ni, p.Q, TN, p.N)) continue;
-          int64_t n0, col_lo, col_hi;
-          tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
-          int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
-          for (int64_t kt = 0; kt < nk; ++kt) {
-            const int64_t k0 = kt * BK;
-            const bool outer = rem == 0;
-            for (rem += BK; rem >= p.Bo;) rem -= p.Bo;
-            if (outer) {
-              // outer step o: stage outer panel o (first step) and o + 1 into L2;
-              // the owner of an outer block is the processor whose own block of
-              // A (columns) / B (rows) contains its first index (block-cyclic:
-              // the processor column / row q mod Q / q mod P)
-              const int64_t o = k0 / p.Bo;
-              for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
-                const int64_t kq = q * p.Bo;
-                const int64_t kend = imin64(p.K, kq + p.Bo);
-                if (c == outer_owner(cyc, q, kq, p.Kq, p.Q)) {
-                  for (int64_t kk = kq; kk < kend; kk += PF_K)
-                    tma_prefetch_2d(&tmApf, (int32_t)kk, (int32_t)m0);
-                  pf += 1;
-                }
-                if (r == outer_owner(cyc, q, kq, p.Kp, p.P)) {
-                  for (int64_t kk = kq; kk < kend; kk += PF_K)
-                    tma_prefetch_2d(&tmBpf, (int32_t)n0, (int32_t)kk);
-                  pf += 1;
-                }
-              }
-            }
-            if (!mbar_wait_cluster(smem_u32(&empty[stage]), phase ^ 1u)) {
-              record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteEmpty);
-              ok = false;
-              break;
-            }
-            const uint32_t fb = smem_u32(&full[stage]);
-            mbar_arrive_expect_tx(fb, A_STAGE + B_STAGE);
-            const uint32_t a_dst = smem_u32(sA + stage * A_STAGE);
-            const uint32_t b_dst = smem_u32(sB + stage * B_STAGE);
-            const int64_t kc = clamp_count(0, p.K, k0, k0 + BK);
-            // A: 16 pieces of 8 rows x 16 k; piece i issued by cluster column i % cn
-            for (int i = cx; i < TM / 8; i += cn) {
-              const int64_t rr = m0 + i * 8;
-              if (cn > 1)
-                tma_load_2d_mc(a_dst + i * 1024, &tmA, (int32_t)k0, (int32_t)rr, fb, row_mask);
-              else
-                tma_load_2d(a_dst + i * 1024, &tmA, (int32_t)k0, (int32_t)rr, fb);
-              const int64_t cnt = clamp_count(row_lo, row_hi, rr, rr + 8) * kc;
-              a_ld += cnt;
-              a_dl += cnt * cn;
-              nops += 1;
-            }
-            // B: 8 n-boxes x 2 pieces of 8 k x 16 n; piece j issued by cluster row j % cm
-            for (int j = cy; j < 2 * (TN / 16); j += cm) {
-              const int64_t nn = n0 + (j >> 1) * 16, kk = k0 + (j & 1) * 8;
-              const uint32_t dst = b_dst + (j >> 1) * 2048 + (j & 1) * 1024;
-              if (cm > 1)
-                tma_load_2d_mc(dst, &tmB, (int32_t)nn, (int32_t)kk, fb, col_mask);
-              else
-                tma_load_2d(dst, &tmB, (int32_t)nn, (int32_t)kk, fb);
-              const int64_t cnt =
-                  clamp_count(col_lo, col_hi, nn, nn + 16) * clamp_count(0, p.K, kk, kk + 8);
-              b_ld += cnt;
-              b_dl += cnt * cm;
-              nops += 1;
-            }
-            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-          }
+  // ---------------- copies (thread 0) ----------------
+  CopyCursor cc = {};
+  // place the cursor on the first sub-tile at or after cc.tile that is not skipped
+  auto seek = [&]() {
+    for (; cc.tile < ntile; ++cc.tile) {
+      const int mi = cc.tile / p.nsub_n, ni = cc.tile - mi * p.nsub_n;
+      if (tile_skipped(cyc, r0, mi, p.P, TM, p.M) || tile_skipped(cyc, c0, ni, p.Q, TN, p.N))
+        continue;
+      tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &cc.m0, &cc.row_lo, &cc.row_hi);
+      tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &cc.n0, &cc.col_lo, &cc.col_hi);
+      break;
+    }
+    cc.kt = 0;
+    cc.rem = 0;
+  };
+  // issue the cursor's k-stage into its ring slot once every CTA the copies
+  // reach has released the slot, then advance.  1: issued; 0: the slot is not
+  // free yet (block = false only); -1: the wait ran out
+  auto issue = [&](bool block) -> int {
+    const uint32_t eb = smem_u32(&empty[cc.stage]);
+    if (block) {
+      if (!mbar_wait_cluster(eb, cc.phase ^ 1u)) return -1;
+    } else if (!mbar_try_wait_cluster(eb, cc.phase ^ 1u)) {
+      return 0;
+    }
+    const int64_t k0 = cc.kt * BK;
+    const bool outer = cc.rem == 0;
+    for (cc.rem += BK; cc.rem >= p.Bo;) cc.rem -= p.Bo;
+    if (outer) {
+      // outer step o: stage outer panel o (first step) and o + 1 into L2; the
+      // owner of an outer block is the processor whose own block of A
+      // (columns) / B (rows) contains its first index (block-cyclic: the
+      // processor column / row q mod Q / q mod P)
+      const int64_t o = k0 / p.Bo;
+      for (int64_t q = (o == 0 ? 0 : o + 1); q <= o + 1 && q < nout; ++q) {
+        const int64_t kq = q * p.Bo;
+        const int64_t kend = imin64(p.K, kq + p.Bo);
+        if (c == outer_owner(cyc, q, kq, p.Kq, p.Q)) {
+          for (int64_t kk = kq; kk < kend; kk += PF_K)
+            tma_prefetch_2d(&tmApf, (int32_t)kk, (int32_t)cc.m0);
+          cc.pf += 1;
+        }
+        if (r == outer_owner(cyc, q, kq, p.Kp, p.P)) {
+          for (int64_t kk = kq; kk < kend; kk += PF_K)
+            tma_prefetch_2d(&tmBpf, (int32_t)cc.n0, (int32_t)kk);
+          cc.pf += 1;
         }
       }
-      if (!ok) atomicExch(&abort_flag, 1);
-      atomicAdd(&p.counters[0], a_ld);
-      atomicAdd(&p.counters[1], a_dl);
-      atomicAdd(&p.counters[2], b_ld);
-      atomicAdd(&p.counters[3], b_dl);
-      atomicAdd(&p.counters[4], pf);
-      atomicAdd(&p.counters[5], nops);
     }
-  } else {
-    // ---------------- consumers: rank-16 updates with DMMA ----------------
-    const int wm = warp >> 2, wn = warp & 3;   // 2 x 4 warps, 64 x 32 each
-    const int g = lane >> 2, t = lane & 3;
-    uint32_t stage = 0, phase = 0;
-    bool ok = true;
-    for (int mi = 0; mi < p.nsub_m; ++mi) {
-      if (tile_skipped(cyc, r0, mi, p.P, TM, p.M)) continue;
-      for (int ni = 0; ni < p.nsub_n; ++ni) {
-        if (tile_skipped(cyc, c0, ni, p.Q, TN, p.N)) continue;
-        double acc[4][4][4];
+    const uint32_t fb = smem_u32(&full[cc.stage]);
+    mbar_arrive_expect_tx(fb, A_STAGE + B_STAGE);
+    const uint32_t a_dst = smem_u32(sA + cc.stage * A_STAGE);
+    const uint32_t b_dst = smem_u32(sB + cc.stage * B_STAGE);
+    const int64_t kc = clamp_count(0, p.K, k0, k0 + BK);
+    // A: 16 pieces of 8 rows x 16 k; piece i issued by cluster column i % cn
+    for (int i = cx; i < TM / 8; i += cn) {
+      const int64_t rr = cc.m0 + i * 8;
+      if (cn > 1)
+        tma_load_2d_mc(a_dst + i * 1024, &tmA, (int32_t)k0, (int32_t)rr, fb, row_mask);
+      else
+        tma_load_2d(a_dst + i * 1024, &tmA, (int32_t)k0, (int32_t)rr, fb);
+      const int64_t cnt = clamp_count(cc.row_lo, cc.row_hi, rr, rr + 8) * kc;
+      cc.a_ld += cnt;
+      cc.a_dl += cnt * cn;
+      cc.nops += 1;
+    }
+    // B: 8 n-boxes x 2 pieces of 8 k x 16 n; piece j issued by cluster row j % cm
+    for (int j = cy; j < 2 * (TN / 16); j += cm) {
+      const int64_t nn = cc.n0 + (j >> 1) * 16, kk = k0 + (j & 1) * 8;
+      const uint32_t dst = b_dst + (j >> 1) * 2048 + (j & 1) * 1024;
+      if (cm > 1)
+        tma_load_2d_mc(dst, &tmB, (int32_t)nn, (int32_t)kk, fb, col_mask);
+      else
+        tma_load_2d(dst, &tmB, (int32_t)nn, (int32_t)kk, fb);
+      const int64_t cnt =
+          clamp_count(cc.col_lo, cc.col_hi, nn, nn + 16) * clamp_count(0, p.K, kk, kk + 8);
+      cc.b_ld += cnt;
+      cc.b_dl += cnt * cm;
+      cc.nops += 1;
+    }
+    if (++cc.stage == STAGES) { cc.stage = 0; cc.phase ^= 1u; }
+    if (++cc.kt == nk) {
+      ++cc.tile;
+      seek();
+    }
+    return 1;
+  };
+  // thread 0: stages issued so far; issue until stage `upto` is issued
+  // (blocking) or while slots are free, never more than the ring holds beyond
+  // the stages multiplied so far (a slot's barrier is then at most one phase
+  // ahead, so its parity test cannot alias)
+  int64_t issued = 0;
+  bool copy_bad = false;        // thread 0: a wait for a free slot ran out
+  auto refill = [&](int64_t upto, int64_t cap, bool block) {
+    while (!copy_bad && cc.tile < ntile && issued < cap && (!block || issued <= upto)) {
+      const int rc = issue(block && issued <= upto);
+      if (rc < 0) {
+        copy_bad = true;
+        record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteEmpty);
+      }
+      if (rc <= 0) break;
+      ++issued;
+    }
+  };
+  if (threadIdx.x == 0) {
+    if (nk > 0) seek();
+    else cc.tile = ntile;
+    refill(STAGES - 1, STAGES, true);           // the first STAGES stages
+  }
+
+  // ---------------- rank-16 updates with DMMA (all warps) ----------------
+  const int wm = warp >> 2, wn = warp & 3;     // 2 x 4 warps, 64 x 32 each
+  const int g = lane >> 2, t = lane & 3;
+  uint32_t stage = 0, phase = 0;
+  int64_t gst = 0;              // stages multiplied so far
+  bool ok = true;
+  for (int mi = 0; mi < p.nsub_m; ++mi) {
+    if (tile_skipped(cyc, r0, mi, p.P, TM, p.M)) continue;
+    for (int ni = 0; ni < p.nsub_n; ++ni) {
+      if (tile_skipped(cyc, c0, ni, p.Q, TN, p.N)) continue;
+      double acc[4][4][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b)
+        for (int b = 0; b < 4; ++b)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.0;
-        for (int64_t kt = 0; kt < nk; ++kt) {
-          bool bad = !mbar_wait(smem_u32(&full[stage]), phase);
-          if (bad) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteFull);
-          // all consumer threads decide together whether to go on
-          if (named_barrier_or(2, NCONS, bad)) {
-            ok = false;
-            break;
-          }
-          const uint8_t *a_base = sA + stage * A_STAGE;
-          const uint8_t *b_base = sB + stage * B_STAGE;
-          // not unrolled: the unrolled loop's hoisted fragment loads spill
-          // registers at the 168-per-thread limit of a 9-warp block
-#pragma unroll 1
-          for (int kk = 0; kk < BK / 4; ++kk) {
-            const int k = kk * 4 + t;
-            double af[4][2], bf[4];
-#pragma unroll
-            for (int mt = 0; mt < 4; ++mt) {
-              const int row = wm * 64 + mt * 16 + g;
-              af[mt][0] = *reinterpret_cast<const double *>(a_base + swz128(row, k * 8));
-              af[mt][1] = *reinterpret_cast<const double *>(a_base + swz128(row + 8, k * 8));
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-              const int n = wn * 32 + nt * 8 + g;
-              bf[nt] = *reinterpret_cast<const double *>(b_base + (n >> 4) * 2048 +
-                                                         swz128(k, (n & 15) * 8));
-            }
-#pragma unroll
-            for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-              for (int nt = 0; nt < 4; ++nt) dmma(acc[mt][nt], af[mt][0], af[mt][1], bf[nt]);
-          }
-          // release the stage to every CTA that delivers into it
-          named_barrier(1, NCONS);
-          if (threadIdx.x == 0) {
-            const uint32_t eb = smem_u32(&empty[stage]);
-            for (int x = 0; x < cn; ++x) mbar_arrive_cluster(eb, (uint32_t)(cy * cn + x));
-            for (int y = 0; y < cm; ++y)
-              if (y != cy) mbar_arrive_cluster(eb, (uint32_t)(y * cn + cx));
-          }
-          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.0;
+      for (int64_t kt = 0; kt < nk; ++kt, ++gst) {
+        // thread 0 makes sure this stage is issued; it does not wait for a
+        // stage its copies could not issue
+        if (threadIdx.x == 0) refill(gst, gst + STAGES, true);
+        const bool bad = (threadIdx.x == 0 && copy_bad) || !mbar_wait(smem_u32(&full[stage]), phase);
+        if (bad && !(threadIdx.x == 0 && copy_bad)) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteFull);
+        // all threads decide together whether to go on
+        if (named_barrier_or(2, NTHREADS, bad)) {
+          ok = false;
+          break;
         }
-        if (!ok) break;
-        // epilogue: C := the sub-tile (beta = 0), rows/cols inside the block
-        // (block-cyclic: inside the tile and the matrix)
-        int64_t m0, row_lo, row_hi, n0, col_lo, col_hi;
-        if (cyc) {
-          tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
-          tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
-        } else {
-          m0 = blk_row_lo + (int64_t)mi * TM, row_hi = blk_row_hi;
-          n0 = blk_col_lo + (int64_t)ni * TN, col_hi = blk_col_hi;
-        }
+        const uint8_t *a_base = sA + stage * A_STAGE;
+        const uint8_t *b_base = sB + stage * B_STAGE;
 #pragma unroll
-        for (int mt = 0; mt < 4; ++mt) {
+        for (int kk = 0; kk < BK / 4; ++kk) {
+          const int k = kk * 4 + t;
+          double af[4][2], bf[4];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int64_t row = m0 + wm * 64 + mt * 16 + g + h * 8;
-            if (row >= row_hi) continue;
-            double *crow = p.C + row * p.ldc;
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-              const int64_t col = n0 + wn * 32 + nt * 8 + 2 * t;
-              const double v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
-              if (col + 1 < col_hi && ((reinterpret_cast<uintptr_t>(crow + col) & 15) == 0)) {
-                *reinterpret_cast<double2 *>(crow + col) = make_double2(v0, v1);
-              } else {
-                if (col < col_hi) crow[col] = v0;
-                if (col + 1 < col_hi) crow[col + 1] = v1;
-              }
-            }
+          for (int mt = 0; mt < 4; ++mt) {
+            const int row = wm * 64 + mt * 16 + g;
+            af[mt][0] = *reinterpret_cast<const double *>(a_base + swz128(row, k * 8));
+            af[mt][1] = *reinterpret_cast<const double *>(a_base + swz128(row + 8, k * 8));
           }
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const int n = wn * 32 + nt * 8 + g;
+            bf[nt] = *reinterpret_cast<const double *>(b_base + (n >> 4) * 2048 +
+                                                       swz128(k, (n & 15) * 8));
+          }
+#pragma unroll
+          for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) dmma(acc[mt][nt], af[mt][0], af[mt][1], bf[nt]);
         }
+        // release the stage to every CTA that delivers into it, then refill
+        // the slots that are free already
+        named_barrier(1, NTHREADS);
+        if (threadIdx.x == 0) {
+          const uint32_t eb = smem_u32(&empty[stage]);
+          for (int x = 0; x < cn; ++x) mbar_arrive_cluster(eb, (uint32_t)(cy * cn + x));
+          for (int y = 0; y < cm; ++y)
+            if (y != cy) mbar_arrive_cluster(eb, (uint32_t)(y * cn + cx));
+          refill(gst + 1, gst + 1 + STAGES, false);
+        }
+        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
       }
       if (!ok) break;
+      // epilogue: C := the sub-tile (beta = 0), rows/cols inside the block
+      // (block-cyclic: inside the tile and the matrix)
+      int64_t m0, row_lo, row_hi, n0, col_lo, col_hi;
+      if (cyc) {
+        tile_rows(cyc, r, mi, p.P, p.Mt, TM, p.M, &m0, &row_lo, &row_hi);
+        tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
+      } else {
+        m0 = blk_row_lo + (int64_t)mi * TM, row_hi = blk_row_hi;
+        n0 = blk_col_lo + (int64_t)ni * TN, col_hi = blk_col_hi;
+      }
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t row = m0 + wm * 64 + mt * 16 + g + h * 8;
+          if (row >= row_hi) continue;
+          double *crow = p.C + row * p.ldc;
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const int64_t col = n0 + wn * 32 + nt * 8 + 2 * t;
+            const double v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+            if (col + 1 < col_hi && ((reinterpret_cast<uintptr_t>(crow + col) & 15) == 0)) {
+              *reinterpret_cast<double2 *>(crow + col) = make_double2(v0, v1);
+            } else {
+              if (col < col_hi) crow[col] = v0;
+              if (col + 1 < col_hi) crow[col + 1] = v1;
+            }
+          }
+        }
+      }
     }
-    if (!ok) atomicExch(&abort_flag, 1);
+    if (!ok) break;
+  }
+  if (!ok) atomicExch(&abort_flag, 1);
+  if (threadIdx.x == 0) {
+    atomicAdd(&p.counters[0], cc.a_ld);
+    atomicAdd(&p.counters[1], cc.a_dl);
+    atomicAdd(&p.counters[2], cc.b_ld);
+    atomicAdd(&p.counters[3], cc.b_dl);
+    atomicAdd(&p.counters[4], cc.pf);
+    atomicAdd(&p.counters[5], cc.nops);
   }
   __syncthreads();
   // an aborted CTA may still have copies in flight into its shared memory:
