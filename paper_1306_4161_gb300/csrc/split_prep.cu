@@ -103,53 +103,71 @@ __global__ void exponents_cols_kernel(const double *__restrict__ B, int64_t ldb,
   }
 }
 
-// The digits of one value, slice by slice: Y_s = RN(|x| 2^-e 2^(w s)) (ties to
-// even) as a signed integer, and digit s = Y_s - 2^w Y_(s-1).  The state holds
-// the significand, the exponent of its last bit, the sign and Y_(s-1), so no
-// table indexed by the (run-time) slice number is needed.
+// The digits of one value, slice by slice.  With F = floor(|x| 2^-e 2^64)
+// (below 2^63, since the exponent scan makes |x| 2^-e < 1/2) and Y_s =
+// RN(|x| 2^-e 2^(W s)) (ties to even), digit s is t_s = Y_s - 2^W Y_(s-1).
+// Writing Y_s = q_s + c_s with q_s = floor(F / 2^(p+1)), p = 63 - W s, and c_s
+// the rounding increment, and since q_(s-1) = floor(q_s / 2^W):
+//   t_s = (q_s mod 2^W) + c_s - 2^W c_(s-1),
+// where q_s mod 2^W is the W-bit field of F above bit p and
+//   c_s = (bit p of F) and (any lower bit of F, or a bit dropped below F,
+//                           or bit p + 1 of F)          (round half to even).
+// Bit p is the same for every value of a slice, so a digit costs a shift, a
+// comparison, a few masks and no branch ("any lower bit" is tz < p, tz the
+// trailing zero count of F, -1 when bits were dropped below F).  W S <= 63
+// (bf16: S <= 7; int8: S <= 8).  A negative x has the negated digits
+// (rounding to nearest is symmetric).
 struct DigitGen {
-  unsigned long long m;
-  int lsb;    // binary exponent of m's least significant bit
+  unsigned long long F;
+  int tz;            // trailing zeros of F; -1 if |x| 2^-e 2^64 is not an integer; 64 if 0
   bool neg;
-  long long prev;
+  int cprev;         // c_(s-1)
 
-  __device__ __forceinline__ void init(double x) {
+  __device__ __forceinline__ void init(double x, int e) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     neg = (bits >> 63) != 0;
     const int E = (int)((bits >> 52) & 0x7FF);
-    m = bits & 0xFFFFFFFFFFFFFull;
+    unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+    int lsb;        // binary exponent of m's least significant bit
     if (E > 0) {
       m |= 1ull << 52;
       lsb = E - 1075;
     } else {
       lsb = -1074;
     }
-    prev = 0;
+    const int sh = lsb - e + 64;     // |x| 2^-e 2^64 = m 2^sh
+    bool sticky;                     // bits of m dropped below F
+    if (sh >= 0) {
+      F = m << (sh < 63 ? sh : 63);  // exact (the guard only keeps the shift defined)
+      sticky = false;
+    } else if (sh > -64) {
+      F = m >> -sh;
+      sticky = (m << (64 + sh)) != 0;
+    } else {
+      F = 0;
+      sticky = m != 0;
+    }
+    tz = sticky ? -1 : (F ? __ffsll((long long)F) - 1 : 64);
+    cprev = 0;
   }
 
-  // digit s (1-based) of w-bit slices for the scale 2^-e
+  // digit s for p = 63 - W s (the same for every value)
   template <int W>
-  __device__ __forceinline__ int next(int s, int e) {
-    // |x| 2^-e 2^(w s) = m 2^sh, rounded to nearest (ties to even):
-    // RNE(m / 2^d) = (m + 2^(d-1) - 1 + ((m >> d) & 1)) >> d for 1 <= d <= 54
-    const int sh = lsb - e + W * s;
-    unsigned long long y;
-    if (sh >= 0) {
-      // m 2^sh < 2^(w s - 1) <= 2^55 when e comes from the exponent scan (the
-      // guard only keeps the shift defined for other e)
-      y = m << (sh < 63 ? sh : 63);
-    } else if (-sh > 54) {
-      y = 0;        // m 2^sh < 2^53 2^-55 < 1/2
-    } else {
-      const int d = -sh;
-      y = (m + ((1ull << (d - 1)) - 1ull) + ((m >> d) & 1ull)) >> d;
-    }
-    const long long Y = neg ? -(long long)y : (long long)y;
-    const int t = (int)(Y - prev * (1ll << W));
-    prev = Y;
-    return t;
+  __device__ __forceinline__ int next(int p) {
+    const uint32_t win = (uint32_t)(F >> p);    // bit 0: rounding bit; bits 1..W: field
+    const int field = (int)((win >> 1) & ((1u << W) - 1u));
+    const int c = (int)(win & 1u) & ((int)(tz < p) | (field & 1));
+    const int t = field + c - (cprev << W);
+    cprev = c;
+    return neg ? -t : t;
   }
 };
+
+// An integer |t| < 2^22 as a float without the integer-to-float unit: its bits
+// placed in the significand of 2^23 + 2^22, then that constant subtracted.
+__device__ __forceinline__ float small_int_to_float(int t) {
+  return __int_as_float(0x4B400000 + t) - 12582912.0f;
+}
 
 // Eight digits of one slice, stored at dst: bf16 (16 bytes) or int8 (8 bytes).
 template <int KIND>
@@ -166,7 +184,8 @@ __device__ __forceinline__ void store8(void *dst, const int (&t)[8]) {
     uint32_t *w = reinterpret_cast<uint32_t *>(&v);
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      __nv_bfloat162 b = __floats2bfloat162_rn((float)t[2 * h], (float)t[2 * h + 1]);
+      __nv_bfloat162 b =
+          __floats2bfloat162_rn(small_int_to_float(t[2 * h]), small_int_to_float(t[2 * h + 1]));
       w[h] = *reinterpret_cast<uint32_t *>(&b);
     }
     *reinterpret_cast<uint4 *>(dst) = v;
@@ -202,20 +221,24 @@ __global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restri
   }
   DigitGen g[8];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) g[u].init(x[u]);
+  for (int u = 0; u < 8; ++u) g[u].init(x[u], ei);
   uint8_t *base = reinterpret_cast<uint8_t *>(out) + (i * Kp + k0) * EB;
   const int64_t plane = M * Kp * EB;
   for (int s = 1; s <= S; ++s) {
     int t[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) t[u] = g[u].next<W>(s, ei);
+    for (int u = 0; u < 8; ++u) t[u] = g[u].next<W>(63 - W * s);
     store8<KIND>(base + (s - 1) * plane, t);
   }
 }
 
-// B slices, transposed: Bs[t][j][k]; a block transposes a 64 (k) x 64 (j) tile,
-// each thread then forms 8 consecutive k of one column j (8 threads write one
-// 64-k row segment of Bs)
+// B slices, transposed: Bs[t][j][k].  A block covers 32 columns x 64 k: lane
+// l of warp w forms the digits of column j0 + l at k = k0 + 8 w .. + 7, so a
+// warp's loads are 32 consecutive doubles of each of 8 rows of B, and the
+// block's 8 warps together write 128 contiguous bytes (bf16) of every column
+// and slice.  One-dimensional grid, column blocks fastest (neighbouring blocks
+// read the same rows of B); any product whose slices fit in memory has fewer
+// than 2^31 blocks.
 template <int KIND>
 __global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restrict__ B,
                                                           int64_t ldb, int64_t K, int64_t N,
@@ -224,31 +247,26 @@ __global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restri
                                                           void *__restrict__ out) {
   constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
   constexpr int EB = KIND == HSUMMA_INT8_SLICES ? 1 : 2;
-  __shared__ double tile[64][65];
-  const int64_t k0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 64;
-  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 256 threads: 64 x 4
-  for (int r = ty; r < 64; r += 4) {
-    const int64_t k = k0 + r, j = j0 + tx;
-    tile[r][tx] = (k < K && j < N) ? B[k * ldb + j] : 0.0;
-  }
-  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t njb = (uint32_t)((N + 31) / 32);
+  const uint32_t kb = blockIdx.x / njb, jb = blockIdx.x - kb * njb;
+  const int64_t j = (int64_t)jb * 32 + lane;
+  const int64_t k0 = (int64_t)kb * 64 + w * 8;
+  if (j >= N) return;
+  const int fj = f[j];
+  double x[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? B[(k0 + u) * ldb + j] : 0.0;
+  DigitGen g[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) g[u].init(x[u], fj);
+  uint8_t *base = reinterpret_cast<uint8_t *>(out) + (j * Kp + k0) * EB;
   const int64_t plane = N * Kp * EB;
-  // thread -> (j = j0 + jj, k = k0 + kk .. kk + 7)
-  for (int idx = threadIdx.x; idx < 64 * 8; idx += 256) {
-    const int jj = idx >> 3, kk = (idx & 7) * 8;
-    const int64_t j = j0 + jj;
-    if (j >= N) continue;
-    const int fj = f[j];
-    DigitGen g[8];
+  for (int s = 1; s <= S; ++s) {
+    int t[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) g[u].init(tile[kk + u][jj]);
-    uint8_t *base = reinterpret_cast<uint8_t *>(out) + (j * Kp + k0 + kk) * EB;
-    for (int s = 1; s <= S; ++s) {
-      int t[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) t[u] = g[u].next<W>(s, fj);
-      store8<KIND>(base + (s - 1) * plane, t);
-    }
+    for (int u = 0; u < 8; ++u) t[u] = g[u].next<W>(63 - W * s);
+    store8<KIND>(base + (s - 1) * plane, t);
   }
 }
 
@@ -330,9 +348,14 @@ __device__ __forceinline__ double round_scaled(__int128 X, int k) {
 // X = sum_d D_d 2^(w (S+1-d)) by Horner's rule (constant shifts), rounded once.
 // Each thread takes four consecutive columns of one row: 16-byte loads from
 // every plane when the rows are 16-byte aligned (N a multiple of 4), 16-byte
-// stores of C when its row allows, element by element otherwise.
+// stores of C when its row allows, element by element otherwise.  The first
+// segment plane of every diagonal is loaded before any arithmetic, so that
+// all S loads of a thread are in flight at once; further segment planes (K
+// beyond one segment) follow one diagonal at a time.
+// (four resident blocks per SM keep more loads in flight; the kernels of 7 and
+// 8 slices need more than the 64 registers that leaves)
 template <int W, int S>
-__global__ void __launch_bounds__(256) recombine_kernel(const int32_t *__restrict__ D, int nseg,
+__global__ void __launch_bounds__(256, S <= 6 ? 4 : 3) recombine_kernel(const int32_t *__restrict__ D, int nseg,
                                                         int64_t M, int64_t N,
                                                         const int32_t *__restrict__ e,
                                                         const int32_t *__restrict__ f,
@@ -343,23 +366,28 @@ __global__ void __launch_bounds__(256) recombine_kernel(const int32_t *__restric
   const int64_t plane = M * N, off = i * N + j0;
   const bool full = j0 + 3 < N;
   const bool vec = full && (N & 3) == 0;
+  auto load4 = [&](const int32_t *src, int (&v)[4]) {
+    if (vec) {
+      const int4 q = __ldg(reinterpret_cast<const int4 *>(src));
+      v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = j0 + u < N ? __ldg(src + u) : 0;
+    }
+  };
+  int first[S][4];
+#pragma unroll
+  for (int d = 0; d < S; ++d) load4(D + (int64_t)(d * nseg) * plane + off, first[d]);
   __int128 X[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int d = 2; d <= S + 1; ++d) {
-    long long Dd[4] = {0, 0, 0, 0};   // the segment planes of a diagonal sum exactly in 64 bits
-    for (int g = 0; g < nseg; ++g) {
-      const int32_t *src = D + (int64_t)((d - 2) * nseg + g) * plane + off;
-      if (vec) {
-        const int4 v = __ldg(reinterpret_cast<const int4 *>(src));
-        Dd[0] += v.x;
-        Dd[1] += v.y;
-        Dd[2] += v.z;
-        Dd[3] += v.w;
-      } else {
+  for (int d = 0; d < S; ++d) {
+    long long Dd[4] = {first[d][0], first[d][1], first[d][2], first[d][3]};
+    // the segment planes of a diagonal sum exactly in 64 bits
+    for (int g = 1; g < nseg; ++g) {
+      int v[4];
+      load4(D + (int64_t)(d * nseg + g) * plane + off, v);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (j0 + u < N) Dd[u] += __ldg(src + u);
-      }
+      for (int u = 0; u < 4; ++u) Dd[u] += v[u];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) X[u] = (X[u] << W) + (__int128)Dd[u];
@@ -424,6 +452,12 @@ int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
   const int64_t Kp = ceil_div(K, 64) * 64;
   if (Kp == 0) return HSUMMA_OK;
   const int64_t nA = M * (Kp / 8);
+  const int64_t ncb = N > 0 ? (Kp / 64) * ceil_div(N, 32) : 0;
+  if (ceil_div(nA, 256) > 0x7fffffff || ncb > 0x7fffffff) {
+    set_error("slicing grid too large (M=%lld N=%lld K=%lld)", (long long)M, (long long)N,
+              (long long)K);
+    return HSUMMA_ERR_UNSUPPORTED;
+  }
   if (nA > 0) {
     const unsigned blocks = (unsigned)ceil_div(nA, 256);
     if (kind == HSUMMA_INT8_SLICES)
@@ -432,7 +466,7 @@ int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
       slices_rows_kernel<HSUMMA_BF16_SLICES><<<blocks, 256, 0, s>>>(A, lda, M, K, Kp, e, S, As);
   }
   if (N > 0) {
-    dim3 grid((unsigned)(Kp / 64), (unsigned)ceil_div(N, 64));
+    const unsigned grid = (unsigned)ncb;
     if (kind == HSUMMA_INT8_SLICES)
       slices_cols_kernel<HSUMMA_INT8_SLICES><<<grid, 256, 0, s>>>(B, ldb, K, N, Kp, f, S, Bs);
     else
