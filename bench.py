@@ -459,7 +459,23 @@ def main():
         e2e = {"value": world * flops() / te / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
                "ms_per_step": te * 1e3}
-        del hA, hB, hC
+        # this box's pinned host-link rates (outside the timed region): the
+        # copies alone need max(H2D bytes / H2D rate, D2H bytes / D2H rate)
+        scratch = torch.empty_like(dA)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        rates = {}
+        for name, dst, src in (("h2d", scratch, hA), ("d2h", hA, scratch)):
+            best = float("inf")
+            for _ in range(3):
+                c0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                c1.record(stream)
+                c1.synchronize()
+                best = min(best, c0.elapsed_time(c1))
+            rates[name] = src.numel() * 8 / best / 1e6
+        e2e["link_gbps"] = {k: round(v, 1) for k, v in rates.items()}
+        e2e["copy_floor_ms"] = max(2 * 8 * n * n / rates["h2d"], 8 * n * n / rates["d2h"]) / 1e6
+        del hA, hB, hC, scratch
 
     # sampled entries of the split result (accuracy is computed in the CPU leg):
     # every tile-border row and column (128 x 128 tiles) and seeded ones, their
