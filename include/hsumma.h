@@ -140,6 +140,12 @@ int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *h_A,
 /* Counters of the last hsumma_gemm launch (call after hsumma_sync). */
 int hsumma_get_counters(hsumma_counters *out);
 
+/* Number of kernel launches the library has issued for products (exponent
+ * scan, slicing, products, recombination; binary64: the product kernel) since
+ * it was loaded.  Read it before and after a region to count that region's
+ * launches.  Host-side count; needs no device and no hsumma_init. */
+unsigned long long hsumma_launches(void);
+
 /* Synchronise `stream` and report device-side errors recorded since the last
  * call (HSUMMA_ERR_TIMEOUT, HSUMMA_ERR_NONFINITE) or a CUDA error. */
 int hsumma_sync(void *stream);

@@ -57,6 +57,7 @@ _SIGS = {
     "hsumma_gemm_host": ([_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64] + [_i32] * 6
                          + [_vp], _i32),
     "hsumma_get_counters": ([ctypes.POINTER(Counters)], _i32),
+    "hsumma_launches": ([], ctypes.c_uint64),
     "hsumma_sync": ([_vp], _i32),
     "hsumma_last_error": ([], ctypes.c_char_p),
     "hsumma_split_exponents": ([_i64, _i64, _i64, _dp, _i64, _dp, _i64, _vp, _vp, _vp], _i32),
@@ -234,6 +235,11 @@ def gemm_host(A, B, C, *, P, Q, G, b, Bouter, kind="fp64", slices=0, layout="blo
 
 def sync(stream=_DEFAULT):
     _check(lib().hsumma_sync(_stream_ptr(stream)))
+
+
+def launches() -> int:
+    """Kernel launches the library has issued for products since it was loaded."""
+    return int(lib().hsumma_launches())
 
 
 def counters() -> dict:

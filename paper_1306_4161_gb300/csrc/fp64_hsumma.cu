@@ -426,6 +426,7 @@ int launch_fp64_hsumma(const GridPlan &g, const double *A, int64_t lda, const do
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch fp64_hsumma_kernel");
+  count_launch();
   return HSUMMA_OK;
 }
 

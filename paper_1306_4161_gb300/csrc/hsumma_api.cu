@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <array>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -193,6 +194,11 @@ static bool tma_ready(const void *p, int64_t ld) {
   return (((uintptr_t)p) & 15) == 0 && (ld & 1) == 0;
 }
 
+// kernel launches issued on the product path since the library was loaded
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n); }
+
 }  // namespace hs
 
 using namespace hs;
@@ -287,6 +293,8 @@ int hsumma_group_shape(int P, int Q, int G, int *I, int *J, int *cluster_m, int 
   const int limit = g_init ? g_state.cluster_limit : 16;
   return resolve_groups(P, Q, G, limit, I, J, cluster_m, cluster_n);
 }
+
+unsigned long long hsumma_launches(void) { return g_launches.load(); }
 
 static int split_kind_and_S(int mode, int *kind, int *S) {
   *kind = mode & 0xff;

@@ -39,6 +39,8 @@ struct DeviceState {
 };
 
 DeviceState &state();
+// Kernel launches issued on the product path (hsumma_launches reads the total).
+void count_launch(int n = 1);
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 

@@ -56,6 +56,7 @@ struct PairParams {
   int32_t *D;
   int64_t M, N, K, Kpad, Mt, Nt, Kq, Kp;
   int P, Q, nsub_m, nsub_n, Bo, S, nkb, nseg;
+  int d_lo, d_hi;                // the diagonals (slice pairs s + t = d) of this launch
   unsigned long long *counters;
   int *status;
 };
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
   cluster_sync();
 
-  const int S = p.S, nkb = p.nkb;
+  const int nkb = p.nkb;
   constexpr bool cyc = CYC;
   const int64_t nout = (p.Kpad + p.Bo - 1) / p.Bo;
 
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int64_t n0, col_lo, col_hi;
             tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
             const int64_t nh = n0 + ry * HN;
-            for (int d = 2; d <= S + 1 && ok; ++d) {
+            for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
                 int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
@@ -188,12 +189,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int64_t o = k0 / p.Bo;
                     int ns = s + 1, nd = d;
                     if (ns >= nd) { ++nd; ns = 1; }
-                    const bool first = (d == 2 && s == 1 && o == 0);
+                    const bool first = (d == p.d_lo && s == 1 && o == 0);
                     for (int w = first ? 0 : 1; w <= 1; ++w) {
                       int64_t q = o + w;
                       int ps = s, pt = t;
                       if (q >= nout) {
-                        if (nd > S + 1) break;
+                        if (nd > p.d_hi) break;
                         q = 0;
                         ps = ns;
                         pt = nd - ns;
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (tile_skipped(cyc, r - ry, mi, p.P, TM, p.M)) continue;
           for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
             if (tile_skipped(cyc, c - px, ni, p.Q, TN, p.N)) continue;
-            for (int d = 2; d <= S + 1 && ok; ++d) {
+            for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
               const int nst = (d - 1) * nkb;
               for (int st = 0; st < nst; ++st, ++gst) {
                 if ((st & 1) != me) continue;
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &t0, &col_lo, &col_hi);
           const int64_t n0 = t0 + h * 128;
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
-          for (int d = 2; d <= S + 1 && ok; ++d) {
+          for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
             const int nst = (d - 1) * nkb;
             for (int seg = 0; seg * SEGST < nst && ok; ++seg) {
               const int seg_len = min(nst, (seg + 1) * SEGST) - seg * SEGST;
@@ -485,8 +486,18 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
-  return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "launch bf16 pair kernel");
+  // one launch per diagonal: the clusters resident together start each launch
+  // in step, and a tile's work is at most S slice pairs, so they drift apart
+  // less than within one launch of all S (S+1) / 2 pairs, and the L2 keeps
+  // serving the panels they share (a whole product in one launch read 2.4 x
+  // the DRAM bytes of its tile rounds at S = 5, a single round exactly those)
+  for (int d = 2; d <= S + 1; ++d) {
+    p.d_lo = p.d_hi = d;
+    e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
+    if (e != cudaSuccess) return cuda_fail(e, "launch bf16 pair kernel");
+    count_launch();
+  }
+  return HSUMMA_OK;
 }
 
 }  // namespace hs

@@ -373,6 +373,7 @@ int launch_split_int8(const GridPlan &g, int S, const void *As, const void *Bs, 
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch int8_diag_kernel");
+  count_launch();
   return HSUMMA_OK;
 }
 

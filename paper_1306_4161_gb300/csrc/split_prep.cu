@@ -411,6 +411,7 @@ template <int W, int S>
 void recombine_launch(dim3 grid, cudaStream_t s, const int32_t *D, int nseg, int64_t M,
                       int64_t N, const int32_t *e, const int32_t *f, double *C, int64_t ldc) {
   recombine_kernel<W, S><<<grid, 256, 0, s>>>(D, nseg, M, N, e, f, C, ldc);
+  count_launch();
 }
 
 template <int W>
@@ -438,9 +439,11 @@ int launch_split_exponents(int64_t M, int64_t N, int64_t K, const double *A, int
   if (M > 0) {
     const int64_t blocks = ceil_div(M, 8);
     exponents_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, lda, M, K, e, status);
+    count_launch();
   }
   if (N > 0) {
     exponents_cols_kernel<<<(unsigned)ceil_div(N, 64), 256, 0, s>>>(B, ldb, K, N, f, status);
+    count_launch();
   }
   cudaError_t err = cudaGetLastError();
   return err == cudaSuccess ? HSUMMA_OK : cuda_fail(err, "launch exponent scan");
@@ -464,6 +467,7 @@ int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
       slices_rows_kernel<HSUMMA_INT8_SLICES><<<blocks, 256, 0, s>>>(A, lda, M, K, Kp, e, S, As);
     else
       slices_rows_kernel<HSUMMA_BF16_SLICES><<<blocks, 256, 0, s>>>(A, lda, M, K, Kp, e, S, As);
+    count_launch();
   }
   if (N > 0) {
     const unsigned grid = (unsigned)ncb;
@@ -471,6 +475,7 @@ int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
       slices_cols_kernel<HSUMMA_INT8_SLICES><<<grid, 256, 0, s>>>(B, ldb, K, N, Kp, f, S, Bs);
     else
       slices_cols_kernel<HSUMMA_BF16_SLICES><<<grid, 256, 0, s>>>(B, ldb, K, N, Kp, f, S, Bs);
+    count_launch();
   }
   cudaError_t err = cudaGetLastError();
   return err == cudaSuccess ? HSUMMA_OK : cuda_fail(err, "launch slicing");
