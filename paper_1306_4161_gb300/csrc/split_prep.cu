@@ -232,13 +232,13 @@ __global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restri
   }
 }
 
-// B slices, transposed: Bs[t][j][k].  A block covers 32 columns x 64 k: lane
-// l of warp w forms the digits of column j0 + l at k = k0 + 8 w .. + 7, so a
-// warp's loads are 32 consecutive doubles of each of 8 rows of B, and the
-// block's 8 warps together write 128 contiguous bytes (bf16) of every column
-// and slice.  One-dimensional grid, column blocks fastest (neighbouring blocks
-// read the same rows of B); any product whose slices fit in memory has fewer
-// than 2^31 blocks.
+// B slices, transposed: Bs[t][j][k].  A block covers 32 columns x 64 k; warp
+// w takes 16 columns (w & 1) and 16 k (w >> 1), and lanes 2i and 2i + 1 take
+// k .. k + 7 and k + 8 .. k + 15 of one column, so that a warp's store of a
+// slice fills 16 whole 32-byte sectors (bf16) and its loads read 16
+// consecutive doubles of each of 16 rows of B.  One-dimensional grid, column
+// blocks fastest (neighbouring blocks read the same rows of B); any product
+// whose slices fit in memory has fewer than 2^31 blocks.
 template <int KIND>
 __global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restrict__ B,
                                                           int64_t ldb, int64_t K, int64_t N,
@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restri
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t njb = (uint32_t)((N + 31) / 32);
   const uint32_t kb = blockIdx.x / njb, jb = blockIdx.x - kb * njb;
-  const int64_t j = (int64_t)jb * 32 + lane;
-  const int64_t k0 = (int64_t)kb * 64 + w * 8;
+  const int64_t j = (int64_t)jb * 32 + (w & 1) * 16 + (lane >> 1);
+  const int64_t k0 = (int64_t)kb * 64 + (w >> 1) * 16 + (lane & 1) * 8;
   if (j >= N) return;
   const int fj = f[j];
   double x[8];
