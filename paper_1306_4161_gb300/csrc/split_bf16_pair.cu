@@ -486,16 +486,28 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  // one launch per diagonal: the clusters resident together start each launch
-  // in step, and a tile's work is at most S slice pairs, so they drift apart
-  // less than within one launch of all S (S+1) / 2 pairs, and the L2 keeps
-  // serving the panels they share (a whole product in one launch read 2.4 x
-  // the DRAM bytes of its tile rounds at S = 5, a single round exactly those)
-  for (int d = 2; d <= S + 1; ++d) {
-    p.d_lo = p.d_hi = d;
+  // Long products run one launch per diagonal.  The hardware starts a cluster
+  // whenever one finishes, so over many rounds of tiles the clusters resident
+  // together drift apart, and with tiles of all S (S+1) / 2 slice pairs the L2
+  // stops serving the panels they share: at 16384^3, S = 5, one launch read
+  // 2.4 x the DRAM bytes of its tile rounds, one launch per diagonal 1.08 x
+  // (a single round reads exactly its bytes either way).  Each launch repeats a
+  // tile's fixed costs (tensor memory, barriers, pipeline fill, last drain),
+  // which short or few-round products cannot afford.  Measured (ms, one launch
+  // against one per diagonal): 1024 tiles x 15 x 16384 k: one launch faster by
+  // 1 %; 2048 and 2304 tiles: per diagonal by 0.5-1.5 %; 3072 tiles x 15 x 8192
+  // k: one launch by 1.3 %; 4096 tiles x 15 x 16384 k: per diagonal by 2-4 %.
+  // Rule: per diagonal from 24 rounds and 15 x 16384 k-columns of pairs a tile.
+  const int resident = state().sm_count / (2 * CN);
+  const bool per_diagonal = resident > 0 && ntiles >= 24 * resident &&
+                            (int64_t)(S * (S + 1) / 2) * Kpad >= 15 * 16384;
+  for (int d = 2; d <= S + 1;) {
+    p.d_lo = d;
+    p.d_hi = per_diagonal ? d : S + 1;
     e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tApf, tBpf, p);
     if (e != cudaSuccess) return cuda_fail(e, "launch bf16 pair kernel");
     count_launch();
+    d = p.d_hi + 1;
   }
   return HSUMMA_OK;
 }
