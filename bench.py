@@ -76,6 +76,23 @@ def measured_traffic(kernel="bf16_pair_kernel"):
         return None
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest x over all ranks (x itself without a process group): the
+    job's time is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(world: int, flops_per_rank: float, ms_max: float) -> float:
+    """Whole-job rate of `world` replicas that each did flops_per_rank in the
+    slowest rank's ms_max."""
+    return world * flops_per_rank / (ms_max * 1e-3) / 1e12
+
+
 def read_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -419,11 +436,8 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
     hs.sync()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * flops() / (ms * 1e-3) / 1e12
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_tflops(world, flops(), ms)
 
     # per-stage device time of the timed steps (events the library recorded
     # around each kernel on the launching stream while the steps ran)
