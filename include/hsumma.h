@@ -42,7 +42,7 @@ extern "C" {
 typedef enum {
   HSUMMA_OK = 0,
   HSUMMA_ERR_ARG = -1,          /* invalid argument (message says which) */
-  HSUMMA_ERR_UNSUPPORTED = -2,  /* valid but outside what this build handles */
+  HSUMMA_ERR_UNSUPPORTED = -2,  /* valid but outside what the library handles */
   HSUMMA_ERR_CUDA = -3,         /* a CUDA runtime call failed */
   HSUMMA_ERR_TIMEOUT = -4,      /* a device-side bounded wait ran out */
   HSUMMA_ERR_NOT_INIT = -5,     /* hsumma_init() has not been called */
@@ -257,7 +257,7 @@ int hsumma_mlp_load(const float *h_theta, const float *h_mean,
  * The paper picks the group count by timing a few runs (Section V-A-1,
  * Section VI) and fixes b and B by hand.  Here the candidates for a product
  * are enumerated by the library, scored by the loaded cost model, or timed one
- * by one (exhaustive search: the fallback, and the judge of the model). */
+ * by one (exhaustive search: the fallback, and the yardstick of the model). */
 
 /* Candidate configurations for a product: *count = their number (at most 72);
  * the first min(count, max) are written to cfg as (P, Q, G, b, Bouter)

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 The paper chooses the group count by sampling a few runs (Section V-A-1,
 Section VI); the learned model that proposes (P, Q, G, b, B) instead is a
-requirement of this build, not of the paper.  Parameter vector layout (also the
+requirement of the method as specified here, not of the paper.  Parameter vector layout (also the
 layout of the device kernels' weight buffer):
   W1[64][10], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[1][64], b4[1]
 (row-major, W[out][in]); y = W x + b per layer.

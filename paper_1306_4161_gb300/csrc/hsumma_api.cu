@@ -218,7 +218,7 @@ int hsumma_init(int device) {
   e = cudaGetDeviceProperties(&prop, device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
   if (prop.major != 10 || prop.minor != 3) {
-    set_error("device %d is sm_%d%d; this build targets sm_103a", device, prop.major,
+    set_error("device %d is sm_%d%d; the library is compiled for sm_103a", device, prop.major,
               prop.minor);
     return HSUMMA_ERR_UNSUPPORTED;
   }
