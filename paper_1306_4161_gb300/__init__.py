@@ -166,6 +166,8 @@ def finalize():
 
 def mode_code(kind: str | int, slices: int = 0, layout: str = "block") -> int:
     """The mode argument: kind in bits 0..7, slices in 8..15, the layout bit."""
+    if layout not in LAYOUTS:
+        raise ValueError(f"layout must be one of {sorted(LAYOUTS)} (got {layout!r})")
     k = KINDS[kind] if isinstance(kind, str) else int(kind)
     return k | (int(slices) << 8) | LAYOUTS[layout]
 

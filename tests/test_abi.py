@@ -75,6 +75,8 @@ def test_mode_encoding():
     assert hs.mode_code("bf16", 5) == 2 | (5 << 8)
     assert hs.mode_code("fp64") == 0
     assert hs.mode_code("int8", 6, "cyclic") == 1 | (6 << 8) | 0x10000
+    with pytest.raises(ValueError):
+        hs.mode_code("fp64", 0, "diagonal")
 
 
 def test_layout_bit_accepted_and_other_high_bits_rejected(lib):
