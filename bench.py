@@ -13,8 +13,12 @@ dominant kernel's duration for the roofline.  Prints one JSON line (rank 0).
 
 --impl reference times the CPU oracle (the plain binary64 triple loop) on a
 bounded sample of the same product (a band of rows of C) on the host cores.
-With N > 1 (torchrun) every rank runs the same problem on its own GPU
-(replicas: the single-GPU path does not shard) and value is the sum.
+
+The library is single-GPU: its cluster kernels deliver panels by TMA multicast
+inside a thread-block cluster, and no run of it spans two or more GPUs.  Under
+torchrun with WORLD_SIZE > 1 the native arm therefore launches nothing: rank 0
+prints one line with an "unavailable" reason and every rank exits 0.  The
+reference arm (CPU only) runs on rank 0 alone; the other ranks exit 0.
 """
 from __future__ import annotations
 
@@ -76,21 +80,14 @@ def measured_traffic(kernel="bf16_pair_kernel"):
         return None
 
 
-def max_over_ranks(x: float, dist, device: str) -> float:
-    """The largest x over all ranks (x itself without a process group): the
-    job's time is its slowest rank's."""
-    if dist is None:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+MULTI_GPU_UNAVAILABLE = ("single-GPU library: its cluster kernels deliver panels by TMA "
+                         "multicast, so no run of it spans two or more GPUs")
 
 
-def whole_job_tflops(world: int, flops_per_rank: float, ms_max: float) -> float:
-    """Whole-job rate of `world` replicas that each did flops_per_rank in the
-    slowest rank's ms_max."""
-    return world * flops_per_rank / (ms_max * 1e-3) / 1e12
+def multi_gpu_line(world: int):
+    """The native arm's line under torchrun with world > 1: nothing runs."""
+    return {"metric": METRIC, "impl": "native", "n_gpus": world,
+            "unavailable": MULTI_GPU_UNAVAILABLE}
 
 
 def read_peaks():
@@ -390,6 +387,11 @@ def main():
         if out is not None:
             print(json.dumps(out), flush=True)
         return
+    if world > 1:
+        # no kernel of this library runs on two or more GPUs (module docstring)
+        if rank == 0:
+            print(json.dumps(multi_gpu_line(world)), flush=True)
+        return
 
     import numpy as np
     import torch
@@ -397,10 +399,6 @@ def main():
     import workloads
 
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hs.init(local)
     n = N_SIZE
     dA = workloads.matrix_torch(n, n, 1002, "uniform", device="cuda")
@@ -409,9 +407,6 @@ def main():
     stream = torch.cuda.current_stream()
 
     def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
         torch.cuda.synchronize()
 
     def step():
@@ -436,8 +431,7 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
     hs.sync()
-    ms = max_over_ranks(ms, dist, "cuda")
-    value = whole_job_tflops(world, flops(), ms)
+    value = flops() / (ms * 1e-3) / 1e12
 
     # per-stage device time of the timed steps (events the library recorded
     # around each kernel on the launching stream while the steps ran)
@@ -476,7 +470,7 @@ def main():
             hs.gemm_host(hA, hB, hC, **SPLIT)
             calls.append(time.perf_counter() - t0)
         te = sum(calls) / reps
-        e2e = {"value": world * flops() / te / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": flops() / te / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
                "ms_per_step": te * 1e3, "calls_ms": [round(c * 1e3, 1) for c in calls]}
         # this box's pinned host-link rates (outside the timed region): the
@@ -539,26 +533,23 @@ def main():
         del dC2
 
     cpu, acc = None, {}
-    if rank == 0 and not args.no_cpu:
+    if not args.no_cpu:
         cpu, acc = cpu_leg(dA[:256].cpu().numpy(), dA[ir].cpu().numpy(), dB.cpu().numpy(),
                            ri, cj, sampled)
 
-    if rank == 0:
-        out = {
-            "metric": METRIC,
-            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (2 GiB each)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk,
-            "breakdown_ms": breakdown_ms, "native_fp64": native_out, "accuracy": acc,
-            "counters": counters,
-        }
-        print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    out = {
+        "metric": METRIC,
+        "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (2 GiB each)",
+                   "parallelism": "single GPU"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk,
+        "breakdown_ms": breakdown_ms, "native_fp64": native_out, "accuracy": acc,
+        "counters": counters,
+    }
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

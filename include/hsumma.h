@@ -95,7 +95,9 @@ typedef struct {
  * compute capability 10.3. */
 int hsumma_init(int device);
 
-/* Free everything the library allocated.  Safe to call twice. */
+/* Free everything the library allocated.  Safe to call twice.  Also drops the
+ * device addresses hsumma_mlp_backward_noalloc keeps (even without
+ * hsumma_init): call it after a cudaDeviceReset. */
 void hsumma_finalize(void);
 
 /* Group resolution (Section III: the s x t grid is arranged into I x J groups
@@ -207,7 +209,11 @@ int hsumma_mlp_forward(int batch, const float *d_theta, const float *d_X,
                        float *d_y, float *d_cache, void *stream);
 
 /* Gradient of mean_i (f(x_i) - t_i)^2 with respect to the parameters (fp32),
- * and the loss: d_grad 9089 floats, d_loss 1 float. */
+ * and the loss: d_grad 9089 floats, d_loss 1 float.  The per-block partial
+ * gradients live in a buffer of the call itself, taken from and returned to
+ * the current device's stream-ordered memory pool on `stream`
+ * (cudaMallocAsync / cudaFreeAsync), so calls on different devices, streams
+ * or host threads do not share it. */
 int hsumma_mlp_backward(int batch, const float *d_theta, const float *d_X,
                         const float *d_target, float *d_grad, float *d_loss,
                         void *stream);
@@ -218,17 +224,20 @@ int hsumma_mlp_backward(int batch, const float *d_theta, const float *d_X,
  * between requests while its memory is fully planned (or held by a caching
  * allocator), or one that cannot take the device-wide synchronisation that
  * cudaMalloc and cudaFree bring while other streams are busy.
- * hsumma_mlp_backward grows a buffer of per-block partial gradients with
- * cudaMalloc; this variant keeps them in one fixed array in the library's
- * device image (about 18.6 MB, held by every device that loads the library
- * until the process exits) and calls no cudaMalloc, cudaFree or allocating
- * routine.  Arguments, layout and results are those of hsumma_mlp_backward;
- * the caller passes every input and output.
+ * hsumma_mlp_backward takes a buffer of per-block partial gradients from the
+ * stream-ordered pool (cudaMallocAsync) on every call; this variant keeps them
+ * in one fixed array in the library's device image (about 18.6 MB, held by
+ * every device that loads the library until the process exits) and calls no
+ * cudaMalloc, cudaFree or allocating routine.  Arguments, layout and results
+ * are those of hsumma_mlp_backward; the caller passes every input and output.
  *   batch: 1..HSUMMA_MLP_NOALLOC_MAX_BATCH; a larger batch returns
  *          HSUMMA_ERR_ARG (message in hsumma_last_error) and launches nothing.
  * The first call on each device (with that device current) looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the array and it keeps the last call's
+ * array's device address (cudaGetSymbolAddress) and keeps it; make that first
+ * call before any stream capture.  A cudaDeviceReset invalidates the kept
+ * address: call hsumma_finalize after such a reset (it drops the kept
+ * addresses, whether or not hsumma_init was called) so that the next call
+ * looks them up again.  All calls share the array and it keeps the last call's
  * contents (nothing in it needs clearing, every slot read is written first in
  * the same call): calls that overlap on the GPU, on different streams or from
  * different host threads, race and give wrong gradients. */

@@ -74,20 +74,21 @@ def kept_pairs(S: int):
 
 
 def diagonal_products(Ad: np.ndarray, Bd: np.ndarray, S: int, w: int) -> dict:
-    """Step 3: D_d = sum_{s+t=d} A_s B_t as exact int64 matrices.
+    """Step 3: D_d = sum_{s+t=d} A_s B_t as exact int64 matrices, over the pairs
+    kept_pairs(S) gives (so the diagonals are d = 2..S+1).
 
     The float64 library matmul is exact here: every product of two digits is an
     integer of magnitude <= 2^(2w-2) and every partial sum of the (d-1) K terms
     stays below 2^53 (asserted), so no rounding happens in any order."""
     K = Ad.shape[2]
-    D = {}
-    for d in range(2, S + 2):
+    acc = {}
+    for s, t in kept_pairs(S):
+        d = s + t
         assert (d - 1) * K * 2 ** (2 * w - 2) < 2 ** 53, "exactness bound"
-        acc = np.zeros((Ad.shape[1], Bd.shape[2]), dtype=np.float64)
-        for s in range(1, d):
-            acc += Ad[s - 1] @ Bd[d - s - 1]
-        D[d] = acc.astype(np.int64)
-    return D
+        if d not in acc:
+            acc[d] = np.zeros((Ad.shape[1], Bd.shape[2]), dtype=np.float64)
+        acc[d] += Ad[s - 1] @ Bd[t - 1]
+    return {d: v.astype(np.int64) for d, v in acc.items()}
 
 
 def round_scaled(X: int, k: int) -> float:
@@ -107,7 +108,7 @@ def recombine(D: dict, e: np.ndarray, f: np.ndarray, S: int, w: int) -> np.ndarr
     """Step 4: C^_ij = RN(2^(e_i+f_j) sum_d D_d,ij 2^(-w d))."""
     M, N = e.size, f.size
     X = np.zeros((M, N), dtype=object)
-    for d in range(2, S + 2):
+    for d in sorted(D):
         X = X + (D[d].astype(object) * (1 << (w * (S + 1 - d))))
     C = np.empty((M, N), dtype=np.float64)
     base = -w * (S + 1)
@@ -154,16 +155,16 @@ def split_entries(A: np.ndarray, B: np.ndarray, rows, cols, S: int,
     K = Ar.shape[1]
     out = np.empty(rows.size, dtype=np.float64)
     base = -w * (S + 1)
-    for t in range(rows.size):
-        a, b = ir[t], ic[t]
-        X = 0
-        for d in range(2, S + 2):
+    pairs = kept_pairs(S)
+    for n in range(rows.size):
+        a, b = ir[n], ic[n]
+        Dd = {}
+        for s, t in pairs:
+            d = s + t
             assert (d - 1) * K * 2 ** (2 * w - 2) < 2 ** 53
-            Dd = 0.0
-            for s in range(1, d):
-                Dd += float(Ad[s - 1, a, :] @ Bd[d - s - 1, :, b])
-            X += int(Dd) << (w * (S + 1 - d))
-        out[t] = round_scaled(X, int(e[a]) + int(f[b]) + base)
+            Dd[d] = Dd.get(d, 0.0) + float(Ad[s - 1, a, :] @ Bd[t - 1, :, b])
+        X = sum(int(v) << (w * (S + 1 - d)) for d, v in Dd.items())
+        out[n] = round_scaled(X, int(e[a]) + int(f[b]) + base)
     return out
 
 

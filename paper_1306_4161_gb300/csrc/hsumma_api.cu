@@ -261,6 +261,7 @@ int hsumma_init(int device) {
 
 void hsumma_finalize(void) {
   std::lock_guard<std::mutex> lk(g_mu);
+  forget_noalloc_scratch();
   if (!g_init) return;
   cudaDeviceSynchronize();
   cudaFree(g_state.d_counters);

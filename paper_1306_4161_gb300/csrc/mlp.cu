@@ -336,9 +336,15 @@ constexpr int kNoAllocDevices = 64;
 static __device__ __align__(256) float g_noalloc_scratch[(size_t)kNoAllocBlocks * (NPARAM + 1)];
 
 // Device address of g_noalloc_scratch on each device (host-side, filled on the
-// first call made with that device current).
+// first call made with that device current; emptied by hsumma_finalize, since a
+// cudaDeviceReset in between leaves a stale address).
 static std::mutex g_noalloc_mutex;
 static float *g_noalloc_addr[kNoAllocDevices] = {};
+
+void forget_noalloc_scratch() {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  for (auto &p : g_noalloc_addr) p = nullptr;
+}
 
 }  // namespace hs
 
@@ -367,31 +373,27 @@ int hsumma_mlp_backward(int batch, const float *theta, const float *X, const flo
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int nb = grid_for(batch);
-  // partial gradients of every block, reduced in block order (deterministic)
-  static float *partial = nullptr;
-  static int partial_blocks = 0;
-  if (partial_blocks < nb) {
-    if (partial) {
-      cudaDeviceSynchronize();
-      cudaFree(partial);
-    }
-    cudaError_t e = cudaMalloc(&partial, (size_t)nb * (NPARAM + 1) * sizeof(float));
-    if (e != cudaSuccess) {
-      partial = nullptr;
-      partial_blocks = 0;
-      return cuda_fail(e, "cudaMalloc(mlp partials)");
-    }
-    partial_blocks = nb;
-  }
+  // partial gradients of every block, reduced in block order (deterministic),
+  // in a buffer of this call only, taken from and returned to the current
+  // device's stream-ordered pool on `s`: calls on different devices, streams or
+  // threads never share it, and growing it synchronises nothing
+  float *partial = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&partial),
+                                  (size_t)nb * (NPARAM + 1) * sizeof(float), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(mlp partials)");
   float *ploss = partial + (size_t)nb * NPARAM;
   const int smem = 2 * NPARAM * (int)sizeof(float);
-  cudaError_t e0 = cudaFuncSetAttribute(mlp_backward_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e0 != cudaSuccess) return cuda_fail(e0, "cudaFuncSetAttribute(mlp backward)");
-  mlp_backward_kernel<<<nb, WARPS * 32, smem, s>>>(batch, theta, X, target, partial, ploss);
-  mlp_reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(nb, batch, partial, ploss, grad, loss);
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? HSUMMA_OK : cuda_fail(e, "launch mlp backward");
+  e = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem);
+  if (e == cudaSuccess) {
+    mlp_backward_kernel<<<nb, WARPS * 32, smem, s>>>(batch, theta, X, target, partial, ploss);
+    mlp_reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(nb, batch, partial, ploss, grad,
+                                                           loss);
+    e = cudaGetLastError();
+  }
+  const cudaError_t ef = cudaFreeAsync(partial, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launch mlp backward");
+  return ef == cudaSuccess ? HSUMMA_OK : cuda_fail(ef, "cudaFreeAsync(mlp partials)");
 }
 
 // Same gradient and loss as hsumma_mlp_backward, with the block partials kept

@@ -144,3 +144,60 @@ def test_round_scaled_is_correctly_rounded():
 def test_metric_zero_denominator():
     assert split.max_rel_error(np.zeros(2), np.zeros(2), np.zeros(2)) == 0.0
     assert split.max_rel_error(np.array([1e-300]), np.zeros(1), np.zeros(1)) == float("inf")
+
+
+@pytest.mark.parametrize("S", [2, 3, 4, 5])
+def test_diagonal_products_form_exactly_the_triangle(S):
+    # one entry, K = 1, digits chosen so that every slice pair contributes its
+    # own power of two: a_s = 2^(s-1), b_t = 2^(S (t-1)), so a_s b_t = 2^(s-1+S(t-1))
+    # has a distinct exponent for each of the S^2 pairs and D_d, read in binary,
+    # names exactly the pairs summed into it.  A dropped or extra pair, a square
+    # pair set or a wrong diagonal changes the diagonals or their bits.
+    Ad = np.array([[[2.0 ** (s - 1)]] for s in range(1, S + 1)])      # S x 1 x 1
+    Bd = np.array([[[2.0 ** (S * (t - 1))]] for t in range(1, S + 1)])
+    D = split.diagonal_products(Ad, Bd, S, 8)
+    assert sorted(D) == list(range(2, S + 2))
+    for d, v in D.items():
+        bits = {(b % S + 1, b // S + 1) for b in range(S * S) if (int(v[0, 0]) >> b) & 1}
+        assert bits == {(s, d - s) for s in range(1, d)}, (d, bits)
+    assert sum(bin(int(v[0, 0])).count("1") for v in D.values()) == S * (S + 1) // 2
+
+
+def _exact_from_digits(A, B, S, kind, square=False):
+    """C^ from the digits of step 2 with exact rationals: the sum over the slice
+    pairs (all S^2 of them if `square`, else s + t <= S + 1) of
+    a_s[i,k] b_t[k,j] 2^(e_i + f_j - w (s + t)), rounded once (float(Fraction) is
+    correctly rounded, ties to even)."""
+    w = split.SLICE_BITS[kind]
+    e, f = split.row_exponents(A), split.col_exponents(B)
+    Ad, Bd = split.split_rows(A, e, S, w), split.split_cols(B, f, S, w)
+    M, K = A.shape
+    N = B.shape[1]
+    C = np.empty((M, N))
+    for i in range(M):
+        for j in range(N):
+            x = Fraction(0)
+            for s in range(1, S + 1):
+                for t in range(1, S + 1):
+                    if not square and s + t > S + 1:
+                        continue
+                    dot = sum(int(Ad[s - 1, i, k]) * int(Bd[t - 1, k, j]) for k in range(K))
+                    x += Fraction(dot) * Fraction(2) ** (int(e[i]) + int(f[j]) - w * (s + t))
+            C[i, j] = float(x)
+    return C
+
+
+@pytest.mark.parametrize("kind", ["int8", "bf16"])
+@pytest.mark.parametrize("S", [2, 3, 4])
+def test_split_gemm_is_the_rounded_exact_triangle_sum(kind, S):
+    # the whole split path against its definition: the exact sum of the kept
+    # slice-pair products (Ozaki et al.: pairs with s + t <= S + 1), rounded
+    # once; and the square pair set gives a different result on the same inputs,
+    # so a path that formed extra pairs would fail here
+    A = workloads.matrix(5, 6, 90 + S, "wide")
+    B = workloads.matrix(6, 4, 190 + S, "wide")
+    got = split.split_gemm(A, B, S, kind)
+    assert np.array_equal(got, _exact_from_digits(A, B, S, kind))
+    assert not np.array_equal(got, _exact_from_digits(A, B, S, kind, square=True))
+    rows, cols = np.array([0, 4, 2, 1]), np.array([3, 0, 1, 2])
+    assert np.array_equal(split.split_entries(A, B, rows, cols, S, kind), got[rows, cols])
