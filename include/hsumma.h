@@ -345,6 +345,27 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *d_A,
  * Results are identical either way. */
 int hsumma_pair_kernel(int enable);
 
+/* Launch policy of the CTA-pair kernel (hsumma_pair_kernel).  The low four
+ * bits choose how the slice pairs are split over launches:
+ *   HSUMMA_PAIR_LAUNCH_AUTO          the library's rule: one launch per
+ *                                    diagonal for long products of many
+ *                                    rounds of tiles, else one launch (the
+ *                                    setting after hsumma_init);
+ *   HSUMMA_PAIR_LAUNCH_ONE           one launch for all S (S + 1) / 2 pairs;
+ *   HSUMMA_PAIR_LAUNCH_PER_DIAGONAL  one launch per diagonal d = s + t;
+ * or-ing HSUMMA_PAIR_PERSISTENT launches one cluster per resident cluster
+ * slot of the device, each sweeping the group tiles cid, cid + ncl, ...,
+ * instead of one cluster per group tile.  A negative value only queries.
+ * Returns the previous policy, HSUMMA_ERR_ARG for an unknown one, or
+ * HSUMMA_ERR_NOT_INIT.  Results are identical under every policy. */
+enum {
+  HSUMMA_PAIR_LAUNCH_AUTO = 0,
+  HSUMMA_PAIR_LAUNCH_ONE = 1,
+  HSUMMA_PAIR_LAUNCH_PER_DIAGONAL = 2
+};
+#define HSUMMA_PAIR_PERSISTENT 0x10
+int hsumma_pair_launch(int policy);
+
 /* Self-test of the failure handling (the paper has no counterpart): launches
  * one block that waits on a shared-memory barrier nothing arrives on, gives up
  * after limit_ns (0 .. 1e9) of device time, and records HSUMMA_ERR_TIMEOUT in
@@ -366,6 +387,15 @@ int hsumma_selftest_timeout(long long limit_ns, void *stream);
  * unrecorded events and makes hsumma_stage_times fail. */
 int hsumma_stage_timing(int enable);
 int hsumma_stage_times(double *h_ms, int *h_calls);
+
+/* Timeline of the last hsumma_gemm_host call, when that call ran with stage
+ * timing on and was pipelined by row blocks (otherwise *h_count = 0): *h_count
+ * phases, in this order: the copy of B in, then for each row block r the copy
+ * of A_r in, the product of block r, the copy of C_r out.  For phase i,
+ * h_ms[2 i] and h_ms[2 i + 1] are its start and end in milliseconds after the
+ * call's first event (CUDA events on the stream that ran the phase); at most
+ * max values are written.  The pipeline has at most 4 row blocks (13 phases). */
+int hsumma_host_timeline(double *h_ms, int max, int *h_count);
 
 /* ---- Peak microbenchmarks (roofline denominators) ---- */
 

@@ -76,9 +76,11 @@ _SIGS = {
     "hsumma_mlp_pick": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hsumma_mlp_load": ([_vp, _vp, _vp], _i32),
     "hsumma_pair_kernel": ([_i32], _i32),
+    "hsumma_pair_launch": ([_i32], _i32),
     "hsumma_selftest_timeout": ([ctypes.c_longlong, _vp], _i32),
     "hsumma_stage_timing": ([_i32], _i32),
     "hsumma_stage_times": ([_vp, ctypes.POINTER(ctypes.c_int)], _i32),
+    "hsumma_host_timeline": ([_vp, _i32, ctypes.POINTER(ctypes.c_int)], _i32),
     "hsumma_candidates": ([_i64, _i64, _i64, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_int)],
                           _i32),
     "hsumma_features": ([_i64, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
@@ -390,6 +392,41 @@ def stage_times():
     n = ctypes.c_int()
     _check(lib().hsumma_stage_times(ms, ctypes.byref(n)))
     return list(ms), n.value
+
+
+HOST_PHASES = ("B in", "A in", "product", "C out")
+
+
+def host_timeline():
+    """Phases of the last gemm_host call made with stage timing on, when it was
+    pipelined by row blocks: a list of (name, block, start ms, end ms) relative
+    to the call's first event ([] otherwise)."""
+    ms = (ctypes.c_double * 32)()
+    n = ctypes.c_int()
+    _check(lib().hsumma_host_timeline(ms, 32, ctypes.byref(n)))
+    out = []
+    for i in range(n.value):
+        name = HOST_PHASES[0] if i == 0 else HOST_PHASES[1 + (i - 1) % 3]
+        block = -1 if i == 0 else (i - 1) // 3
+        out.append((name, block, ms[2 * i], ms[2 * i + 1]))
+    return out
+
+
+PAIR_LAUNCH = {"auto": 0, "one": 1, "per_diagonal": 2}
+PAIR_PERSISTENT = 0x10
+
+
+def pair_launch(split=None, persistent=False):
+    """Launch policy of the CTA-pair kernel: split in {"auto", "one",
+    "per_diagonal"} (None only queries), persistent clusters or not.  Returns
+    the previous policy as (split, persistent)."""
+    _ensure_init()
+    code = -1 if split is None else PAIR_LAUNCH[split] | (PAIR_PERSISTENT if persistent else 0)
+    r = lib().hsumma_pair_launch(code)
+    if r < 0:
+        _check(r)
+    names = {v: k for k, v in PAIR_LAUNCH.items()}
+    return names[r & 0xf], bool(r & PAIR_PERSISTENT)
 
 
 def pair_kernel(enable=None) -> bool:

@@ -111,6 +111,36 @@ bool encode_tmap_3d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
   return true;
 }
 
+bool encode_tmap_kpanels(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
+                         const void *base, uint64_t Kp, uint64_t rows, uint64_t planes,
+                         uint32_t box_rows, uint32_t kz) {
+  if (!g_encode) {
+    set_error("tensor-map encoder unavailable (hsumma_init not called?)");
+    return false;
+  }
+  const uint64_t panel = 128 / (uint64_t)elem_bytes;   // elements in 128 bytes
+  if (Kp % panel) {
+    set_error("k-panel view needs Kp a multiple of %llu", (unsigned long long)panel);
+    return false;
+  }
+  cuuint64_t dims[4] = {panel, rows, Kp / panel, planes};
+  cuuint64_t strides[3] = {Kp * (uint64_t)elem_bytes, 128, Kp * rows * (uint64_t)elem_bytes};
+  cuuint32_t box[4] = {(cuuint32_t)panel, box_rows, kz, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(out, dtype, 4, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (k panels) failed (%d): Kp %llu, rows %llu, planes %llu, "
+              "box %u x %u",
+              (int)r, (unsigned long long)Kp, (unsigned long long)rows,
+              (unsigned long long)planes, box_rows, kz);
+    return false;
+  }
+  return true;
+}
+
 static int launch_split_diagonals(const GridPlan &g, int kind, int S, const void *As,
                                   const void *Bs, int32_t *D, cudaStream_t s) {
   if (kind == HSUMMA_BF16_SLICES) {
@@ -271,6 +301,10 @@ void hsumma_finalize(void) {
   if (g_state.tune_buf) cudaFree(g_state.tune_buf);
   if (g_state.copy_in) cudaStreamDestroy(g_state.copy_in);
   if (g_state.copy_out) cudaStreamDestroy(g_state.copy_out);
+  for (auto &x : g_state.pipe_ev)
+    if (x) cudaEventDestroy(x);
+  for (auto &x : g_state.pipe_tev)
+    if (x) cudaEventDestroy(x);
   {
     std::lock_guard<std::mutex> lock(g_stage_mu);
     for (auto &ev : g_stage_ev)
@@ -525,12 +559,24 @@ int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
 // empty; 1 if no R in {4, 3, 2} fits.
 static int host_row_blocks(int64_t M, int P, int I, int64_t Mt) {
   for (int R : {4, 3, 2}) {
-    if (P % R || I % R) continue;
+    if (R > kMaxHostBlocks || P % R || I % R) continue;
     const int64_t rows = (int64_t)(P / R) * Mt;
     if (rows < 512 || (R - 1) * rows >= M) continue;
     return R;
   }
   return 1;
+}
+
+// The pipeline's events, created on first use and kept until hsumma_finalize:
+// ordering events always, timing events when `timed`.
+static cudaError_t pipeline_events(bool timed) {
+  cudaError_t e = cudaSuccess;
+  for (auto &x : g_state.pipe_ev)
+    if (!x && e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  if (timed)
+    for (auto &x : g_state.pipe_tev)
+      if (!x && e == cudaSuccess) e = cudaEventCreate(&x);
+  return e;
 }
 
 // hsumma_gemm_host pipelined by row blocks: C_r = A_r B for the R row blocks
@@ -540,6 +586,8 @@ static int host_row_blocks(int64_t M, int P, int I, int64_t Mt) {
 // is copied back on the copy-out stream while the next block computes.  Every
 // element is computed as in the unblocked product (row exponents are per row,
 // column exponents over the whole of B), so the result is the same bit for bit.
+// With stage timing on, timing events bracket every phase (the timeline of
+// hsumma_host_timeline).
 static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA, int64_t lda,
                                const double *hB, int64_t ldb, double *hC, int64_t ldc,
                                const GridPlan &full, int R, int kind, int S, double *dA,
@@ -549,43 +597,45 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   if (e == cudaSuccess && !g_state.copy_out)
     e = cudaStreamCreateWithFlags(&g_state.copy_out, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate(copy streams)");
+  bool timed;
+  {
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    timed = g_stage_on;
+  }
+  e = pipeline_events(timed);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate(pipeline)");
   cudaStream_t ci = g_state.copy_in, co = g_state.copy_out;
   const int64_t rows = (int64_t)(full.P / R) * full.Mt;
-  // events: B copied, A block r copied, C block r computed, all copied back
-  std::vector<cudaEvent_t> ev(2 * R + 2, nullptr);
-  for (auto &x : ev)
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-  auto cleanup = [&]() {
-    for (auto &x : ev)
-      if (x) cudaEventDestroy(x);
+  // ordering events: [0] the caller's earlier work, [1] B copied, [2 + r] A
+  // block r copied, [2 + R + r] C block r computed, [2 + 2 R] all copied back
+  cudaEvent_t *ev = g_state.pipe_ev;
+  cudaEvent_t evPrior = ev[0], evB = ev[1], evDone = ev[2 + 2 * R];
+  // timing events: [0] start, then (start, end) of phase i at [1 + 2 i], [2 + 2 i]
+  cudaEvent_t *tev = g_state.pipe_tev;
+  auto mark = [&](int phase, int end, cudaStream_t st) {
+    return timed ? cudaEventRecord(tev[1 + 2 * phase + end], st) : cudaSuccess;
   };
-  if (e != cudaSuccess) {
-    cleanup();
-    return cuda_fail(e, "cudaEventCreate(pipeline)");
-  }
-  cudaEvent_t evB = ev[0], evDone = ev[2 * R + 1];
-  auto fail = [&](cudaError_t err, const char *what) {
-    cleanup();
-    return cuda_fail(err, what);
-  };
-  auto fail_st = [&](int st) {
-    cleanup();
-    return st;
-  };
+  auto fail = [&](cudaError_t err, const char *what) { return cuda_fail(err, what); };
 
   e = cudaMemsetAsync(g_state.d_counters, 0, 8 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return fail(e, "cudaMemsetAsync(counters)");
+  if (timed) e = cudaEventRecord(tev[0], s);
   // copies in: B, then A block by block
-  e = cudaEventRecord(ev[1], s);  // the caller's earlier work on s comes first
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, ev[1], 0);
+  if (e == cudaSuccess) e = cudaEventRecord(evPrior, s);  // the caller's earlier work first
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, evPrior, 0);
+  if (e == cudaSuccess) e = mark(0, 0, ci);
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(dB, ldb * 8, hB, ldb * 8, N * 8, K, cudaMemcpyHostToDevice, ci);
+  if (e == cudaSuccess) e = mark(0, 1, ci);
   if (e == cudaSuccess) e = cudaEventRecord(evB, ci);
   for (int r = 0; r < R && e == cudaSuccess; ++r) {
     const int64_t r0 = r * rows, mr = (M - r0) < rows ? (M - r0) : rows;
-    e = cudaMemcpy2DAsync(dA + r0 * lda, lda * 8, hA + r0 * lda, lda * 8, K * 8, mr,
-                          cudaMemcpyHostToDevice, ci);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + r], ci);
+    e = mark(1 + 3 * r, 0, ci);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(dA + r0 * lda, lda * 8, hA + r0 * lda, lda * 8, K * 8, mr,
+                            cudaMemcpyHostToDevice, ci);
+    if (e == cudaSuccess) e = mark(1 + 3 * r, 1, ci);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + r], ci);
   }
   if (e != cudaSuccess) return fail(e, "copy operands in");
 
@@ -597,7 +647,7 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(B)");
   if (kind != HSUMMA_FP64) {
     st = ensure_workspace(split_ws_bytes(rows, N, K, kind, S));
-    if (st != HSUMMA_OK) return fail_st(st);
+    if (st != HSUMMA_OK) return st;
     const int64_t Kp = ceil_div(K, 64) * 64;
     const size_t eb = kind == HSUMMA_INT8_SLICES ? 1 : 2;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -615,15 +665,16 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
     if (st == HSUMMA_OK)
       st = launch_split_slices(0, N, K, nullptr, 1, dB, ldb, nullptr, f_cols, kind, S, nullptr,
                                Bs, s);
-    if (st != HSUMMA_OK) return fail_st(st);
+    if (st != HSUMMA_OK) return st;
   }
   for (int r = 0; r < R; ++r) {
     const int64_t r0 = r * rows, mr = (M - r0) < rows ? (M - r0) : rows;
     GridPlan g;
     st = make_plan(mr, N, K, full.P / R, full.Q, full.G / R, full.b, full.Bo, kind, full.cyc,
                    &g);
-    if (st != HSUMMA_OK) return fail_st(st);
-    e = cudaStreamWaitEvent(s, ev[1 + r], 0);
+    if (st != HSUMMA_OK) return st;
+    e = cudaStreamWaitEvent(s, ev[2 + r], 0);
+    if (e == cudaSuccess) e = mark(2 + 3 * r, 0, s);
     if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(A block)");
     const double *Ar = dA + r0 * lda;
     double *Cr = dC + r0 * ldc;
@@ -638,20 +689,27 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
       if (st == HSUMMA_OK)
         st = launch_split_recombine(mr, N, K, kind, S, D, e_rows, f_cols, Cr, ldc, s);
     }
-    if (st != HSUMMA_OK) return fail_st(st);
-    cudaEvent_t done = ev[1 + R + r];
-    e = cudaEventRecord(done, s);
+    if (st != HSUMMA_OK) return st;
+    cudaEvent_t done = ev[2 + R + r];
+    e = mark(2 + 3 * r, 1, s);
+    if (e == cudaSuccess) e = cudaEventRecord(done, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(co, done, 0);
+    if (e == cudaSuccess) e = mark(3 + 3 * r, 0, co);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(hC + r0 * ldc, ldc * 8, Cr, ldc * 8, N * 8, mr,
                             cudaMemcpyDeviceToHost, co);
+    if (e == cudaSuccess) e = mark(3 + 3 * r, 1, co);
     if (e != cudaSuccess) return fail(e, "copy a block of C out");
   }
   e = cudaEventRecord(evDone, co);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, evDone, 0);
   if (e != cudaSuccess) return fail(e, "join copy streams");
-  cleanup();  // destroying recorded events is safe: they are released once complete
-  return hsumma_sync(reinterpret_cast<void *>(s));
+  st = hsumma_sync(reinterpret_cast<void *>(s));
+  if (timed) {
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    g_state.timeline_phases = st == HSUMMA_OK ? 1 + 3 * R : 0;
+  }
+  return st;
 }
 
 int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t lda,
@@ -660,6 +718,10 @@ int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t 
   if (!g_init) {
     set_error("hsumma_init has not been called");
     return HSUMMA_ERR_NOT_INIT;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    g_state.timeline_phases = 0;   // set again by a timed pipelined call
   }
   int st = check_matrix_args(M, N, K, hA, lda, hB, ldb, hC, ldc);
   if (st != HSUMMA_OK) return st;
@@ -906,6 +968,47 @@ int hsumma_stage_times(double *ms, int *calls) {
   }
   *calls = (int)g_stage_used;
   return HSUMMA_OK;
+}
+
+int hsumma_host_timeline(double *ms, int max, int *count) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  if (!count || (max > 0 && !ms)) {
+    set_error("null output pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  const int n = g_state.timeline_phases;
+  *count = n;
+  for (int i = 0; i < n && 2 * i + 1 < max; ++i) {
+    for (int k = 0; k < 2; ++k) {
+      float t = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&t, g_state.pipe_tev[0],
+                                           g_state.pipe_tev[1 + 2 * i + k]);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime(timeline)");
+      ms[2 * i + k] = t;
+    }
+  }
+  return HSUMMA_OK;
+}
+
+int hsumma_pair_launch(int policy) {
+  if (!g_init) {
+    set_error("hsumma_init has not been called");
+    return HSUMMA_ERR_NOT_INIT;
+  }
+  const int was = g_state.pair_launch;
+  if (policy >= 0) {
+    const int split = policy & 0xf;
+    if ((policy & ~(0xf | HSUMMA_PAIR_PERSISTENT)) || split > HSUMMA_PAIR_LAUNCH_PER_DIAGONAL) {
+      set_error("unknown pair launch policy %#x", policy);
+      return HSUMMA_ERR_ARG;
+    }
+    g_state.pair_launch = policy;
+  }
+  return was;
 }
 
 int hsumma_pair_kernel(int enable) {

@@ -21,6 +21,12 @@ struct GridPlan {
                          // block-checkerboard (one block per processor)
 };
 
+// Row blocks of the pipelined host-buffer product (at most), and the timing
+// events of its timeline: a start event, then a start and an end for each of
+// the 1 + 3 R phases (B in; per block: A_r in, compute, C_r out).
+constexpr int kMaxHostBlocks = 4;
+constexpr int kHostTimelineEvents = 1 + 2 * (1 + 3 * kMaxHostBlocks);
+
 struct DeviceState {
   int device = -1;
   int sm_count = 0;
@@ -32,10 +38,17 @@ struct DeviceState {
   void *host_staging = nullptr;              // device buffers of hsumma_gemm_host
   size_t host_staging_bytes = 0;
   bool bf16_pair = false;                    // bf16 products of 2 x 1 groups on CTA pairs
+  int pair_launch = 0;                       // launch policy of the pair kernel (HSUMMA_PAIR_*)
+  int pair_resident[3] = {0, 0, 0};          // resident clusters of CN pairs (0: not queried)
   void *tune_buf = nullptr;                  // model scoring inputs of hsumma_choose
   size_t tune_bytes = 0;
   cudaStream_t copy_in = nullptr;            // hsumma_gemm_host's copy streams
   cudaStream_t copy_out = nullptr;
+  // hsumma_gemm_host's pipeline events, created once: ordering events (no
+  // timing) and, when stage timing is on, timing events around every phase
+  cudaEvent_t pipe_ev[kMaxHostBlocks * 2 + 3] = {};
+  cudaEvent_t pipe_tev[kHostTimelineEvents] = {};
+  int timeline_phases = 0;                   // phases the last timed call recorded
 };
 
 DeviceState &state();
@@ -55,6 +68,14 @@ bool encode_tmap_3d(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
                     const void *base, uint64_t inner, uint64_t rows, uint64_t planes,
                     uint32_t box_inner, uint32_t box_rows, CUtensorMapSwizzle swizzle);
 
+// k-panel view of a slice tensor (S x rows x Kp, row-major, Kp a multiple of
+// 64): 4-D {64, rows, Kp / 64, S} with strides {Kp, 64, rows Kp} elements, so
+// that one box {64, box_rows, kz, 1} copies kz consecutive 64-column panels of
+// box_rows rows at once (128-byte swizzle, 2-byte elements).
+bool encode_tmap_kpanels(CUtensorMap *out, CUtensorMapDataType dtype, int elem_bytes,
+                         const void *base, uint64_t Kp, uint64_t rows, uint64_t planes,
+                         uint32_t box_rows, uint32_t kz);
+
 // Launchers (return an hsumma_status).
 int launch_fp64_hsumma(const GridPlan &g, const double *A, int64_t lda, const double *B,
                        int64_t ldb, double *C, int64_t ldc, cudaStream_t s);
@@ -70,11 +91,16 @@ int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
 // Exact diagonal sums are stored as int32 planes D[d-2][seg][M][N]: a diagonal's
 // sum over its (d-1) K products is cut into segments whose partial sums stay
 // below 2^31 (bf16: 127 chunks of 1024 products of magnitude <= 2^14; int8:
-// 2^17 products of magnitude <= 2^12 per segment).
+// 2^18 products of magnitude <= 2^12 per segment).  The product kernels step
+// through k in stages of at most 128 columns, a pair's last stage padded to
+// 128, so the longest diagonal (S pairs) spans S ceil(Kp / 128) 128-column
+// stages; the plane count covers that many, and every kernel writes every
+// plane of every diagonal (zeros past the diagonal's own segments).
 constexpr int kSegChunks = 127;
 inline int split_planes(int64_t K, int S, int kind = 2) {
   const int64_t Kp = (K + 63) / 64 * 64;
-  const int64_t prods = (int64_t)S * Kp;     // longest diagonal: S pairs
+  const int64_t K128 = (Kp + 127) / 128 * 128;
+  const int64_t prods = (int64_t)S * K128;   // longest diagonal: S pairs
   const int64_t per_seg = kind == 1 ? (int64_t)1 << 18 : (int64_t)kSegChunks * 1024;
   const int64_t n = (prods + per_seg - 1) / per_seg;
   return n < 1 ? 1 : (int)n;

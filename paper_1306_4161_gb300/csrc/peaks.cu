@@ -97,114 +97,111 @@ __global__ void __launch_bounds__(256) peak_hmma_kernel(int64_t iters, float *si
   if (s == 1234.5f) sink[0] = s;
 }
 
-// One CTA per SM; one thread issues 128 x 256 x 16 bf16 MMAs from a 48 KB
-// shared-memory operand pair into two alternating tensor-memory accumulators.
-constexpr int TC_SMEM = 48 * 1024 + 1024 + 64 + 64 * 1024;  // padding keeps 1 CTA per SM
+// tcgen05 rate: one CTA per SM (its shared memory is more than half an SM's,
+// so no second CTA can share the SM and its tensor memory), one thread issuing
+// bf16 MMAs of the product kernels' shapes back to back: 128 x 256 x 16 on one
+// SM, or 256 x 256 x 16 spanning a CTA pair.  The operands are small integers
+// in [-128, 127] (the slice digits' form, exact in bf16), not zeros, since the
+// rate under the power limit depends on the data.  Commits go out every 64
+// MMAs and the issuer waits only for the group before, so the tensor pipe never
+// drains between groups.  A single issuing thread reaches the full rate (one
+// MMA per 128 cycles for both shapes), so this is also the product kernels'
+// issue structure.
+constexpr int TC_SMEM = 120 * 1024 + 1024 + 256;   // > half of an SM's 228 KB
+constexpr int TC_GROUP = 64;                       // MMAs per commit
+
+template <bool PAIR>
 __global__ void __launch_bounds__(128, 1) peak_tc05_kernel(int64_t iters, int *status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 48 * 1024);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 48 * 1024);   // 2 barriers
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
   const int warp = threadIdx.x >> 5;
-  // defined operand values (zeros): the rate does not depend on them
-  for (int i = threadIdx.x; i < 48 * 1024 / 16; i += blockDim.x)
-    reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  // operands: A (16 KB, 128 rows of 64 bf16) and B (32 KB) of small integers
+  for (int i = threadIdx.x; i < 48 * 1024 / 4; i += blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u + 12345u * (rank + 1);
+    h ^= h >> 13;
+    h *= 0x5bd1e995u;
+    h ^= h >> 15;
+    const float lo = (float)((int)(h & 0xffu) - 128), hi = (float)((int)((h >> 8) & 0xffu) - 128);
+    reinterpret_cast<uint32_t *>(smem)[i] = (__float_as_uint(lo) >> 16) |
+                                           (__float_as_uint(hi) & 0xffff0000u);
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (threadIdx.x == 0) {
-    mbar_init(smem_u32(bar), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    tmem_alloc(smem_u32(slot), 512);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tbase = *slot;
-  if (threadIdx.x == 0) {
-    const uint32_t a = smem_u32(smem), b = a + 16 * 1024;
-    const uint32_t idesc = idesc_bf16_f32(128, 256);
-    uint32_t phase = 0;
-    for (int64_t it = 0; it < iters; ++it) {
-      const uint32_t k = (uint32_t)(it & 3);
-      mma_bf16(tbase + (uint32_t)((it >> 2) & 1) * 256, sdesc_k128(a + k * 32),
-               sdesc_k128(b + k * 32), idesc, k ? 1u : 0u);
-      if ((it & 255) == 255 || it == iters - 1) {
-        mma_commit(smem_u32(bar));
-        if (!mbar_wait(smem_u32(bar), phase)) {
-          record_error(status, HSUMMA_ERR_TIMEOUT, kSiteAccFull);
-          break;
-        }
-        phase ^= 1u;
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tmem_dealloc(tbase, 512);
-  }
-}
-
-// CTA pairs (clusters of 2, one CTA per SM): the first CTA of each pair issues
-// 256 x 256 x 16 bf16 MMAs spanning both SMs; the second waits for the
-// commits so that both stay resident until the last MMA completes.
-__global__ void __launch_bounds__(128, 1) peak_tc05_pair_kernel(int64_t iters, int *status) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 48 * 1024);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
-  const int warp = threadIdx.x >> 5;
-  const uint32_t rank = cluster_ctarank();
-  for (int i = threadIdx.x; i < 48 * 1024 / 16; i += blockDim.x)
-    reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (threadIdx.x == 0) {
-    mbar_init(smem_u32(bar), 1);
+    mbar_init(smem_u32(&bar[0]), 1);
+    mbar_init(smem_u32(&bar[1]), 1);
     fence_mbar_init();
   }
   if (warp == 0) {
-    tmem_alloc2(smem_u32(slot), 512);
-    tmem_relinquish2();
+    if (PAIR) {
+      tmem_alloc2(smem_u32(slot), 512);
+      tmem_relinquish2();
+    } else {
+      tmem_alloc(smem_u32(slot), 512);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *slot;
-  cluster_sync();
-  if (threadIdx.x == 0) {
+  if (PAIR) cluster_sync();
+  if (threadIdx.x == 0 && (rank & 1u) == 0) {
     const uint32_t a = smem_u32(smem), b = a + 16 * 1024;
-    const uint32_t idesc = idesc_bf16_f32(256, 256);
-    uint32_t phase = 0;
-    for (int64_t it = 0; it < iters; ++it) {
-      const bool commit = (it & 255) == 255 || it == iters - 1;
-      if ((rank & 1) == 0) {
-        const uint32_t k = (uint32_t)(it & 3);
-        mma2_bf16(tbase + (uint32_t)((it >> 2) & 1) * 256, sdesc_k128(a + k * 32),
-                  sdesc_k128(b + k * 32), idesc, k ? 1u : 0u);
-        if (commit) mma2_commit_mc(smem_u32(bar), (uint16_t)3u);
+    const uint32_t idesc = idesc_bf16_f32(PAIR ? 256 : 128, 256);
+    uint64_t ad[4], bd[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ad[k] = sdesc_k128(a + k * 32);
+      bd[k] = sdesc_k128(b + k * 32);
+    }
+    uint32_t ph[2] = {0u, 0u};
+    int64_t grp = 0;
+    bool ok = true;
+    for (int64_t it = 0; it < iters && ok; it += 4) {
+      // four k-steps into accumulator 0 or 1 (alternating every four)
+      const uint32_t acc = tbase + (uint32_t)((it >> 2) & 1) * 256u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (PAIR)
+          mma2_bf16(acc, ad[k], bd[k], idesc, k ? 1u : 0u);
+        else
+          mma_bf16(acc, ad[k], bd[k], idesc, k ? 1u : 0u);
       }
-      if (commit) {
-        if (!mbar_wait(smem_u32(bar), phase)) {
-          record_error(status, HSUMMA_ERR_TIMEOUT, kSiteAccFull);
-          break;
+      if ((it + 4) % TC_GROUP == 0 || it + 4 >= iters) {
+        const uint32_t bb = smem_u32(&bar[grp & 1]);
+        if (PAIR)
+          mma2_commit_mc(bb, (uint16_t)1u);
+        else
+          mma_commit(bb);
+        if (grp >= 1) {   // the group before this one
+          const int pb = (int)((grp - 1) & 1);
+          ok = mbar_wait(smem_u32(&bar[pb]), ph[pb]);
+          ph[pb] ^= 1u;
         }
-        phase ^= 1u;
+        ++grp;
       }
     }
+    if (ok && grp >= 1) {
+      const int pb = (int)((grp - 1) & 1);
+      ok = mbar_wait(smem_u32(&bar[pb]), ph[pb]);
+    }
+    if (!ok) record_error(status, HSUMMA_ERR_TIMEOUT, kSiteAccFull);
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync();
+  if (PAIR) cluster_sync();   // the pair's MMAs are complete before either CTA frees
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc2(tbase, 512);
+    if (PAIR)
+      tmem_dealloc2(tbase, 512);
+    else
+      tmem_dealloc(tbase, 512);
   }
-  cluster_sync();
+  if (PAIR) cluster_sync();
 }
 
 __global__ void copy_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst, int64_t n) {
@@ -244,10 +241,12 @@ int run_peak(int kind, int64_t work, double *rate) {
         peak_hmma_kernel<<<sms * 8, 256>>>(iters, (float *)sink);
         work_units = 2.0 * 16 * 8 * 16 * 4 * iters * sms * 8 * 8;
         break;
-      case HSUMMA_PEAK_TC05_BF16:
-        peak_tc05_kernel<<<sms, 128, TC_SMEM>>>(iters, state().d_status);
-        work_units = 2.0 * 128 * 256 * 16 * (double)iters * sms;
+      case HSUMMA_PEAK_TC05_BF16: {
+        const int64_t it4 = iters < 4 ? 4 : (iters & ~int64_t(3));   // whole k-blocks
+        peak_tc05_kernel<false><<<sms, 128, TC_SMEM>>>(it4, state().d_status);
+        work_units = 2.0 * 128 * 256 * 16 * (double)it4 * sms;
         break;
+      }
       case HSUMMA_PEAK_TC05_BF16_PAIR: {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(sms & ~1), 1, 1);
@@ -260,8 +259,9 @@ int run_peak(int kind, int64_t work, double *rate) {
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, peak_tc05_pair_kernel, iters, state().d_status);
-        work_units = 2.0 * 256 * 256 * 16 * (double)iters * (sms / 2);
+        const int64_t it4 = iters < 4 ? 4 : (iters & ~int64_t(3));
+        cudaLaunchKernelEx(&cfg, peak_tc05_kernel<true>, it4, state().d_status);
+        work_units = 2.0 * 256 * 256 * 16 * (double)it4 * (sms / 2);
         break;
       }
       case HSUMMA_PEAK_COPY:
@@ -276,13 +276,13 @@ int run_peak(int kind, int64_t work, double *rate) {
     st = HSUMMA_ERR_ARG;
   }
   if (st == HSUMMA_OK && kind == HSUMMA_PEAK_TC05_BF16) {
-    e = cudaFuncSetAttribute(peak_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TC_SMEM);
+    e = cudaFuncSetAttribute(peak_tc05_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaFuncSetAttribute");
   }
   if (st == HSUMMA_OK && kind == HSUMMA_PEAK_TC05_BF16_PAIR) {
-    e = cudaFuncSetAttribute(peak_tc05_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TC_SMEM);
+    e = cudaFuncSetAttribute(peak_tc05_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaFuncSetAttribute");
   }
   if (st == HSUMMA_OK && kind == HSUMMA_PEAK_COPY) {

@@ -369,11 +369,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
           for (int d = 2; d <= S + 1 && ok; ++d) {
             const int nst = (d - 1) * nkb;
-            for (int seg = 0; seg * SEGST < nst && ok; ++seg) {
-              const int seg_len = min(nst, (seg + 1) * SEGST) - seg * SEGST;
+            const int nseg_d = (nst + SEGST - 1) / SEGST;
+            for (int seg = 0; seg < p.nseg && ok; ++seg) {
+              const int seg_len = seg < nseg_d ? min(nst, (seg + 1) * SEGST) - seg * SEGST : 0;
               int acc[128];
 #pragma unroll
               for (int i = 0; i < 128; ++i) acc[i] = 0;
+              // a plane past this diagonal's segments is written as zeros: the
+              // recombination adds every plane of every diagonal
               for (int local = 0; local < seg_len; ++local) {
                 if (!chunk_end(local, seg_len)) continue;
                 const int who = local & 1;

@@ -17,12 +17,15 @@
 // Synchronisation (no forwarding step): the first CTA of the pair ("leader")
 // expects the bytes of both CTAs on its own "full" barrier, and the second
 // CTA's copies count their bytes on that barrier directly (cta_group::2 bulk
-// tensor copies).  Two issuing threads of the leader take the k-stages of
-// parity 0 and 1 into separate accumulators (tensor-memory columns 0..255 and
-// 256..511 of both SMs), with the staggered chunk ends of split_bf16.cu; each
-// stage's MMA completion releases the stage in both CTAs, and each chunk end
-// hands the accumulator to the drain warps of both CTAs, which return it to
-// the leader.  Every wait is bounded (4 s) and ends in an error status.
+// tensor copies).  One issuing thread of the leader runs every MMA: a single
+// thread sustains the full tensor rate (one 256 x 256 x 16 pair MMA per 128
+// cycles), so the two accumulators (tensor-memory columns 0..255 and 256..511
+// of both SMs) are used in turn, a chunk of at most 16 k-stages (1024
+// products, the bound of exact fp32 sums) in each: while the drain warps of
+// both CTAs empty one accumulator, the MMAs fill the other.  Each stage's MMA
+// completion releases the stage in both CTAs, each chunk end hands the
+// accumulator to the drain warps, and they return it to the leader.  Every
+// wait is bounded (4 s) and ends in an error status.
 //
 // 2 x 2 groups: the two CTAs of a processor row each load one half (64 rows)
 // of the row's A tile and multicast it to both (cta_group::2 copies that count
@@ -30,9 +33,11 @@
 // four CTAs once both pairs' MMAs have read it (the commits of both leaders,
 // multicast to the cluster).
 //
-// Roles (384 threads per CTA): warp 0 issues the copies, warps 1 and 2 issue
-// the MMAs (leader only; warp 1 of each CTA owns its tensor memory), warp 3
-// idles, warps 4..11 drain their CTA's 128 rows into exact int32 planes.
+// Roles (320 threads per CTA): warp 0 issues the copies, warp 1 issues the MMAs
+// (leader only) and owns its CTA's tensor memory, warps 2..9 drain their CTA's
+// 128 rows into exact int32 planes (a warp reads the tensor-memory lanes of
+// its own quarter, warp mod 4, so warps 2..5 and 6..9 each cover all 128 rows,
+// for the two column halves).
 #include "internal.h"
 #include "ptx.cuh"
 #include "tc05.cuh"
@@ -41,12 +46,17 @@
 namespace hs {
 namespace {
 
-constexpr int TM = 128, TN = 256, HN = TN / 2, BKS = 64, STAGES = 6;
-constexpr int A_BYTES = TM * BKS * 2, BH_BYTES = HN * BKS * 2;
+constexpr int TM = 128, TN = 256, HN = TN / 2;
+constexpr int PK = 64;                 // k-columns of a panel (128 bytes of bf16)
+constexpr int KZ = 2;                  // panels per stage: one copy brings both
+constexpr int BKS = PK * KZ;           // k-columns per stage
+constexpr int STAGES = 3;
+constexpr int A_PANEL = TM * PK * 2, B_PANEL = HN * PK * 2;   // 16 KB each
+constexpr int A_BYTES = KZ * A_PANEL, BH_BYTES = KZ * B_PANEL;
 constexpr int STAGE_BYTES = A_BYTES + BH_BYTES;
-constexpr int CH = 16;                 // k-stages per accumulator chunk (1024 products)
+constexpr int CH = 8;                  // stages per accumulator chunk (1024 products)
 constexpr int NEPI = 8;                // draining warps per CTA
-constexpr int NTHREADS = (4 + NEPI) * 32;
+constexpr int NTHREADS = (2 + NEPI) * 32;   // copy warp, MMA warp, drain warps
 constexpr int SEGST = 127 * CH;        // stages per int32 segment
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
@@ -76,12 +86,10 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
   }
 }
 
-// the chunk schedule of split_bf16.cu: issuer 0 closes a chunk every 16 of its
-// stages, issuer 1 after 8 and then every 16; both at the segment's last stage
+// a chunk closes after every CH stages of a segment and at its last stage;
+// chunk n of the launch uses accumulator n mod 2
 __device__ __forceinline__ bool chunk_end(int local, int seg_len) {
-  const int c = (local >> 1) + 1;
-  if (local + 2 >= seg_len) return true;
-  return (local & 1) ? ((c + 8) % CH == 0) : (c % CH == 0);
+  return (local + 1) % CH == 0 || local + 1 == seg_len;
 }
 
 // group tile L -> processor row r and column c of the CTA that is member `ry`
@@ -178,15 +186,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
-                int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
+                int rem = 0;   // panel start mod B, kept without a 64-bit division
                 for (int kb = 0; kb < nkb; ++kb) {
                   const int64_t k0 = (int64_t)kb * BKS;
-                  const bool outer = rem == 0;
-                  for (rem += BKS; rem >= p.Bo;) rem -= p.Bo;
-                  if (outer) {
+                  // outer steps fall on panel starts (B is a multiple of 64)
+                  for (int h = 0; h < KZ; ++h) {
+                    const int64_t kh = k0 + (int64_t)h * PK;
+                    if (kh >= p.Kpad) break;
+                    const bool outer = rem == 0;
+                    for (rem += PK; rem >= p.Bo;) rem -= p.Bo;
+                    if (!outer) continue;
                     // owners stage the next outer panel into L2, one outer block
                     // ahead without gaps (the rule of split_bf16.cu)
-                    const int64_t o = k0 / p.Bo;
+                    const int64_t o = kh / p.Bo;
                     int ns = s + 1, nd = d;
                     if (ns >= nd) { ++nd; ns = 1; }
                     const bool first = (d == p.d_lo && s == 1 && o == 0);
@@ -201,12 +213,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                       }
                       const int64_t kq = q * p.Bo, kend = imin64(p.Kpad, kq + p.Bo);
                       if (c == outer_owner(cyc, q, kq, p.Kq, p.Q)) {
-                        for (int64_t kk = kq; kk < kend; kk += BKS)
+                        for (int64_t kk = kq; kk < kend; kk += PK)
                           tma_prefetch_3d(&tmApf, (int32_t)kk, (int32_t)m0, ps - 1);
                         pf += 1;
                       }
                       if (r == outer_owner(cyc, q, kq, p.Kp, p.P)) {
-                        for (int64_t kk = kq; kk < kend; kk += BKS)
+                        for (int64_t kk = kq; kk < kend; kk += PK)
                           tma_prefetch_3d(&tmBpf, (int32_t)kk, (int32_t)n0, pt - 1);
                         pf += 1;
                       }
@@ -221,27 +233,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   const uint32_t a_dst = smem_u32(smem + stage * STAGE_BYTES);
                   const uint32_t b_dst = a_dst + A_BYTES;
                   // the pair leader's barrier counts the stage's bytes of both CTAs
+                  // (a panel past Kpad, at the end of an odd panel count, is
+                  // zero-filled by the copy and counts in full)
                   const uint32_t fb = cluster_addr(smem_u32(&full[stage]), (uint32_t)lead);
                   if (leader) mbar_arrive_expect_tx(smem_u32(&full[stage]), 2 * STAGE_BYTES);
+                  const int32_t kz0 = (int32_t)(k0 / PK);
                   if (CN == 2) {
-                    // half of the row's A tile, to both CTAs of the processor row
-                    tma_load_3d_pair_mc(a_dst + px * (A_BYTES / 2), &tmA, (int32_t)k0,
-                                        (int32_t)am0, s - 1, fb, row_mask);
+                    // half (64 rows) of the row's A tile, panel by panel, to both
+                    // CTAs of the processor row
+                    for (int h = 0; h < KZ; ++h)
+                      tma_load_4d_pair_mc(a_dst + h * A_PANEL + px * (A_PANEL / 2), &tmA, 0,
+                                          (int32_t)am0, kz0 + h, s - 1, fb, row_mask);
                   } else if (leader) {
-                    tma_load_3d(a_dst, &tmA, (int32_t)k0, (int32_t)m0, s - 1, fb);
+                    tma_load_4d(a_dst, &tmA, 0, (int32_t)m0, kz0, s - 1, fb);
                   } else {
-                    tma_load_3d_pair(a_dst, &tmA, (int32_t)k0, (int32_t)m0, s - 1, fb);
+                    tma_load_4d_pair(a_dst, &tmA, 0, (int32_t)m0, kz0, s - 1, fb);
                   }
                   if (leader)
-                    tma_load_3d(b_dst, &tmB, (int32_t)k0, (int32_t)nh, t - 1, fb);
+                    tma_load_4d(b_dst, &tmB, 0, (int32_t)nh, kz0, t - 1, fb);
                   else
-                    tma_load_3d_pair(b_dst, &tmB, (int32_t)k0, (int32_t)nh, t - 1, fb);
+                    tma_load_4d_pair(b_dst, &tmB, 0, (int32_t)nh, kz0, t - 1, fb);
                   const int64_t kc = span(0, p.K, k0, k0 + BKS);
                   const int64_t ca = span(row_lo, row_hi, am0, am0 + TM / CN) * kc;
                   a_ld += ca;
                   a_dl += ca * CN;
                   b_ld += span(col_lo, col_hi, nh, nh + HN) * kc;
-                  nops += 2;
+                  nops += CN == 2 ? KZ + 1 : 2;
                   if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
               }
@@ -267,14 +284,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       atomicAdd(&p.counters[4], pf);
       atomicAdd(&p.counters[5], nops);
     }
-  } else if ((warp == 1 || warp == 2) && leader) {
-    // ---------------- pair MMAs: issuer `me` takes the stages of parity me ----------------
+  } else if (warp == 1 && leader) {
+    // ---------------- pair MMAs: one issuer, the accumulators in turn ----------------
     if (lane == 0) {
-      const int me = warp - 1;
-      uint32_t gst = 0, nchunk = 0;
+      uint32_t gst = 0, nchunk = 0, dt = tmem_base;
       bool in_chunk = false;
-      const uint32_t dt = tmem_base + (uint32_t)(me * TN);
       bool ok = true;
+      // panels that lie inside Kpad in the last stage of a pair (2 unless the
+      // panel count is odd)
+      const int last_panels = (int)((p.Kpad - (int64_t)(nkb - 1) * BKS) / PK);
       for (int L = cid; L < ntiles && ok; L += ncl) {
         int r, c;
         tile_proc<CN>(L, ncx, ncy, ry, px, &r, &c);
@@ -284,20 +302,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (tile_skipped(cyc, c - px, ni, p.Q, TN, p.N)) continue;
             for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
               const int nst = (d - 1) * nkb;
+              int kb = 0;   // stage within the pair
               for (int st = 0; st < nst; ++st, ++gst) {
-                if ((st & 1) != me) continue;
+                const int npan = kb == nkb - 1 ? last_panels : KZ;
+                if (++kb == nkb) kb = 0;
                 const int seg_lo = st - st % SEGST;
                 const int seg_len = min(nst, seg_lo + SEGST) - seg_lo;
                 const int local = st - seg_lo;
                 bool first = false;
                 if (!in_chunk) {
-                  if (!wait_or_abort(smem_u32(&acc_empty[me]), (nchunk & 1u) ^ 1u, &abort_flag)) {
+                  // accumulator nchunk & 1, for the (nchunk >> 1)-th time
+                  const uint32_t acc = nchunk & 1u;
+                  if (!wait_or_abort(smem_u32(&acc_empty[acc]), ((nchunk >> 1) & 1u) ^ 1u,
+                                     &abort_flag)) {
                     if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteAccEmpty);
                     abort_flag = 1;
                     ok = false;
                     break;
                   }
                   tc_fence_after();
+                  dt = tmem_base + acc * (uint32_t)TN;
                   in_chunk = true;
                   first = true;
                 }
@@ -312,13 +336,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t a_addr = smem_u32(smem + stage * STAGE_BYTES);
                 const uint32_t b_addr = a_addr + A_BYTES;
 #pragma unroll
-                for (int k = 0; k < BKS / 16; ++k) {
-                  mma2_bf16(dt, sdesc_k128(a_addr + k * 32), sdesc_k128(b_addr + k * 32), IDESC2,
-                            (first && k == 0) ? 0u : 1u);
+                for (int h = 0; h < KZ; ++h) {
+                  if (h >= npan) break;
+#pragma unroll
+                  for (int k = 0; k < PK / 16; ++k) {
+                    mma2_bf16(dt, sdesc_k128(a_addr + h * A_PANEL + k * 32),
+                              sdesc_k128(b_addr + h * B_PANEL + k * 32), IDESC2,
+                              (first && h == 0 && k == 0) ? 0u : 1u);
+                  }
                 }
                 mma2_commit_mc(smem_u32(&empty[stage]), all_mask);
                 if (chunk_end(local, seg_len)) {
-                  mma2_commit_mc(smem_u32(&acc_full[me]), pair_mask);
+                  mma2_commit_mc(smem_u32(&acc_full[nchunk & 1u]), pair_mask);
                   ++nchunk;
                   in_chunk = false;
                 }
@@ -328,11 +357,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-  } else if (warp >= 4) {
+  } else if (warp >= 2) {
     // ---------------- drain (both CTAs): this SM's 128 rows -> exact int32 planes ----------------
     const int q = warp & 3;                 // tensor-memory lane quarter of this warp
-    const int h = (warp - 4) >> 2;          // column half of the 256-column tile
-    uint32_t nchunk0 = 0, nchunk1 = 0;
+    const int h = (warp - 2) >> 2;          // column half of the 256-column tile
+    uint32_t nchunk = 0;
     bool ok = true;
     for (int L = cid; L < ntiles && ok; L += ncl) {
       int r, c;
@@ -350,15 +379,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
           for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
             const int nst = (d - 1) * nkb;
-            for (int seg = 0; seg * SEGST < nst && ok; ++seg) {
-              const int seg_len = min(nst, (seg + 1) * SEGST) - seg * SEGST;
+            const int nseg_d = (nst + SEGST - 1) / SEGST;
+            for (int seg = 0; seg < p.nseg && ok; ++seg) {
+              const int seg_len = seg < nseg_d ? min(nst, (seg + 1) * SEGST) - seg * SEGST : 0;
               int acc[128];
 #pragma unroll
               for (int i = 0; i < 128; ++i) acc[i] = 0;
+              // a plane past this diagonal's segments is written as zeros: the
+              // recombination adds every plane of every diagonal
               for (int local = 0; local < seg_len; ++local) {
                 if (!chunk_end(local, seg_len)) continue;
-                const int who = local & 1;
-                const uint32_t par = who ? (nchunk1 & 1u) : (nchunk0 & 1u);
+                const uint32_t who = nchunk & 1u, par = (nchunk >> 1) & 1u;
                 // warp-uniform decision before the warp-collective tcgen05.ld
                 const bool got = wait_or_abort(smem_u32(&acc_full[who]), par, &abort_flag);
                 if (!__all_sync(0xffffffffu, got)) {
@@ -367,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t ta =
-                    tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(who * TN) + h * 128;
+                    tmem_base + ((uint32_t)(q * 32) << 16) + who * (uint32_t)TN + h * 128;
                 // two 16-column loads in flight per wait: four round trips
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
@@ -391,7 +422,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   else
                     mbar_arrive_cluster_relaxed(smem_u32(&acc_empty[who]), (uint32_t)lead);
                 }
-                if (who) ++nchunk1; else ++nchunk0;
+                ++nchunk;
               }
               if (!ok) break;
               if (row < row_hi) {
@@ -442,11 +473,12 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   const int64_t Kpad = ceil_div(g.K, 64) * 64;
   const auto BF16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap tA, tB, tApf, tBpf;
-  if (!encode_tmap_3d(&tA, BF16, 2, As, Kpad, g.M, S, BKS, TM / CN,
-                      CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_tmap_3d(&tB, BF16, 2, Bs, Kpad, g.N, S, BKS, HN, CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_tmap_3d(&tApf, BF16, 2, As, Kpad, g.M, S, BKS, TM, CU_TENSOR_MAP_SWIZZLE_NONE) ||
-      !encode_tmap_3d(&tBpf, BF16, 2, Bs, Kpad, g.N, S, BKS, TN, CU_TENSOR_MAP_SWIZZLE_NONE))
+  // copies: KZ panels per copy (64 rows and one panel per copy for the A
+  // halves of 2 x 2 groups); owner prefetches: one panel per instruction
+  if (!encode_tmap_kpanels(&tA, BF16, 2, As, Kpad, g.M, S, TM / CN, CN == 2 ? 1 : KZ) ||
+      !encode_tmap_kpanels(&tB, BF16, 2, Bs, Kpad, g.N, S, HN, KZ) ||
+      !encode_tmap_3d(&tApf, BF16, 2, As, Kpad, g.M, S, PK, TM, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+      !encode_tmap_3d(&tBpf, BF16, 2, Bs, Kpad, g.N, S, PK, TN, CU_TENSOR_MAP_SWIZZLE_NONE))
     return HSUMMA_ERR_ARG;
   PairParams p{};
   p.D = D;
@@ -464,7 +496,7 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   p.nsub_n = (int)(g.cyc ? ceil_div(ceil_div(g.N, TN), g.Q) : ceil_div(g.Nt, TN));
   p.Bo = g.Bo;
   p.S = S;
-  p.nkb = (int)(Kpad / BKS);
+  p.nkb = (int)ceil_div(Kpad, BKS);
   p.nseg = split_planes(g.K, S, HSUMMA_BF16_SLICES);
   p.counters = state().d_counters;
   p.status = state().d_status;
@@ -475,7 +507,32 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair smem)");
   cudaLaunchConfig_t cfg = {};
   const int ntiles = (g.P / 2) * (g.Q / CN);
-  cfg.gridDim = dim3((unsigned)(2 * CN * ntiles), 1, 1);
+  const int policy = state().pair_launch;
+  int nclusters = ntiles;
+  if (policy & HSUMMA_PAIR_PERSISTENT) {
+    // one cluster per resident slot, each sweeping tiles L = cid, cid + ncl, ...
+    int &res = state().pair_resident[CN];
+    if (res == 0) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3((unsigned)(2 * CN), 1, 1);
+      q.blockDim = dim3(NTHREADS, 1, 1);
+      q.dynamicSmemBytes = SMEM_BYTES;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = (unsigned)(2 * CN);
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      e = cudaOccupancyMaxActiveClusters(&res, kern, &q);
+      if (e != cudaSuccess || res < 1) {
+        res = 0;
+        return cuda_fail(e, "cudaOccupancyMaxActiveClusters(pair kernel)");
+      }
+    }
+    nclusters = ntiles < res ? ntiles : res;
+  }
+  cfg.gridDim = dim3((unsigned)(2 * CN * nclusters), 1, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = s;
@@ -499,8 +556,11 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   // k: one launch by 1.3 %; 4096 tiles x 15 x 16384 k: per diagonal by 2-4 %.
   // Rule: per diagonal from 24 rounds and 15 x 16384 k-columns of pairs a tile.
   const int resident = state().sm_count / (2 * CN);
-  const bool per_diagonal = resident > 0 && ntiles >= 24 * resident &&
-                            (int64_t)(S * (S + 1) / 2) * Kpad >= 15 * 16384;
+  const int split = policy & 0xf;
+  const bool per_diagonal =
+      split == HSUMMA_PAIR_LAUNCH_PER_DIAGONAL ||
+      (split == HSUMMA_PAIR_LAUNCH_AUTO && resident > 0 && ntiles >= 24 * resident &&
+       (int64_t)(S * (S + 1) / 2) * Kpad >= 15 * 16384);
   for (int d = 2; d <= S + 1;) {
     p.d_lo = d;
     p.d_hi = per_diagonal ? d : S + 1;

@@ -207,7 +207,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
         for (int d = 2; d <= S + 1 && ok; ++d) {
           const int nst = (d - 1) * nkb;
-          for (int seg = 0; seg * SEG_STAGES < nst && ok; ++seg) {
+          // every plane of the diagonal is written: those past its own
+          // segments as zeros (the recombination adds every plane)
+          for (int seg = 0; seg < p.nseg && ok; ++seg) {
             const int st1 = min(nst, (seg + 1) * SEG_STAGES);
             int acc[4][4][4];
 #pragma unroll

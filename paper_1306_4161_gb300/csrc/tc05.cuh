@@ -211,6 +211,39 @@ __device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const void *tm, int
       : "memory");
 }
 
+// 4-D tiled loads over the k-panel view {64, rows, Kp / 64, S} of a slice
+// tensor (see encode_tmap_kpanels): a box {64, rows, kz, 1} brings kz
+// consecutive 64-column panels of a tile in one copy, landing as kz panels of
+// rows x 128 bytes one after the other.  Plain, CTA-pair (bytes counted on the
+// pair leader's barrier) and multicast CTA-pair forms, as for the 3-D loads.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tm, int32_t x, int32_t y,
+                                            int32_t z, int32_t w, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d_pair(uint32_t dst, const void *tm, int32_t x,
+                                                 int32_t y, int32_t z, int32_t w, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d_pair_mc(uint32_t dst, const void *tm, int32_t x,
+                                                    int32_t y, int32_t z, int32_t w,
+                                                    uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster.cta_group::2 [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar), "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_3d(const void *tm, int32_t x, int32_t y,
                                                 int32_t z) {
   asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];" ::"l"(

@@ -57,6 +57,33 @@ def test_workspace_sizes(lib):
     assert hs.split_planes(16384, "int8", 8) == 1
 
 
+def test_planes_cover_every_kernel_segment(lib):
+    # The product kernels cut a diagonal's exact sum into int32 segments of a
+    # fixed number of k-stages: 1016 stages of 128 columns (bf16 on CTA pairs),
+    # 2032 stages of 64 (bf16 on one CTA) or 2048 of 128 (int8), a pair's last
+    # stage padded to the stage width.  Every segment of the longest diagonal
+    # (S pairs) must have a plane: a kernel writing more would write past the
+    # sums' storage.  Odd panel counts (Kp / 64 odd) make the 128-column stages
+    # longer than Kp; K = 43328, S = 3 and K = 87360, S = 3 are cases where
+    # that padding adds a segment.
+    cd = lambda a, b: -(-a // b)
+    Ks = sorted({64, 700, 4096, 16384, 32768, 43328, 43392, 87360, 87296, 130048, 130112,
+                 260032, 260096} | {64 * n for n in range(1, 4000, 37)})
+    for K in Ks:
+        Kp = cd(K, 64) * 64
+        for S in range(1, 8):
+            for kind, stage, seg in (("bf16", 128, 1016), ("bf16", 64, 2032), ("int8", 128, 2048)):
+                if kind == "int8" and S > 8:
+                    continue
+                planes = hs.split_planes(K, kind, S)
+                segs = cd(S * cd(Kp, stage), seg)
+                assert segs <= planes, (K, S, kind, stage, segs, planes)
+                # and no plane is wasted beyond one for the padding
+                assert planes <= cd(S * Kp, seg * stage) + 1
+    assert hs.split_planes(43328, "bf16", 3) == 2
+    assert hs.split_planes(87360, "int8", 3) == 2
+
+
 def test_errors_before_init(lib):
     st = lib.hsumma_gemm(4, 4, 4, None, 4, None, 4, None, 4, 1, 1, 1, 16, 16, 0, None)
     assert st == -5
