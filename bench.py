@@ -35,12 +35,13 @@ sys.path.insert(0, ROOT)
 
 N_SIZE = 16384
 METRIC = "FP64-accurate TFLOP/s at n=16384, split-precision vs native FP64, % of roofline"
-SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=2048, kind="bf16", slices=5)
+SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=512, kind="bf16", slices=5)
 NATIVE = dict(P=128, Q=128, G=8192, b=32, Bouter=128)
 WORKLOAD = ("split_vs_fp64_16384: M=N=K=16384, A,B uniform[-1,1] (SplitMix64 seeds 1002/2002), "
             "bf16 slices S=5 (15 pair products), virtual grid 128x64 of 128x256 blocks, "
             "G=4096 groups of 2x1 (each group one CTA pair: the in-group B broadcast is the "
-            "two-SM MMA), b=64, B=2048 (owner L2 prefetch); "
+            "two-SM MMA; persistent clusters, one launch per diagonal), b=64, B=512 "
+            "(owner L2 prefetch); "
             "native fp64 beside it on a 128x128 grid, G=8192 groups of 2x1 (2-CTA clusters), "
             "b=32, B=128")
 

@@ -349,13 +349,14 @@ int hsumma_pair_kernel(int enable);
  * bits choose how the slice pairs are split over launches:
  *   HSUMMA_PAIR_LAUNCH_AUTO          the library's rule: one launch per
  *                                    diagonal for long products of many
- *                                    rounds of tiles, else one launch (the
- *                                    setting after hsumma_init);
+ *                                    rounds of tiles, else one launch;
  *   HSUMMA_PAIR_LAUNCH_ONE           one launch for all S (S + 1) / 2 pairs;
  *   HSUMMA_PAIR_LAUNCH_PER_DIAGONAL  one launch per diagonal d = s + t;
  * or-ing HSUMMA_PAIR_PERSISTENT launches one cluster per resident cluster
  * slot of the device, each sweeping the group tiles cid, cid + ncl, ...,
- * instead of one cluster per group tile.  A negative value only queries.
+ * instead of one cluster per group tile.  After hsumma_init the policy is
+ * HSUMMA_PAIR_LAUNCH_AUTO | HSUMMA_PAIR_PERSISTENT.  A negative value only
+ * queries.
  * Returns the previous policy, HSUMMA_ERR_ARG for an unknown one, or
  * HSUMMA_ERR_NOT_INIT.  Results are identical under every policy. */
 enum {

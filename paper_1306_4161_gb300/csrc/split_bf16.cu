@@ -18,19 +18,25 @@
 // int32 sums are stored as one plane of the output, D[d-2][seg][i][j], and the
 // recombination adds the planes of a diagonal exactly.
 //
-// Two MMA issuers.  On this GPU one issuing thread sustains about one MMA per
-// 135 ns whatever its shape, half of what the SM's tensor core can execute;
-// two threads issuing into separate accumulators reach the full rate.  Issuer
-// i (warp 1 + i) takes the k-stages of parity i and owns the accumulator in
-// tensor-memory columns [256 i, 256 i + 256); the issuers' chunk boundaries are
-// staggered by half a chunk, so one accumulator is being filled while the
-// other is drained.  Chunk ends, in stage order, are the drain events.
+// One MMA issuer.  A single issuing thread sustains the full tensor rate (one
+// 128 x 256 x 16 MMA per 128 cycles), so the two accumulators (tensor-memory
+// columns 0..255 and 256..511) are used in turn, chunk n in accumulator
+// n mod 2: while the drain warps empty one, the MMAs fill the other.
 //
-// Roles (384 threads): warp 0 issues the copies, warps 1 and 2 issue the MMAs
-// (warp 1 also owns tensor memory), warp 3 idles, warps 4..11 drain (two per
-// 32-lane quarter of tensor memory, 128 columns each; 128 int32 sums per
-// thread).  Shared memory: 4 stages of 16 KB (A, 128 x 64) + 32 KB (B,
-// 256 x 64).
+// Roles (384 threads): warp 0 issues the copies, warp 1 issues the MMAs and
+// owns tensor memory, warps 2 and 3 idle, warps 4..11 drain (a warp reads the
+// tensor-memory lanes of its quarter, warp mod 4; warps 4..7 and 8..11 cover
+// the 128 rows for the two column halves; 128 int32 sums per thread).  With
+// 12 warps the compiler fits every role in 168 registers without spilling;
+// with the idle warps left out it spills.
+//
+// Shared memory: a ring of 4 stages, the A slots (16 KB, 128 x 64) side by
+// side and then the B slots (32 KB, 256 x 64).  What bounds this kernel is
+// the delivery of its operands: 48 KB per 512-cycle stage (96 B per cycle at
+// the full tensor rate, against about 70 that the copy engine of an SM
+// streams, and about 360 cycles per copy), and the issuing thread's own path
+// per stage.  Copies of two panels at once (measured) and two issuing threads
+// (measured) were both slower for flat groups.
 #include "internal.h"
 #include "ptx.cuh"
 #include "tc05.cuh"
@@ -42,9 +48,10 @@ namespace {
 constexpr int TM = 128, TN = 256, BKS = 64, STAGES = 4;
 constexpr int A_BYTES = TM * BKS * 2, B_BYTES = TN * BKS * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int B_REGION = STAGES * A_BYTES;   // ring: all A slots, then all B slots
 constexpr int CH = 16;                 // k-stages per accumulator chunk
 constexpr int NEPI = 8;                // draining warps
-constexpr int NTHREADS = (4 + NEPI) * 32;
+constexpr int NTHREADS = (4 + NEPI) * 32;   // copy warp, MMA warp, two idle warps, drain warps
 constexpr int SEGST = 127 * CH;        // stages per int32 segment
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
@@ -66,6 +73,9 @@ __device__ __forceinline__ int64_t span(int64_t lo, int64_t hi, int64_t a, int64
 // wait that also gives up as soon as another role of the CTA has aborted
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
                                               volatile int *abort_flag, bool cluster_scope) {
+  // the first try needs no clock: most waits succeed at once
+  if (cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))
+    return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))
@@ -76,13 +86,10 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
 }
 
 // Does stage `local` (counted from the start of its segment of `seg_len`
-// stages) end a chunk of the issuer that owns it (issuer = local & 1)?  Issuer
-// 0 closes a chunk every 16 of its stages, issuer 1 after 8 and then every 16;
-// both close one at their last stage of the segment.
+// stages) end a chunk?  A chunk closes after every CH stages of a segment and
+// at its last stage.
 __device__ __forceinline__ bool chunk_end(int local, int seg_len) {
-  const int c = (local >> 1) + 1;
-  if (local + 2 >= seg_len) return true;
-  return (local & 1) ? ((c + 8) % CH == 0) : (c % CH == 0);
+  return (local + 1) % CH == 0 || local + 1 == seg_len;
 }
 
 // cluster tile L -> processor row r and column c of this CTA: tiles are
@@ -162,6 +169,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ---------------- copies ----------------
+    // One issuing thread at one stage per 512 cycles: everything that does not
+    // change along k (the counted rows, the pieces of a clustered operand) is
+    // worked out once per sub-tile, so that the per-stage path stays short.
     if (lane == 0) {
       unsigned long long a_ld = 0, a_dl = 0, b_ld = 0, b_dl = 0, pf = 0, nops = 0;
       uint32_t stage = 0, phase = 0;
@@ -177,9 +187,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (tile_skipped(cyc, c - cx, ni, p.Q, TN, p.N)) continue;
             int64_t n0, col_lo, col_hi;
             tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
+            // rows of A and columns of B this CTA copies for the sub-tile (its
+            // share of the cluster row / column: a contiguous box, or 8-row
+            // pieces dealt round robin), inside its block and the matrix; every
+            // slice pair delivers them over all K
+            int64_t a_rows = 0, b_cols = 0;
+            for (int i = a_contig ? cx * (a_box / 8) : cx; i < TM / 8; i += a_contig ? TM / 8 : cn)
+              a_rows += span(row_lo, row_hi, m0 + (int64_t)i * 8, m0 + (int64_t)i * 8 + a_box);
+            for (int i = b_contig ? cy * (b_box / 8) : cy; i < TN / 8; i += b_contig ? TN / 8 : cm)
+              b_cols += span(col_lo, col_hi, n0 + (int64_t)i * 8, n0 + (int64_t)i * 8 + b_box);
             for (int d = 2; d <= S + 1 && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
+                a_ld += (unsigned long long)(a_rows * p.K);
+                a_dl += (unsigned long long)(a_rows * p.K * cn);
+                b_ld += (unsigned long long)(b_cols * p.K);
+                b_dl += (unsigned long long)(b_cols * p.K * cm);
                 int rem = 0;   // k0 mod B, kept without a 64-bit division per stage
                 for (int kb = 0; kb < nkb; ++kb) {
                   const int64_t k0 = (int64_t)kb * BKS;
@@ -225,35 +248,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   }
                   const uint32_t fb = smem_u32(&full[stage]);
                   mbar_arrive_expect_tx(fb, STAGE_BYTES);
-                  const uint32_t a_base = smem_u32(smem + stage * STAGE_BYTES);
-                  const uint32_t b_base = a_base + A_BYTES;
-                  const int64_t kc = span(0, p.K, k0, k0 + BKS);
+                  const uint32_t a_base = smem_u32(smem + stage * A_BYTES);
+                  const uint32_t b_base = smem_u32(smem + B_REGION + stage * B_BYTES);
                   // A tile (128 rows): contiguous share of the cluster row, or 8-row
                   // pieces dealt round-robin when the width does not divide 16
                   for (int i = a_contig ? cx * (a_box / 8) : cx; i < TM / 8;
                        i += a_contig ? TM / 8 : cn) {
-                    const int64_t ar = m0 + (int64_t)i * 8;
                     const uint32_t dst = a_base + i * 8 * 128;
+                    const int32_t y = (int32_t)(m0 + (int64_t)i * 8);
                     if (cn > 1)
-                      tma_load_3d_mc(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb, row_mask);
+                      tma_load_3d_mc(dst, &tmA, (int32_t)k0, y, s - 1, fb, row_mask);
                     else
-                      tma_load_3d(dst, &tmA, (int32_t)k0, (int32_t)ar, s - 1, fb);
-                    const int64_t ca = span(row_lo, row_hi, ar, ar + a_box) * kc;
-                    a_ld += ca;
-                    a_dl += ca * cn;
+                      tma_load_3d(dst, &tmA, (int32_t)k0, y, s - 1, fb);
                     nops += 1;
                   }
                   for (int i = b_contig ? cy * (b_box / 8) : cy; i < TN / 8;
                        i += b_contig ? TN / 8 : cm) {
-                    const int64_t br = n0 + (int64_t)i * 8;
                     const uint32_t dst = b_base + i * 8 * 128;
+                    const int32_t y = (int32_t)(n0 + (int64_t)i * 8);
                     if (cm > 1)
-                      tma_load_3d_mc(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb, col_mask);
+                      tma_load_3d_mc(dst, &tmB, (int32_t)k0, y, t - 1, fb, col_mask);
                     else
-                      tma_load_3d(dst, &tmB, (int32_t)k0, (int32_t)br, t - 1, fb);
-                    const int64_t cb = span(col_lo, col_hi, br, br + b_box) * kc;
-                    b_ld += cb;
-                    b_dl += cb * cm;
+                      tma_load_3d(dst, &tmB, (int32_t)k0, y, t - 1, fb);
                     nops += 1;
                   }
                   if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -279,15 +295,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       atomicAdd(&p.counters[4], pf);
       atomicAdd(&p.counters[5], nops);
     }
-  } else if (warp == 1 || warp == 2) {
-    // ---------------- MMA issue: issuer `me` takes the stages of parity me ----------------
+  } else if (warp == 1) {
+    // ---------------- MMA issue: one thread, the accumulators in turn ----------------
     if (lane == 0) {
-      const int me = warp - 1;
       uint32_t gst = 0;   // stage counter over the whole launch: ring slot and phase
-      uint32_t nchunk = 0;
+      uint32_t nchunk = 0, dt = tmem_base;
       bool in_chunk = false;
       const uint16_t rel_mask = row_mask | col_mask;
-      const uint32_t dt = tmem_base + (uint32_t)(me * TN);
       bool ok = true;
       for (int L = cid; L < ntiles && ok; L += ncl) {
         int r, c;
@@ -299,20 +313,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int d = 2; d <= S + 1 && ok; ++d) {
               const int nst = (d - 1) * nkb;
               for (int st = 0; st < nst; ++st, ++gst) {
-                if ((st & 1) != me) continue;
                 const int seg_lo = st - st % SEGST;
                 const int seg_len = min(nst, seg_lo + SEGST) - seg_lo;
                 const int local = st - seg_lo;
                 bool first = false;
                 if (!in_chunk) {
-                  if (!wait_or_abort(smem_u32(&acc_empty[me]), (nchunk & 1u) ^ 1u, &abort_flag,
-                                     false)) {
+                  const uint32_t acc = nchunk & 1u;
+                  if (!wait_or_abort(smem_u32(&acc_empty[acc]), ((nchunk >> 1) & 1u) ^ 1u,
+                                     &abort_flag, false)) {
                     if (!abort_flag) record_error(p.status, HSUMMA_ERR_TIMEOUT, kSiteAccEmpty);
                     abort_flag = 1;
                     ok = false;
                     break;
                   }
                   tc_fence_after();
+                  dt = tmem_base + acc * (uint32_t)TN;
                   in_chunk = true;
                   first = true;
                 }
@@ -324,8 +339,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   break;
                 }
                 tc_fence_after();
-                const uint32_t a_addr = smem_u32(smem + stage * STAGE_BYTES);
-                const uint32_t b_addr = a_addr + A_BYTES;
+                const uint32_t a_addr = smem_u32(smem + stage * A_BYTES);
+                const uint32_t b_addr = smem_u32(smem + B_REGION + stage * B_BYTES);
 #pragma unroll
                 for (int k = 0; k < BKS / 16; ++k) {
                   mma_bf16(dt, sdesc_k128(a_addr + k * 32), sdesc_k128(b_addr + k * 32), IDESC,
@@ -337,7 +352,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 else
                   mma_commit(smem_u32(&empty[stage]));
                 if (chunk_end(local, seg_len)) {
-                  mma_commit(smem_u32(&acc_full[me]));
+                  mma_commit(smem_u32(&acc_full[nchunk & 1u]));
                   ++nchunk;
                   in_chunk = false;
                 }
@@ -351,7 +366,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---------------- drain: chunk ends in stage order -> exact int32 planes ----------------
     const int q = warp & 3;                 // tensor-memory lane quarter of this warp
     const int h = (warp - 4) >> 2;          // column half
-    uint32_t nchunk0 = 0, nchunk1 = 0;
+    uint32_t nchunk = 0;
     bool ok = true;
     for (int L = cid; L < ntiles && ok; L += ncl) {
       int r, c;
@@ -379,8 +394,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               // recombination adds every plane of every diagonal
               for (int local = 0; local < seg_len; ++local) {
                 if (!chunk_end(local, seg_len)) continue;
-                const int who = local & 1;
-                const uint32_t par = who ? (nchunk1 & 1u) : (nchunk0 & 1u);
+                const uint32_t who = nchunk & 1u, par = (nchunk >> 1) & 1u;
                 // the whole warp decides together: tcgen05.ld below is warp-collective
                 const bool got = wait_or_abort(smem_u32(&acc_full[who]), par, &abort_flag, false);
                 if (!__all_sync(0xffffffffu, got)) {
@@ -389,7 +403,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t ta =
-                    tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(who * TN) + h * 128;
+                    tmem_base + ((uint32_t)(q * 32) << 16) + who * (uint32_t)TN + h * 128;
                 // two 16-column loads in flight per wait: four round trips
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
@@ -406,7 +420,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&acc_empty[who]));
-                if (who) ++nchunk1; else ++nchunk0;
+                ++nchunk;
               }
               if (!ok) break;
               if (row < row_hi) {

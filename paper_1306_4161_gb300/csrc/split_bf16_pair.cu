@@ -33,11 +33,11 @@
 // four CTAs once both pairs' MMAs have read it (the commits of both leaders,
 // multicast to the cluster).
 //
-// Roles (320 threads per CTA): warp 0 issues the copies, warp 1 issues the MMAs
-// (leader only) and owns its CTA's tensor memory, warps 2..9 drain their CTA's
-// 128 rows into exact int32 planes (a warp reads the tensor-memory lanes of
-// its own quarter, warp mod 4, so warps 2..5 and 6..9 each cover all 128 rows,
-// for the two column halves).
+// Roles (384 threads per CTA): warp 0 issues the copies, warp 1 issues the MMAs
+// (leader only) and owns its CTA's tensor memory, warps 2 and 3 idle, warps
+// 4..11 drain their CTA's 128 rows into exact int32 planes (a warp reads the
+// tensor-memory lanes of its quarter, warp mod 4; warps 4..7 and 8..11 cover
+// the 128 rows for the two column halves).
 #include "internal.h"
 #include "ptx.cuh"
 #include "tc05.cuh"
@@ -56,7 +56,7 @@ constexpr int A_BYTES = KZ * A_PANEL, BH_BYTES = KZ * B_PANEL;
 constexpr int STAGE_BYTES = A_BYTES + BH_BYTES;
 constexpr int CH = 8;                  // stages per accumulator chunk (1024 products)
 constexpr int NEPI = 8;                // draining warps per CTA
-constexpr int NTHREADS = (2 + NEPI) * 32;   // copy warp, MMA warp, drain warps
+constexpr int NTHREADS = (4 + NEPI) * 32;   // copy warp, MMA warp, two idle warps, drain warps
 constexpr int SEGST = 127 * CH;        // stages per int32 segment
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
@@ -78,6 +78,8 @@ __device__ __forceinline__ int64_t span(int64_t lo, int64_t hi, int64_t a, int64
 
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
                                               volatile int *abort_flag) {
+  // the first try needs no clock: most waits succeed at once
+  if (mbar_try_wait_cluster(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try_wait_cluster(bar, parity)) return true;
@@ -183,9 +185,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int64_t n0, col_lo, col_hi;
             tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &n0, &col_lo, &col_hi);
             const int64_t nh = n0 + ry * HN;
+            // rows of A and columns of B this CTA copies for the sub-tile (inside
+            // its block and the matrix); every slice pair delivers them over all K
+            const int64_t a_rows = span(row_lo, row_hi, am0, am0 + TM / CN);
+            const int64_t b_cols = span(col_lo, col_hi, nh, nh + HN);
             for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
+                a_ld += (unsigned long long)(a_rows * p.K);
+                a_dl += (unsigned long long)(a_rows * p.K * CN);
+                b_ld += (unsigned long long)(b_cols * p.K);
                 int rem = 0;   // panel start mod B, kept without a 64-bit division
                 for (int kb = 0; kb < nkb; ++kb) {
                   const int64_t k0 = (int64_t)kb * BKS;
@@ -253,11 +262,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     tma_load_4d(b_dst, &tmB, 0, (int32_t)nh, kz0, t - 1, fb);
                   else
                     tma_load_4d_pair(b_dst, &tmB, 0, (int32_t)nh, kz0, t - 1, fb);
-                  const int64_t kc = span(0, p.K, k0, k0 + BKS);
-                  const int64_t ca = span(row_lo, row_hi, am0, am0 + TM / CN) * kc;
-                  a_ld += ca;
-                  a_dl += ca * CN;
-                  b_ld += span(col_lo, col_hi, nh, nh + HN) * kc;
                   nops += CN == 2 ? KZ + 1 : 2;
                   if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
@@ -357,10 +361,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-  } else if (warp >= 2) {
+  } else if (warp >= 4) {
     // ---------------- drain (both CTAs): this SM's 128 rows -> exact int32 planes ----------------
     const int q = warp & 3;                 // tensor-memory lane quarter of this warp
-    const int h = (warp - 2) >> 2;          // column half of the 256-column tile
+    const int h = (warp - 4) >> 2;          // column half of the 256-column tile
     uint32_t nchunk = 0;
     bool ok = true;
     for (int L = cid; L < ntiles && ok; L += ncl) {

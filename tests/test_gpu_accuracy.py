@@ -13,7 +13,7 @@ from tests.gpu_util import border_grid, lib_ready, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
-BENCH_SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=2048)    # bench.py's split launch
+BENCH_SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=512)     # bench.py's split launch
 BENCH_NATIVE = dict(P=128, Q=128, G=8192, b=32, Bouter=128)   # bench.py's binary64 launch
 INT8_FLAT = dict(P=128, Q=128, G=1, b=128, Bouter=2048)
 

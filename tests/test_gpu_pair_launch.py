@@ -74,24 +74,24 @@ def test_pair_launch_rejects_unknown_policy():
         hs.pair_launch("sideways")
     assert hs.lib().hsumma_pair_launch(0x7) == -1        # split code out of range
     assert hs.lib().hsumma_pair_launch(0x100) == -1      # unknown bit
-    assert hs.pair_launch() == ("auto", False)           # unchanged, the default
+    assert hs.pair_launch() == ("auto", True)            # unchanged, the default
 
 
 def test_bench_launch_bit_exact_at_16384():
     # bench.py's split step as it runs: M = N = K = 16384, uniform[-1, 1], bf16
     # S = 5, a 128 x 64 grid of 128 x 256 blocks, G = 4096 groups of 2 x 1 (one
-    # CTA pair each), b = 64, B = 2048; at this size the library's rule makes
-    # one launch per diagonal (exponent scan 2, slicing 2, products 5,
-    # recombination 1 launches).  Sampled entries, including every corner and
-    # tile border, bit for bit against the oracle.
+    # CTA pair each), b = 64, B = 512; persistent pair clusters, and at this
+    # size the library's rule makes one launch per diagonal (exponent scan 2,
+    # slicing 2, products 5, recombination 1 launches).  Sampled entries,
+    # including every corner and tile border, bit for bit against the oracle.
     hs = lib_ready()
     torch = torch_cuda()
     n, S = 16384, 5
-    assert hs.pair_launch() == ("auto", False) and hs.pair_kernel() is True
+    assert hs.pair_launch() == ("auto", True) and hs.pair_kernel() is True
     dA = workloads.matrix_torch(n, n, 1002, "uniform", device="cuda")
     dB = workloads.matrix_torch(n, n, 2002, "uniform", device="cuda")
     n0 = hs.launches()
-    C = hs.gemm(dA, dB, P=128, Q=64, G=4096, b=64, Bouter=2048, kind="bf16", slices=S)
+    C = hs.gemm(dA, dB, P=128, Q=64, G=4096, b=64, Bouter=512, kind="bf16", slices=S)
     hs.sync()
     assert hs.launches() - n0 == 2 + 2 + S + 1
     rows, cols = sample_entries(n, n, 48, 123)
