@@ -91,6 +91,27 @@ def multi_gpu_line(world: int):
             "unavailable": MULTI_GPU_UNAVAILABLE}
 
 
+def timeline_summary(tl, n):
+    """One host-buffer call's pipeline, from its timed phases: the device time
+    of the block products, when the first product started (the exposed copy-in),
+    the time after the last one (the exposed copy-out), the products' waits
+    for data in between, and the host-link rates the copies ran at."""
+    prod = sorted((a, b) for nm, r, c, a, b in tl if nm == "product")
+    cin = [(a, b) for nm, r, c, a, b in tl if nm in ("B in", "A in")]
+    cout = [(a, b) for nm, r, c, a, b in tl if nm == "C out"]
+    if not prod:
+        return {}
+    waits = sum(max(0.0, prod[i][0] - prod[i - 1][1]) for i in range(1, len(prod)))
+    busy_in = sum(b - a for a, b in cin)
+    busy_out = sum(b - a for a, b in cout)
+    return {"products_ms": round(sum(b - a for a, b in prod), 2),
+            "first_product_at_ms": round(prod[0][0], 2),
+            "waits_between_ms": round(waits, 2),
+            "after_last_product_ms": round(max(b for a, b in cout) - prod[-1][1], 2),
+            "h2d_gbps": round(2 * 8 * n * n / busy_in / 1e6, 1) if busy_in > 0 else None,
+            "d2h_gbps": round(8 * n * n / busy_out / 1e6, 1) if busy_out > 0 else None}
+
+
 def read_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -466,26 +487,25 @@ def main():
         hB = dB.cpu().pin_memory()
         hC = torch.empty((n, n), dtype=torch.float64).pin_memory()
         hs.gemm_host(hA, hB, hC, **SPLIT)
-        calls = []
+        # every call with its pipeline phases timed (CUDA events on the streams
+        # that ran them): where the time above the device time goes, call by call
+        calls, lines = [], []
+        hs.stage_timing(True)
         for _ in range(args.e2e_calls):
             t0 = time.perf_counter()
             hs.gemm_host(hA, hB, hC, **SPLIT)
             calls.append(time.perf_counter() - t0)
+            lines.append(hs.host_timeline())
+        hs.stage_timing(False)
         te = float(np.median(calls))
+        med = int(np.argsort(calls)[len(calls) // 2])
         e2e = {"value": flops() / te / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
                "ms_per_step": te * 1e3, "of": f"median of {len(calls)} calls",
-               "calls_ms": [round(c * 1e3, 1) for c in calls]}
-        # one more call with the pipeline's phases timed (CUDA events on the
-        # streams that ran them): where the time above the device time goes
-        hs.stage_timing(True)
-        t0 = time.perf_counter()
-        hs.gemm_host(hA, hB, hC, **SPLIT)
-        wall = time.perf_counter() - t0
-        hs.stage_timing(False)
-        e2e["timeline"] = {"call_ms": round(wall * 1e3, 2),
-                           "phases_ms": [[name, blk, round(a, 2), round(b, 2)]
-                                         for name, blk, a, b in hs.host_timeline()]}
+               "calls": [dict(call_ms=round(c * 1e3, 1), **timeline_summary(tl, n))
+                         for c, tl in zip(calls, lines)],
+               "median_call_phases_ms": [[nm, r, c, round(a, 2), round(b, 2)]
+                                         for nm, r, c, a, b in lines[med]]}
         # this box's pinned host-link rates (outside the timed region): the
         # copies alone need max(H2D bytes / H2D rate, D2H bytes / D2H rate)
         scratch = torch.empty_like(dA)

@@ -389,14 +389,23 @@ int hsumma_selftest_timeout(long long limit_ns, void *stream);
 int hsumma_stage_timing(int enable);
 int hsumma_stage_times(double *h_ms, int *h_calls);
 
-/* Timeline of the last hsumma_gemm_host call, when that call ran with stage
- * timing on and was pipelined by row blocks (otherwise *h_count = 0): *h_count
- * phases, in this order: the copy of B in, then for each row block r the copy
- * of A_r in, the product of block r, the copy of C_r out.  For phase i,
- * h_ms[2 i] and h_ms[2 i + 1] are its start and end in milliseconds after the
- * call's first event (CUDA events on the stream that ran the phase); at most
- * max values are written.  The pipeline has at most 4 row blocks (13 phases). */
+/* hsumma_gemm_host runs a product of at least two blocks as a pipeline: C is
+ * cut into R row blocks (R in {4, 3, 2}, R | P, R | I) and Cb column blocks
+ * (Cb in {2, 1}, Cb | Q, Cb | J), each block keeping the product's groups;
+ * B_0 and A_0 are copied in first, and each block product starts once its
+ * A_r and B_c are on the device while the rest copy in and the finished
+ * blocks of C copy out.
+ * Timeline of the last hsumma_gemm_host call, when that call ran with stage
+ * timing on and was pipelined (otherwise *h_count = 0): *h_count phases, in
+ * this order: the copies of B_c in (c < Cb), the copies of A_r in (r < R),
+ * the block products (r-major: C_00, C_01, C_10, ...), the copies of the
+ * blocks of C out (same order).  For phase i, h_ms[2 i] and h_ms[2 i + 1] are
+ * its start and end in milliseconds after the call's first event (CUDA events
+ * on the stream that ran the phase); at most max values are written (at most
+ * 22 phases).  hsumma_host_timeline_blocks gives R and Cb of that call (0 and
+ * 0 when there is no timeline). */
 int hsumma_host_timeline(double *h_ms, int max, int *h_count);
+int hsumma_host_timeline_blocks(int *rows, int *cols);
 
 /* ---- Peak microbenchmarks (roofline denominators) ---- */
 

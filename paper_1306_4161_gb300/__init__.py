@@ -81,6 +81,7 @@ _SIGS = {
     "hsumma_stage_timing": ([_i32], _i32),
     "hsumma_stage_times": ([_vp, ctypes.POINTER(ctypes.c_int)], _i32),
     "hsumma_host_timeline": ([_vp, _i32, ctypes.POINTER(ctypes.c_int)], _i32),
+    "hsumma_host_timeline_blocks": ([ctypes.POINTER(ctypes.c_int)] * 2, _i32),
     "hsumma_candidates": ([_i64, _i64, _i64, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_int)],
                           _i32),
     "hsumma_features": ([_i64, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
@@ -394,22 +395,20 @@ def stage_times():
     return list(ms), n.value
 
 
-HOST_PHASES = ("B in", "A in", "product", "C out")
-
-
 def host_timeline():
     """Phases of the last gemm_host call made with stage timing on, when it was
-    pipelined by row blocks: a list of (name, block, start ms, end ms) relative
-    to the call's first event ([] otherwise)."""
-    ms = (ctypes.c_double * 32)()
-    n = ctypes.c_int()
-    _check(lib().hsumma_host_timeline(ms, 32, ctypes.byref(n)))
-    out = []
-    for i in range(n.value):
-        name = HOST_PHASES[0] if i == 0 else HOST_PHASES[1 + (i - 1) % 3]
-        block = -1 if i == 0 else (i - 1) // 3
-        out.append((name, block, ms[2 * i], ms[2 * i + 1]))
-    return out
+    pipelined: a list of (name, row block, column block, start ms, end ms)
+    relative to the call's first event, name one of "B in", "A in", "product",
+    "C out" (block -1 where a phase has no such index); [] otherwise."""
+    ms = (ctypes.c_double * 64)()
+    n, R, Cb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().hsumma_host_timeline(ms, 64, ctypes.byref(n)))
+    _check(lib().hsumma_host_timeline_blocks(ctypes.byref(R), ctypes.byref(Cb)))
+    R, Cb = R.value, Cb.value
+    names = [("B in", -1, c) for c in range(Cb)] + [("A in", r, -1) for r in range(R)]
+    names += [("product", r, c) for r in range(R) for c in range(Cb)]
+    names += [("C out", r, c) for r in range(R) for c in range(Cb)]
+    return [(nm, r, c, ms[2 * i], ms[2 * i + 1]) for i, (nm, r, c) in enumerate(names[:n.value])]
 
 
 PAIR_LAUNCH = {"auto": 0, "one": 1, "per_diagonal": 2}

@@ -17,6 +17,7 @@ it leaves the grid and the panel sizes to the user.  This module
     with P = Q = G = b = Bouter = 0 uses it.
 
     python -m paper_1306_4161_gb300.autotune collect --out DIR
+    python -m paper_1306_4161_gb300.autotune collect-large --out DIR
     python -m paper_1306_4161_gb300.autotune train --data DIR --out DIR/cost_model.npz
     python -m paper_1306_4161_gb300.autotune evaluate --data DIR --model DIR/cost_model.npz
 """
@@ -179,8 +180,66 @@ def collect(out_dir, n_samples=2000, per_shape=20, n_heldout=200, seed=4000, rep
     log(f"collected in {time.time() - t0:.0f}s")
 
 
-def _save_heldout(out_dir, shape_rows, offs, cfgs, mss, base_cfg, base_ms):
-    np.savez_compressed(os.path.join(out_dir, "heldout.npz"),
+BENCH_PRODUCT = (16384, 16384, 16384, "bf16", 5)   # the benchmark's split product
+
+
+def collect_large(out_dir, n_train=40, per_shape=10, n_heldout=30, seed=4000, reps=1,
+                  log=print):
+    """The large-product extension (M, N, K in [8192, 32768], bf16 and int8;
+    workloads.tuning_shapes_large): training samples, per_shape seeded
+    candidates of each of n_train products (samples_large.npz, product ids from
+    100000), and a held-out set, every candidate of each of n_heldout other
+    products and of the benchmark's product (heldout_large.npz).  One timed run
+    per configuration (these products run 0.1 to several seconds)."""
+    import torch
+    wl = _workloads()
+    os.makedirs(out_dir, exist_ok=True)
+    hs.init(0)
+    timer = Timer()
+    t0 = time.time()
+    rows = []
+    for i, (M, N, K, kind, S) in enumerate(wl.tuning_shapes_large(n_train, seed + 5)):
+        A, B, C = operands(M, N, K, seed + 30000 + i)
+        cands = hs.candidates(M, N, K, kind, S)
+        order = np.argsort(wl.splitmix64(seed + 200000 + i, 0, len(cands)), kind="stable")
+        time_config(timer, A, B, C, cands[0], kind, S, reps=1)     # grows the workspace
+        for j in sorted(order[:per_shape].tolist()):
+            ms = time_config(timer, A, B, C, cands[j], kind, S, reps)
+            rows.append((M, N, K, KIND_CODE[kind], S, *cands[j], ms, 100000 + i))
+        hs.sync()
+        del A, B, C
+        torch.cuda.empty_cache()
+        log(f"large train {i + 1}/{n_train} shapes, {time.time() - t0:.0f}s")
+    if rows:
+        np.savez_compressed(os.path.join(out_dir, "samples_large.npz"),
+                            rows=np.array(rows, dtype=np.float64))
+    shapes = wl.tuning_shapes_large(n_heldout, seed + 6) + [BENCH_PRODUCT]
+    shape_rows, offs, cfgs, mss, base_cfg, base_ms = [], [0], [], [], [], []
+    for i, (M, N, K, kind, S) in enumerate(shapes):
+        A, B, C = operands(M, N, K, seed + 40000 + i)
+        cands = hs.candidates(M, N, K, kind, S)
+        time_config(timer, A, B, C, cands[0], kind, S, reps=1)
+        ms = [time_config(timer, A, B, C, c, kind, S, reps) for c in cands]
+        base = paper_rule(M, N, K, kind, S)
+        bms = time_config(timer, A, B, C, base, kind, S, reps)
+        hs.sync()
+        shape_rows.append((M, N, K, KIND_CODE[kind], S))
+        cfgs.extend(cands)
+        mss.extend(ms)
+        offs.append(len(cfgs))
+        base_cfg.append(base)
+        base_ms.append(bms)
+        del A, B, C
+        torch.cuda.empty_cache()
+        log(f"large held-out {i + 1}/{len(shapes)} shapes, {time.time() - t0:.0f}s")
+        _save_heldout(out_dir, shape_rows, offs, cfgs, mss, base_cfg, base_ms,
+                      name="heldout_large.npz")
+    log(f"collected the large products in {time.time() - t0:.0f}s")
+
+
+def _save_heldout(out_dir, shape_rows, offs, cfgs, mss, base_cfg, base_ms,
+                  name="heldout.npz"):
+    np.savez_compressed(os.path.join(out_dir, name),
                         shapes=np.array(shape_rows, dtype=np.int64),
                         offsets=np.array(offs, dtype=np.int64),
                         cfg=np.array(cfgs, dtype=np.int64).reshape(-1, 5),
@@ -200,6 +259,17 @@ def load_heldout(path):
                         ms=d["ms"][a:b], base_cfg=tuple(int(v) for v in d["base_cfg"][i]),
                         base_ms=float(d["base_ms"][i])))
     return out
+
+
+def load_samples(data_dir):
+    """Training rows: samples.npz and, when present, samples_large.npz
+    (untimed configurations, which failed to launch, left out)."""
+    parts = [np.load(os.path.join(data_dir, "samples.npz"))["rows"]]
+    large = os.path.join(data_dir, "samples_large.npz")
+    if os.path.exists(large):
+        parts.append(np.load(large)["rows"])
+    rows = np.concatenate(parts)
+    return rows[np.isfinite(rows[:, 10])]
 
 
 def split_by_product(rows, frac=0.1):
@@ -434,6 +504,12 @@ def main(argv=None):
     t.add_argument("--val", default=os.path.join(TUNING_DIR, "validation.npz"),
                    help="products with every candidate timed (heldout.npz format) that select "
                         "the checkpoint; '' uses the training products' last 10 %% instead")
+    cl = sub.add_parser("collect-large")
+    cl.add_argument("--out", default=TUNING_DIR)
+    cl.add_argument("--products", type=int, default=40)
+    cl.add_argument("--per-shape", type=int, default=10)
+    cl.add_argument("--heldout", type=int, default=30)
+    cl.add_argument("--seed", type=int, default=4000)
     e = sub.add_parser("evaluate")
     e.add_argument("--data", default=TUNING_DIR)
     e.add_argument("--model", default=MODEL_PATH)
@@ -442,8 +518,7 @@ def main(argv=None):
     if a.cmd == "collect":
         collect(a.out, a.samples, a.per_shape, a.heldout, a.seed)
     elif a.cmd == "train":
-        rows = np.load(os.path.join(a.data, "samples.npz"))["rows"]
-        rows = rows[np.isfinite(rows[:, 10])]
+        rows = load_samples(a.data)
         if a.val:
             X, y = sample_features(rows)
             model = train(X, y, a.steps, a.lr, a.seed, val_products=load_heldout(a.val))
@@ -454,9 +529,20 @@ def main(argv=None):
             model = train(X, y, a.steps, a.lr, a.seed, X_val=Xv, y_val=yv)
         model["analytic"] = fit_analytic(rows)
         save_model(model, a.out)
+    elif a.cmd == "collect-large":
+        collect_large(a.out, a.products, a.per_shape, a.heldout, a.seed)
     else:
         hs.init(0)
-        rep = evaluate(read_model(a.model), load_heldout(os.path.join(a.data, "heldout.npz")))
+        model = read_model(a.model)
+        rep = evaluate(model, load_heldout(os.path.join(a.data, "heldout.npz")))
+        large = os.path.join(a.data, "heldout_large.npz")
+        if os.path.exists(large):
+            held = load_heldout(large)
+            rep["large"] = evaluate(model, held)
+            bench = [h for h in held if (h["M"], h["N"], h["K"], h["kind"], h["S"]) ==
+                     BENCH_PRODUCT]
+            if bench:
+                rep["large"]["bench_product"] = evaluate(model, bench)
         text = json.dumps(rep, indent=1)
         print(text)
         if a.report:

@@ -571,6 +571,16 @@ static int host_row_blocks(int64_t M, int P, int I, int64_t Mt) {
   return 1;
 }
 
+// Column blocks likewise: 2 blocks of Q/2 processor columns (2 | Q and 2 | J)
+// of at least 512 columns each, both non-empty, else 1.
+static int host_col_blocks(int64_t N, int Q, int J, int64_t Nt) {
+  const int C = kMaxHostColBlocks;
+  if (Q % C || J % C) return 1;
+  const int64_t cols = (int64_t)(Q / C) * Nt;
+  if (cols < 512 || (C - 1) * cols >= N) return 1;
+  return C;
+}
+
 // The pipeline's events, created on first use and kept until hsumma_finalize:
 // ordering events always, timing events when `timed`.
 static cudaError_t pipeline_events(bool timed) {
@@ -583,18 +593,21 @@ static cudaError_t pipeline_events(bool timed) {
   return e;
 }
 
-// hsumma_gemm_host pipelined by row blocks: C_r = A_r B for the R row blocks
-// of A and C.  B is copied first on the copy-in stream, then the blocks of A;
-// the caller's stream scans and slices B once (split path), then per block
-// waits for its rows of A and runs the path on them; each finished block of C
-// is copied back on the copy-out stream while the next block computes.  Every
-// element is computed as in the unblocked product (row exponents are per row,
-// column exponents over the whole of B), so the result is the same bit for bit.
-// With stage timing on, timing events bracket every phase (the timeline of
-// hsumma_host_timeline).
+// hsumma_gemm_host pipelined by blocks: C_rc = A_r B_c for the R row blocks of
+// A and C and the Cb column blocks of B and C.  The copy-in stream brings B_0,
+// A_0, then the other column blocks of B, then the other row blocks of A; the
+// caller's stream, for the split path, scans and slices each column block of
+// B once when it has arrived and each row block of A before its first
+// product, and runs the products row block by row block (C_00, C_01, C_10, ...),
+// each after the copies it needs; each finished block of C goes back on the
+// copy-out stream while the next one computes.  The first product thus waits
+// only for A_0 and B_0.  Every element is computed as in the unblocked product
+// (row exponents are per row of A and column exponents per column of B, each
+// over all of K), so the result is the same bit for bit.  With stage timing
+// on, timing events bracket every phase (the timeline of hsumma_host_timeline).
 static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA, int64_t lda,
                                const double *hB, int64_t ldb, double *hC, int64_t ldc,
-                               const GridPlan &full, int R, int kind, int S, double *dA,
+                               const GridPlan &full, int R, int Cb, int kind, int S, double *dA,
                                double *dB, double *dC, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (!g_state.copy_in) e = cudaStreamCreateWithFlags(&g_state.copy_in, cudaStreamNonBlocking);
@@ -610,12 +623,20 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate(pipeline)");
   cudaStream_t ci = g_state.copy_in, co = g_state.copy_out;
   const int64_t rows = (int64_t)(full.P / R) * full.Mt;
-  // ordering events: [0] the caller's earlier work, [1] B copied, [2 + r] A
-  // block r copied, [2 + R + r] C block r computed, [2 + 2 R] all copied back
+  const int64_t cols = (int64_t)(full.Q / Cb) * full.Nt;
+  auto row_count = [&](int r) { return (M - r * rows) < rows ? (M - r * rows) : rows; };
+  auto col_count = [&](int c) { return (N - c * cols) < cols ? (N - c * cols) : cols; };
+  // ordering events: [0] the caller's earlier work, [1] all copied back,
+  // [2 + c] B_c copied, [2 + Cb + r] A_r copied, [2 + Cb + R + (r Cb + c)] C_rc computed
   cudaEvent_t *ev = g_state.pipe_ev;
-  cudaEvent_t evPrior = ev[0], evB = ev[1], evDone = ev[2 + 2 * R];
-  // timing events: [0] start, then (start, end) of phase i at [1 + 2 i], [2 + 2 i]
+  cudaEvent_t evPrior = ev[0], evDone = ev[1];
+  auto evB = [&](int c) { return ev[2 + c]; };
+  auto evA = [&](int r) { return ev[2 + Cb + r]; };
+  auto evC = [&](int r, int c) { return ev[2 + Cb + R + r * Cb + c]; };
+  // timing events: [0] start, then (start, end) of phase i at [1 + 2 i], [2 + 2 i];
+  // phases: B_c in (c < Cb), A_r in (r < R), product rc, C_rc out (r-major)
   cudaEvent_t *tev = g_state.pipe_tev;
+  const int ph_b = 0, ph_a = Cb, ph_prod = Cb + R, ph_out = Cb + R + R * Cb;
   auto mark = [&](int phase, int end, cudaStream_t st) {
     return timed ? cudaEventRecord(tev[1 + 2 * phase + end], st) : cudaSuccess;
   };
@@ -624,86 +645,107 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   e = cudaMemsetAsync(g_state.d_counters, 0, 8 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return fail(e, "cudaMemsetAsync(counters)");
   if (timed) e = cudaEventRecord(tev[0], s);
-  // copies in: B, then A block by block
   if (e == cudaSuccess) e = cudaEventRecord(evPrior, s);  // the caller's earlier work first
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, evPrior, 0);
-  if (e == cudaSuccess) e = mark(0, 0, ci);
-  if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(dB, ldb * 8, hB, ldb * 8, N * 8, K, cudaMemcpyHostToDevice, ci);
-  if (e == cudaSuccess) e = mark(0, 1, ci);
-  if (e == cudaSuccess) e = cudaEventRecord(evB, ci);
-  for (int r = 0; r < R && e == cudaSuccess; ++r) {
-    const int64_t r0 = r * rows, mr = (M - r0) < rows ? (M - r0) : rows;
-    e = mark(1 + 3 * r, 0, ci);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(dA + r0 * lda, lda * 8, hA + r0 * lda, lda * 8, K * 8, mr,
+  // copies in: B_0, A_0, B_1 .., A_1 ..
+  auto copy_b = [&](int c) {
+    cudaError_t x = mark(ph_b + c, 0, ci);
+    if (x == cudaSuccess)
+      x = cudaMemcpy2DAsync(dB + c * cols, ldb * 8, hB + c * cols, ldb * 8, col_count(c) * 8, K,
                             cudaMemcpyHostToDevice, ci);
-    if (e == cudaSuccess) e = mark(1 + 3 * r, 1, ci);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + r], ci);
-  }
+    if (x == cudaSuccess) x = mark(ph_b + c, 1, ci);
+    if (x == cudaSuccess) x = cudaEventRecord(evB(c), ci);
+    return x;
+  };
+  auto copy_a = [&](int r) {
+    const int64_t r0 = r * rows;
+    cudaError_t x = mark(ph_a + r, 0, ci);
+    if (x == cudaSuccess)
+      x = cudaMemcpy2DAsync(dA + r0 * lda, lda * 8, hA + r0 * lda, lda * 8, K * 8, row_count(r),
+                            cudaMemcpyHostToDevice, ci);
+    if (x == cudaSuccess) x = mark(ph_a + r, 1, ci);
+    if (x == cudaSuccess) x = cudaEventRecord(evA(r), ci);
+    return x;
+  };
+  if (e == cudaSuccess) e = copy_b(0);
+  if (e == cudaSuccess) e = copy_a(0);
+  for (int c = 1; c < Cb && e == cudaSuccess; ++c) e = copy_b(c);
+  for (int r = 1; r < R && e == cudaSuccess; ++r) e = copy_a(r);
   if (e != cudaSuccess) return fail(e, "copy operands in");
 
-  // the split path: B's exponents and slices once; a block-sized workspace
+  // split-path workspace for one block: e (rows), f (all N), A slices of one
+  // row block, B slices of every column block, the diagonal sums of one block
   int32_t *e_rows = nullptr, *f_cols = nullptr, *D = nullptr;
-  void *As = nullptr, *Bs = nullptr;
+  uint8_t *As = nullptr, *Bs = nullptr;
+  size_t bs_stride = 0;
   int st = HSUMMA_OK;
-  e = cudaStreamWaitEvent(s, evB, 0);
-  if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(B)");
   if (kind != HSUMMA_FP64) {
-    st = ensure_workspace(split_ws_bytes(rows, N, K, kind, S));
-    if (st != HSUMMA_OK) return st;
     const int64_t Kp = ceil_div(K, 64) * 64;
     const size_t eb = kind == HSUMMA_INT8_SLICES ? 1 : 2;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    bs_stride = al((size_t)S * cols * Kp * eb);
+    const size_t need = al(rows * 4) + al(N * 4) + al((size_t)S * rows * Kp * eb) +
+                        Cb * bs_stride + al((size_t)S * split_planes(K, S, kind) * rows * cols * 4);
+    st = ensure_workspace(need);
+    if (st != HSUMMA_OK) return st;
     uint8_t *ws = reinterpret_cast<uint8_t *>(g_state.workspace);
     e_rows = reinterpret_cast<int32_t *>(ws);
     ws += al(rows * 4);
     f_cols = reinterpret_cast<int32_t *>(ws);
     ws += al(N * 4);
     As = ws;
-    ws += al(S * rows * Kp * eb);
+    ws += al((size_t)S * rows * Kp * eb);
     Bs = ws;
-    ws += al(S * N * Kp * eb);
+    ws += Cb * bs_stride;
     D = reinterpret_cast<int32_t *>(ws);
-    st = launch_split_exponents(0, N, K, nullptr, 1, dB, ldb, nullptr, f_cols, s);
-    if (st == HSUMMA_OK)
-      st = launch_split_slices(0, N, K, nullptr, 1, dB, ldb, nullptr, f_cols, kind, S, nullptr,
-                               Bs, s);
-    if (st != HSUMMA_OK) return st;
   }
   for (int r = 0; r < R; ++r) {
-    const int64_t r0 = r * rows, mr = (M - r0) < rows ? (M - r0) : rows;
-    GridPlan g;
-    st = make_plan(mr, N, K, full.P / R, full.Q, full.G / R, full.b, full.Bo, kind, full.cyc,
-                   &g);
-    if (st != HSUMMA_OK) return st;
-    e = cudaStreamWaitEvent(s, ev[2 + r], 0);
-    if (e == cudaSuccess) e = mark(2 + 3 * r, 0, s);
-    if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(A block)");
+    const int64_t r0 = r * rows, mr = row_count(r);
     const double *Ar = dA + r0 * lda;
-    double *Cr = dC + r0 * ldc;
-    if (kind == HSUMMA_FP64) {
-      st = launch_fp64_hsumma(g, Ar, lda, dB, ldb, Cr, ldc, s);
-    } else {
-      st = launch_split_exponents(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, s);
-      if (st == HSUMMA_OK)
-        st = launch_split_slices(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, kind, S, As,
-                                 nullptr, s);
-      if (st == HSUMMA_OK) st = launch_split_diagonals(g, kind, S, As, Bs, D, s);
-      if (st == HSUMMA_OK)
-        st = launch_split_recombine(mr, N, K, kind, S, D, e_rows, f_cols, Cr, ldc, s);
+    for (int c = 0; c < Cb; ++c) {
+      const int64_t c0 = c * cols, nc = col_count(c);
+      GridPlan g;
+      st = make_plan(mr, nc, K, full.P / R, full.Q / Cb, full.G / (R * Cb), full.b, full.Bo,
+                     kind, full.cyc, &g);
+      if (st != HSUMMA_OK) return st;
+      // this block's operands: A_r, and B_c (scanned and sliced at its first use)
+      e = cudaStreamWaitEvent(s, evA(r), 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, evB(c), 0);
+      if (e == cudaSuccess) e = mark(ph_prod + r * Cb + c, 0, s);
+      if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(operands)");
+      double *Crc = dC + r0 * ldc + c0;
+      if (kind == HSUMMA_FP64) {
+        st = launch_fp64_hsumma(g, Ar, lda, dB + c0, ldb, Crc, ldc, s);
+      } else {
+        void *Bsc = Bs + c * bs_stride;
+        if (r == 0) {
+          st = launch_split_exponents(0, nc, K, nullptr, 1, dB + c0, ldb, nullptr, f_cols + c0,
+                                      s);
+          if (st == HSUMMA_OK)
+            st = launch_split_slices(0, nc, K, nullptr, 1, dB + c0, ldb, nullptr, f_cols + c0,
+                                     kind, S, nullptr, Bsc, s);
+        }
+        if (st == HSUMMA_OK && c == 0) {
+          st = launch_split_exponents(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, s);
+          if (st == HSUMMA_OK)
+            st = launch_split_slices(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, kind, S, As,
+                                     nullptr, s);
+        }
+        if (st == HSUMMA_OK) st = launch_split_diagonals(g, kind, S, As, Bsc, D, s);
+        if (st == HSUMMA_OK)
+          st = launch_split_recombine(mr, nc, K, kind, S, D, e_rows, f_cols + c0, Crc, ldc, s);
+      }
+      if (st != HSUMMA_OK) return st;
+      e = mark(ph_prod + r * Cb + c, 1, s);
+      if (e == cudaSuccess) e = cudaEventRecord(evC(r, c), s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(co, evC(r, c), 0);
+      if (e == cudaSuccess) e = mark(ph_out + r * Cb + c, 0, co);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(hC + r0 * ldc + c0, ldc * 8, Crc, ldc * 8, nc * 8, mr,
+                              cudaMemcpyDeviceToHost, co);
+      if (e == cudaSuccess) e = mark(ph_out + r * Cb + c, 1, co);
+      if (e != cudaSuccess) return fail(e, "copy a block of C out");
     }
-    if (st != HSUMMA_OK) return st;
-    cudaEvent_t done = ev[2 + R + r];
-    e = mark(2 + 3 * r, 1, s);
-    if (e == cudaSuccess) e = cudaEventRecord(done, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(co, done, 0);
-    if (e == cudaSuccess) e = mark(3 + 3 * r, 0, co);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(hC + r0 * ldc, ldc * 8, Cr, ldc * 8, N * 8, mr,
-                            cudaMemcpyDeviceToHost, co);
-    if (e == cudaSuccess) e = mark(3 + 3 * r, 1, co);
-    if (e != cudaSuccess) return fail(e, "copy a block of C out");
   }
   e = cudaEventRecord(evDone, co);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, evDone, 0);
@@ -711,7 +753,9 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   st = hsumma_sync(reinterpret_cast<void *>(s));
   if (timed) {
     std::lock_guard<std::mutex> lock(g_stage_mu);
-    g_state.timeline_phases = st == HSUMMA_OK ? 1 + 3 * R : 0;
+    g_state.timeline_phases = st == HSUMMA_OK ? ph_out + R * Cb : 0;
+    g_state.timeline_rows = R;
+    g_state.timeline_cols = Cb;
   }
   return st;
 }
@@ -761,10 +805,20 @@ int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t 
     const bool exact_ok = kind == HSUMMA_FP64 || (double)S * (double)K * 16384.0 < 9.0e18;
     const bool tma_ok = kind != HSUMMA_FP64 || (tma_ready(dA, lda) && tma_ready(dB, ldb) &&
                                                 (lda % 2) == 0);
-    const int R = host_row_blocks(M, P, full.I, full.Mt);
-    if (R > 1 && exact_ok && tma_ok)
-      return gemm_host_pipelined(M, N, K, hA, lda, hB, ldb, hC, ldc, full, R, kind, S, dA, dB,
-                                 dC, s);
+    int R = host_row_blocks(M, P, full.I, full.Mt);
+    int Cb = host_col_blocks(N, Q, full.J, full.Nt);
+    // every block must resolve to the same groups and clusters as the product
+    auto keeps_groups = [&](int r, int c) {
+      int I, J, cm, cn;
+      return resolve_groups(P / r, Q / c, full.G / (r * c), g_state.cluster_limit, &I, &J, &cm,
+                            &cn) == HSUMMA_OK &&
+             I * r == full.I && J * c == full.J && cm == full.cm && cn == full.cn;
+    };
+    if (Cb > 1 && !keeps_groups(R, Cb)) Cb = 1;
+    if (R > 1 && !keeps_groups(R, Cb)) R = 1;
+    if (R * Cb > 1 && exact_ok && tma_ok)
+      return gemm_host_pipelined(M, N, K, hA, lda, hB, ldb, hC, ldc, full, R, Cb, kind, S, dA,
+                                 dB, dC, s);
   }
   cudaError_t e;
   if (M && K) {
@@ -971,6 +1025,17 @@ int hsumma_stage_times(double *ms, int *calls) {
     }
   }
   *calls = (int)g_stage_used;
+  return HSUMMA_OK;
+}
+
+int hsumma_host_timeline_blocks(int *rows, int *cols) {
+  if (!rows || !cols) {
+    set_error("null output pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  *rows = g_state.timeline_phases ? g_state.timeline_rows : 0;
+  *cols = g_state.timeline_phases ? g_state.timeline_cols : 0;
   return HSUMMA_OK;
 }
 

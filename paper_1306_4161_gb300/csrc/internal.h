@@ -21,11 +21,15 @@ struct GridPlan {
                          // block-checkerboard (one block per processor)
 };
 
-// Row blocks of the pipelined host-buffer product (at most), and the timing
-// events of its timeline: a start event, then a start and an end for each of
-// the 1 + 3 R phases (B in; per block: A_r in, compute, C_r out).
-constexpr int kMaxHostBlocks = 4;
-constexpr int kHostTimelineEvents = 1 + 2 * (1 + 3 * kMaxHostBlocks);
+// Row and column blocks of the pipelined host-buffer product (at most), and
+// the timing events of its timeline: a start event, then a start and an end
+// for each of its Cb + R + 2 R Cb phases (the copies of B_c in, of A_r in,
+// then per block the product and the copy of C_rc out).
+constexpr int kMaxHostBlocks = 4;      // row blocks
+constexpr int kMaxHostColBlocks = 2;   // column blocks
+constexpr int kMaxHostPhases =
+    kMaxHostColBlocks + kMaxHostBlocks + 2 * kMaxHostBlocks * kMaxHostColBlocks;
+constexpr int kHostTimelineEvents = 1 + 2 * kMaxHostPhases;
 
 struct DeviceState {
   int device = -1;
@@ -46,9 +50,11 @@ struct DeviceState {
   cudaStream_t copy_out = nullptr;
   // hsumma_gemm_host's pipeline events, created once: ordering events (no
   // timing) and, when stage timing is on, timing events around every phase
-  cudaEvent_t pipe_ev[kMaxHostBlocks * 2 + 3] = {};
+  cudaEvent_t pipe_ev[3 + kMaxHostColBlocks + kMaxHostBlocks +
+                      kMaxHostBlocks * kMaxHostColBlocks] = {};
   cudaEvent_t pipe_tev[kHostTimelineEvents] = {};
   int timeline_phases = 0;                   // phases the last timed call recorded
+  int timeline_rows = 0, timeline_cols = 0;  // and its row and column blocks
 };
 
 DeviceState &state();

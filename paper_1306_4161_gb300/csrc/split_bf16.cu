@@ -104,8 +104,10 @@ __device__ __forceinline__ void tile_proc(int L, int ncx, int ncy, int cm, int c
   *c = (idx / in_group) * cn + cx;
 }
 
-// CYC: block-cyclic layout of the grid, else block-checkerboard
-template <bool CYC>
+// CYC: block-cyclic layout of the grid, else block-checkerboard; FLAT: groups
+// served flat (no cluster), which folds the cluster arithmetic of the copy
+// thread's per-stage path away
+template <bool CYC, bool FLAT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     bf16_diag_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB,
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cx = (int)cluster_ctaid_x(), cy = (int)cluster_ctaid_y();
-  const int cn = p.cn, cm = p.cm;
+  const int cn = FLAT ? 1 : p.cn, cm = FLAT ? 1 : p.cm;
   // persistent clusters: cluster `cid` plays the virtual processors of the
   // cluster tiles L = cid, cid + ncl, ... (walked in raster order), so the
   // clusters resident together work on neighbouring blocks in step
@@ -460,10 +462,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }  // namespace
 
 int bf16_cluster_limit(int *limit) {
-  cudaError_t e = cudaFuncSetAttribute(bf16_diag_kernel<false>,
+  cudaError_t e = cudaFuncSetAttribute(bf16_diag_kernel<false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-  e = cudaFuncSetAttribute(bf16_diag_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  e = cudaFuncSetAttribute(bf16_diag_kernel<false, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(non-portable cluster)");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16, 1, 1);
@@ -477,7 +479,7 @@ int bf16_cluster_limit(int *limit) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  e = cudaOccupancyMaxPotentialClusterSize(&n, bf16_diag_kernel<false>, &cfg);
+  e = cudaOccupancyMaxPotentialClusterSize(&n, bf16_diag_kernel<false, false>, &cfg);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxPotentialClusterSize");
   *limit = n;
   return HSUMMA_OK;
@@ -518,7 +520,9 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
   p.nseg = split_planes(g.K, S);
   p.counters = state().d_counters;
   p.status = state().d_status;
-  auto kern = g.cyc ? bf16_diag_kernel<true> : bf16_diag_kernel<false>;
+  const bool flat = g.cm * g.cn == 1;
+  auto kern = g.cyc ? (flat ? bf16_diag_kernel<true, true> : bf16_diag_kernel<true, false>)
+                    : (flat ? bf16_diag_kernel<false, true> : bf16_diag_kernel<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");

@@ -363,3 +363,43 @@ def test_a_wait_that_runs_out_is_reported_and_cleared():
     C = hs.gemm(dA, dB, P=2, Q=2, G=1, b=64, Bouter=128, kind="bf16", slices=3)
     hs.sync()
     assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 3, "bf16"))
+
+
+@pytest.mark.parametrize("kind,S,P,Q,G,dist", [
+    ("bf16", 3, 16, 8, 64, "wide"),        # 2 x 1 groups on CTA pairs
+    ("fp64", 0, 16, 16, 16, "smallint"),   # 4 x 4 clusters
+])
+def test_host_entry_pipelined_in_two_dimensions(kind, S, P, Q, G, dist):
+    # 4 row blocks x 2 column blocks: B_0 and A_0 first, each block product
+    # after its own operands; the timeline lists every phase in order and C is
+    # the unblocked product bit for bit
+    hs = lib_ready()
+    torch = torch_cuda()
+    M, N = 2048, 1032          # ragged column blocks (the second one is shorter)
+    K = 700 if kind == "bf16" else 512
+    A = torch.from_numpy(workloads.matrix(M, K, 57, dist)).pin_memory()
+    B = torch.from_numpy(workloads.matrix(K, N, 58, dist)).pin_memory()
+    big = np.full((M, N + 8), 7.0)
+    hC = big[:, :N]
+    b = 64 if kind == "bf16" else 32
+    hs.stage_timing(True)
+    try:
+        hs.gemm_host(A, B, hC, P=P, Q=Q, G=G, b=b, Bouter=4 * b, kind=kind, slices=S)
+        tl = hs.host_timeline()
+    finally:
+        hs.stage_timing(False)
+    names = [(nm, r, c) for nm, r, c, _, _ in tl]
+    assert names[:6] == [("B in", -1, 0), ("B in", -1, 1), ("A in", 0, -1), ("A in", 1, -1),
+                         ("A in", 2, -1), ("A in", 3, -1)]
+    prods = [(r, c) for nm, r, c in names if nm == "product"]
+    assert prods == [(r, c) for r in range(4) for c in range(2)]
+    assert len(tl) == 2 + 4 + 2 * 8
+    t = {(nm, r, c): (a, e) for nm, r, c, a, e in tl}
+    # the first product waits for A_0 and B_0 only
+    assert t[("product", 0, 0)][0] >= max(t[("B in", -1, 0)][1], t[("A in", 0, -1)][1]) - 1e-3
+    if kind == "fp64":
+        want = (A.numpy().astype(np.int64) @ B.numpy().astype(np.int64)).astype(np.float64)
+    else:
+        want = split.split_gemm(A.numpy(), B.numpy(), S, kind)
+    assert np.array_equal(hC, want)
+    assert np.all(big[:, N:] == 7.0)
