@@ -378,6 +378,40 @@ def run_table(sections):
         del A, B, C
 
 
+# Small cases for profiler captures: (n, configuration).  Each run makes one
+# warm-up product and then the product to capture (ncu -s 1 -c 1).
+PROFILE_CASES = {
+    # bf16 S = 5 on CTA pairs (2 x 1 groups): one persistent launch at this size
+    "pair6144": (6144, dict(P=48, Q=24, G=576, b=64, Bouter=512, kind="bf16", slices=5)),
+    # bf16 S = 5 on single CTAs, flat (64-processor software groups)
+    "diag6144": (6144, dict(P=48, Q=24, G=18, b=64, Bouter=1024, kind="bf16", slices=5)),
+    # int8 S = 5, flat
+    "int8_4096": (4096, dict(P=32, Q=32, G=1, b=128, Bouter=2048, kind="int8", slices=5)),
+    # binary64 with 2 x 2 clusters (inner level by multicast), and flat
+    "fp64_2048_cluster": (2048, dict(P=16, Q=16, G=64, b=32, Bouter=128)),
+    "fp64_2048_flat": (2048, dict(P=16, Q=16, G=256, b=32, Bouter=128)),
+}
+
+
+def run_profile_case(name):
+    """Two products of a small case (seeded uniform inputs), for a profiler
+    to capture the second; prints the group shape and the counters."""
+    import torch
+    import paper_1306_4161_gb300 as hs
+    import workloads
+    n, cfg = PROFILE_CASES[name]
+    hs.init(0)
+    A = workloads.matrix_torch(n, n, 1002, "uniform", device="cuda")
+    B = workloads.matrix_torch(n, n, 2002, "uniform", device="cuda")
+    C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        hs.gemm(A, B, out=C, **cfg)
+        hs.sync()
+    print(json.dumps({"case": name, "n": n, "group_shape": hs.group_shape(cfg["P"], cfg["Q"],
+                                                                          cfg["G"]),
+                      "counters": hs.counters()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,7 +430,12 @@ def main():
                     help="comma-separated workload numbers 0..3 (4: block against "
                          "block-cyclic layout): print throughput rows of their "
                          "configurations instead of the benchmark line")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one small case twice (for a profiler) instead of the benchmark")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     configure(args.size)
     if args.table is not None:
         run_table({int(x) for x in args.table.split(",") if x.strip()})
@@ -475,8 +514,8 @@ def main():
                                f"({S} launches of the kernel, one per diagonal)",
                 "duration_ms": dur[2], "timed_stages": ncalls,
                 "traffic": measured_traffic() if N_SIZE == 16384 else None,
-                "traffic_unit": "bytes per product stage (ncu dram read + write, summed over "
-                                "its launches)"}
+                "traffic_unit": "bytes per product stage (ncu dram read + write), scaled from "
+                                "a capture at n = 6144 (profiles/traffic.json)"}
     breakdown_ms = {"exponent_scan": dur[0], "slicing": dur[1], "diagonal_products": dur[2],
                     "recombination": dur[3]}
 
