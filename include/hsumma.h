@@ -177,7 +177,11 @@ int hsumma_split_slices(int64_t M, int64_t N, int64_t K, const double *d_A,
 
 /* Number of int32 planes per diagonal that step 3 writes for this K: a
  * diagonal's exact sum is split into segments whose partial sums stay below
- * 2^31 in magnitude.  Returns the count (>= 1) or HSUMMA_ERR_ARG. */
+ * 2^31 in magnitude (bf16: 127 x 1024 products, int8: 2^18).  The count
+ * covers the longest diagonal, S pairs of K rounded up to a multiple of 128
+ * (the product kernels' stage width); every plane of every diagonal is
+ * written, zeros past a diagonal's own segments.  Returns the count (>= 1)
+ * or HSUMMA_ERR_ARG. */
 int hsumma_split_planes(int64_t K, int kind, int S);
 
 /* Step 3, the kept pair products (pairs s + t <= S + 1) multiplied on the

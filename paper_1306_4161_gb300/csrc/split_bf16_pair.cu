@@ -10,9 +10,15 @@
 // rows.  Each CTA loads its own 128 rows of A and one half (128 columns) of the
 // group's B panel; the pair MMA reads both halves from the two SMs, which is
 // the in-group column broadcast of Section III done by the tensor cores
-// instead of a copy.  Each SM therefore holds 32 KB per k-stage (48 KB in the
-// single-CTA kernel) and the ring is 6 stages deep: about 1.6 times the work
-// in flight per byte of shared memory, and a third less traffic from L2.
+// instead of a copy.  Each SM therefore needs 32 KB per 64 k-columns (48 KB in
+// the single-CTA kernel), a third less traffic from L2 per product.
+//
+// A stage is two 64-column panels (128 k-columns, 64 KB per SM) and the ring
+// holds 3: each operand of a stage arrives in one 32 KB copy through a 4-D
+// "k-panel" tensor map that lands both panels one after the other.  An SM's
+// copy engine takes about as long for a 16 KB copy as for a 32 KB one, so
+// copies of single panels would cap the operand stream near 36 B per cycle,
+// against the 64 B per cycle and SM that the full tensor rate needs here.
 //
 // Synchronisation (no forwarding step): the first CTA of the pair ("leader")
 // expects the bytes of both CTAs on its own "full" barrier, and the second
@@ -20,18 +26,19 @@
 // tensor copies).  One issuing thread of the leader runs every MMA: a single
 // thread sustains the full tensor rate (one 256 x 256 x 16 pair MMA per 128
 // cycles), so the two accumulators (tensor-memory columns 0..255 and 256..511
-// of both SMs) are used in turn, a chunk of at most 16 k-stages (1024
-// products, the bound of exact fp32 sums) in each: while the drain warps of
-// both CTAs empty one accumulator, the MMAs fill the other.  Each stage's MMA
+// of both SMs) are used in turn, a chunk of at most 8 stages (1024 products,
+// the bound of exact fp32 sums) in each: while the drain warps of both CTAs
+// empty one accumulator, the MMAs fill the other.  Each stage's MMA
 // completion releases the stage in both CTAs, each chunk end hands the
 // accumulator to the drain warps, and they return it to the leader.  Every
 // wait is bounded (4 s) and ends in an error status.
 //
 // 2 x 2 groups: the two CTAs of a processor row each load one half (64 rows)
 // of the row's A tile and multicast it to both (cta_group::2 copies that count
-// the bytes on each destination's pair leader); a stage is released in all
-// four CTAs once both pairs' MMAs have read it (the commits of both leaders,
-// multicast to the cluster).
+// the bytes on each destination's pair leader), one copy per panel, since a
+// two-panel box of half a tile would not land in the MMA's layout; a stage is
+// released in all four CTAs once both pairs' MMAs have read it (the commits of
+// both leaders, multicast to the cluster).
 //
 // Roles (384 threads per CTA): warp 0 issues the copies, warp 1 issues the MMAs
 // (leader only) and owns its CTA's tensor memory, warps 2 and 3 idle, warps
