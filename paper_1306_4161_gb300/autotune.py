@@ -184,7 +184,7 @@ BENCH_PRODUCT = (16384, 16384, 16384, "bf16", 5)   # the benchmark's split produ
 
 
 def collect_large(out_dir, n_train=40, per_shape=10, n_heldout=30, seed=4000, reps=1,
-                  log=print):
+                  log=print, samples_name="samples_large.npz"):
     """The large-product extension (M, N, K in [8192, 32768], bf16 and int8;
     workloads.tuning_shapes_large): training samples, per_shape seeded
     candidates of each of n_train products (samples_large.npz, product ids from
@@ -211,8 +211,10 @@ def collect_large(out_dir, n_train=40, per_shape=10, n_heldout=30, seed=4000, re
         torch.cuda.empty_cache()
         log(f"large train {i + 1}/{n_train} shapes, {time.time() - t0:.0f}s")
     if rows:
-        np.savez_compressed(os.path.join(out_dir, "samples_large.npz"),
+        np.savez_compressed(os.path.join(out_dir, samples_name),
                             rows=np.array(rows, dtype=np.float64))
+    if n_heldout <= 0:
+        return
     shapes = wl.tuning_shapes_large(n_heldout, seed + 6) + [BENCH_PRODUCT]
     shape_rows, offs, cfgs, mss, base_cfg, base_ms = [], [0], [], [], [], []
     for i, (M, N, K, kind, S) in enumerate(shapes):
@@ -262,12 +264,12 @@ def load_heldout(path):
 
 
 def load_samples(data_dir):
-    """Training rows: samples.npz and, when present, samples_large.npz
+    """Training rows: samples.npz and every samples_large*.npz present
     (untimed configurations, which failed to launch, left out)."""
     parts = [np.load(os.path.join(data_dir, "samples.npz"))["rows"]]
-    large = os.path.join(data_dir, "samples_large.npz")
-    if os.path.exists(large):
-        parts.append(np.load(large)["rows"])
+    for name in sorted(os.listdir(data_dir)):
+        if name.startswith("samples_large") and name.endswith(".npz"):
+            parts.append(np.load(os.path.join(data_dir, name))["rows"])
     rows = np.concatenate(parts)
     return rows[np.isfinite(rows[:, 10])]
 
@@ -510,6 +512,8 @@ def main(argv=None):
     cl.add_argument("--per-shape", type=int, default=10)
     cl.add_argument("--heldout", type=int, default=30)
     cl.add_argument("--seed", type=int, default=4000)
+    cl.add_argument("--samples-name", default="samples_large.npz",
+                    help="file of the training samples (every samples_large*.npz trains)")
     e = sub.add_parser("evaluate")
     e.add_argument("--data", default=TUNING_DIR)
     e.add_argument("--model", default=MODEL_PATH)
@@ -530,7 +534,8 @@ def main(argv=None):
         model["analytic"] = fit_analytic(rows)
         save_model(model, a.out)
     elif a.cmd == "collect-large":
-        collect_large(a.out, a.products, a.per_shape, a.heldout, a.seed)
+        collect_large(a.out, a.products, a.per_shape, a.heldout, a.seed,
+                      samples_name=a.samples_name)
     else:
         hs.init(0)
         model = read_model(a.model)
