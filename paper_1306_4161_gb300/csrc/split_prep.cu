@@ -192,12 +192,13 @@ __device__ __forceinline__ void store8(void *dst, const int (&t)[8]) {
   }
 }
 
-// A slices: As[s][i][k], k < Kp (zero beyond K); each thread 8 consecutive k
-template <int KIND>
+// A slices: As[s][i][k], k < Kp (zero beyond K); each thread 8 consecutive k.
+// S is a template parameter so that every digit's bit position is a constant.
+template <int KIND, int S>
 __global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restrict__ A,
                                                           int64_t lda, int64_t M, int64_t K,
                                                           int64_t Kp,
-                                                          const int32_t *__restrict__ e, int S,
+                                                          const int32_t *__restrict__ e,
                                                           void *__restrict__ out) {
   constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
   constexpr int EB = KIND == HSUMMA_INT8_SLICES ? 1 : 2;
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restri
   for (int u = 0; u < 8; ++u) g[u].init(x[u], ei);
   uint8_t *base = reinterpret_cast<uint8_t *>(out) + (i * Kp + k0) * EB;
   const int64_t plane = M * Kp * EB;
+#pragma unroll
   for (int s = 1; s <= S; ++s) {
     int t[8];
 #pragma unroll
@@ -239,11 +241,11 @@ __global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restri
 // consecutive doubles of each of 16 rows of B.  One-dimensional grid, column
 // blocks fastest (neighbouring blocks read the same rows of B); any product
 // whose slices fit in memory has fewer than 2^31 blocks.
-template <int KIND>
+template <int KIND, int S>
 __global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restrict__ B,
                                                           int64_t ldb, int64_t K, int64_t N,
                                                           int64_t Kp,
-                                                          const int32_t *__restrict__ f, int S,
+                                                          const int32_t *__restrict__ f,
                                                           void *__restrict__ out) {
   constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
   constexpr int EB = KIND == HSUMMA_INT8_SLICES ? 1 : 2;
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restri
   for (int u = 0; u < 8; ++u) g[u].init(x[u], fj);
   uint8_t *base = reinterpret_cast<uint8_t *>(out) + (j * Kp + k0) * EB;
   const int64_t plane = N * Kp * EB;
+#pragma unroll
   for (int s = 1; s <= S; ++s) {
     int t[8];
 #pragma unroll
@@ -430,6 +433,37 @@ void recombine_dispatch(int S, dim3 grid, cudaStream_t s, const int32_t *D, int 
   }
 }
 
+// One slicing launch with the slice count as a template argument: rows of A
+// (ROWS) or columns of B; X is the operand, L its leading dimension, R its
+// rows (A) or columns (B), x the exponents.
+template <int KIND, bool ROWS, int S>
+void slices_launch(unsigned grid, cudaStream_t s, const double *X, int64_t L, int64_t R,
+                   int64_t K, int64_t Kp, const int32_t *x, void *out) {
+  if (ROWS)
+    slices_rows_kernel<KIND, S><<<grid, 256, 0, s>>>(X, L, R, K, Kp, x, out);
+  else
+    slices_cols_kernel<KIND, S><<<grid, 256, 0, s>>>(X, L, K, R, Kp, x, out);
+}
+
+template <int KIND, bool ROWS>
+void slices_dispatch(int S, unsigned grid, cudaStream_t s, const double *X, int64_t L,
+                     int64_t R, int64_t K, int64_t Kp, const int32_t *x, void *out) {
+  switch (S) {
+    case 1: slices_launch<KIND, ROWS, 1>(grid, s, X, L, R, K, Kp, x, out); break;
+    case 2: slices_launch<KIND, ROWS, 2>(grid, s, X, L, R, K, Kp, x, out); break;
+    case 3: slices_launch<KIND, ROWS, 3>(grid, s, X, L, R, K, Kp, x, out); break;
+    case 4: slices_launch<KIND, ROWS, 4>(grid, s, X, L, R, K, Kp, x, out); break;
+    case 5: slices_launch<KIND, ROWS, 5>(grid, s, X, L, R, K, Kp, x, out); break;
+    case 6: slices_launch<KIND, ROWS, 6>(grid, s, X, L, R, K, Kp, x, out); break;
+    case 7: slices_launch<KIND, ROWS, 7>(grid, s, X, L, R, K, Kp, x, out); break;
+    default:
+      // 8 slices exist for int8 only (W S <= 63; bf16 stops at 7)
+      if constexpr (KIND == HSUMMA_INT8_SLICES)
+        slices_launch<KIND, ROWS, 8>(grid, s, X, L, R, K, Kp, x, out);
+      break;
+  }
+}
+
 }  // namespace
 
 int launch_split_exponents(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
@@ -464,17 +498,17 @@ int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
   if (nA > 0) {
     const unsigned blocks = (unsigned)ceil_div(nA, 256);
     if (kind == HSUMMA_INT8_SLICES)
-      slices_rows_kernel<HSUMMA_INT8_SLICES><<<blocks, 256, 0, s>>>(A, lda, M, K, Kp, e, S, As);
+      slices_dispatch<HSUMMA_INT8_SLICES, true>(S, blocks, s, A, lda, M, K, Kp, e, As);
     else
-      slices_rows_kernel<HSUMMA_BF16_SLICES><<<blocks, 256, 0, s>>>(A, lda, M, K, Kp, e, S, As);
+      slices_dispatch<HSUMMA_BF16_SLICES, true>(S, blocks, s, A, lda, M, K, Kp, e, As);
     count_launch();
   }
   if (N > 0) {
     const unsigned grid = (unsigned)ncb;
     if (kind == HSUMMA_INT8_SLICES)
-      slices_cols_kernel<HSUMMA_INT8_SLICES><<<grid, 256, 0, s>>>(B, ldb, K, N, Kp, f, S, Bs);
+      slices_dispatch<HSUMMA_INT8_SLICES, false>(S, grid, s, B, ldb, N, K, Kp, f, Bs);
     else
-      slices_cols_kernel<HSUMMA_BF16_SLICES><<<grid, 256, 0, s>>>(B, ldb, K, N, Kp, f, S, Bs);
+      slices_dispatch<HSUMMA_BF16_SLICES, false>(S, grid, s, B, ldb, N, K, Kp, f, Bs);
     count_launch();
   }
   cudaError_t err = cudaGetLastError();
