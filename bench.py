@@ -506,10 +506,17 @@ def main():
     peaks = read_peaks()
     bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
     gemm_tflops = npairs * flops() / (dur[2] * 1e-3) / 1e12
+    burst = peaks.get("bf16_tflops") or 1900.0
+    # the tensor pipe's own rate at the clock sampled during the timed steps:
+    # 8192 bf16 flops per cycle and SM (hsumma_peak(TC05_*) measures it)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    pipe = 8192.0 * sms * clk["sm_mhz"] * 1e6 / 1e12 if clk.get("sm_mhz") else None
     roofline = {"bound": "tensor", "kernel": "bf16_pair_kernel",
                 "achieved": gemm_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": gemm_tflops / bf16_peak,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)",
+                "frac_of_burst": gemm_tflops / burst,
+                "frac_of_tensor_pipe_at_clock": gemm_tflops / pipe if pipe else None,
                 "algorithmic": f"{npairs} bf16 products x 2 n^3 per product stage "
                                f"({S} launches of the kernel, one per diagonal)",
                 "duration_ms": dur[2], "timed_stages": ncalls,
