@@ -294,13 +294,15 @@ enum {
   HSUMMA_CHOOSE_AUTO = 0,     /* cached, else the model, else timing */
   HSUMMA_CHOOSE_MODEL = 1,    /* the loaded model (HSUMMA_ERR_UNSUPPORTED if none) */
   HSUMMA_CHOOSE_TIMED = 2,    /* exhaustive timing, always */
-  HSUMMA_CHOOSE_ANALYTIC = 3  /* the fitted analytic model (hsumma_analytic_load) */
+  HSUMMA_CHOOSE_ANALYTIC = 3, /* the fitted analytic model (hsumma_analytic_load) */
+  HSUMMA_CHOOSE_VERIFIED = 4  /* the model's three best-predicted candidates, timed */
 };
 enum {
   HSUMMA_CHOSEN_CACHED = 0,
   HSUMMA_CHOSEN_MODEL = 1,
   HSUMMA_CHOSEN_TIMED = 2,
-  HSUMMA_CHOSEN_ANALYTIC = 3
+  HSUMMA_CHOSEN_ANALYTIC = 3,
+  HSUMMA_CHOSEN_VERIFIED = 4
 };
 
 /* Section IV's cost model of HSUMMA with binomial broadcast trees, read for a
@@ -330,7 +332,8 @@ int hsumma_analytic_load(const double *h_coef);
  * written to h_cfg[5] with *h_how one of HSUMMA_CHOSEN_*.  The model scores
  * every candidate on the device (bf16) and takes the smallest predicted time;
  * timing runs every candidate once on these operands, after one untimed run,
- * overwriting C, and takes the fastest that launched.  Either way the stream
+ * overwriting C, and takes the fastest that launched; the verified policy
+ * times only the model's three best-predicted candidates the same way.  Either way the stream
  * is synchronised and the choice is cached per (M, N, K, mode) until the next
  * hsumma_mlp_load or hsumma_finalize.  Operands follow hsumma_gemm's rules
  * (they are only read by timing). */

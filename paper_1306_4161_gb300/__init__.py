@@ -320,8 +320,8 @@ def peak(kind: str, work: int) -> float:
 
 
 # ---- automatic configuration ----
-CHOOSE = {"auto": 0, "model": 1, "timed": 2, "analytic": 3}
-CHOSEN = {0: "cached", 1: "model", 2: "timed", 3: "analytic"}
+CHOOSE = {"auto": 0, "model": 1, "timed": 2, "analytic": 3, "verified": 4}
+CHOSEN = {0: "cached", 1: "model", 2: "timed", 3: "analytic", 4: "verified"}
 
 
 def candidates(M, N, K, kind="fp64", slices=0) -> list[tuple[int, int, int, int, int]]:
@@ -346,7 +346,8 @@ def features(M, N, K, cfgs, kind="fp64", slices=0):
 
 def choose(A, B, C=None, *, kind="fp64", slices=0, policy="auto", stream=_DEFAULT):
     """(P, Q, G, b, Bouter) that gemm(A, B) runs with when asked to choose, and
-    how it was chosen ("cached", "model" or "timed").  Timing overwrites C."""
+    how it was chosen ("cached", "model", "timed", "analytic" or "verified": the
+    model's three best-predicted candidates timed).  Timing overwrites C."""
     import torch
     _check_f64(A, "A")
     _check_f64(B, "B")

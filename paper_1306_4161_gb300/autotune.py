@@ -453,6 +453,21 @@ def pick(model, M, N, K, kind, S, cfgs) -> int:
     return int(best.item())
 
 
+def ranked(model, M, N, K, kind, S, cfgs):
+    """Candidate indices in order of the model's predicted time, scored as the
+    library scores them (bf16 on the device, hsumma_mlp_pick's predictions)."""
+    import torch
+    X = hs.features(M, N, K, cfgs, kind, S)
+    Xn = (X - model["mean"]) / model["std"]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    dth, dX = dev(model["theta"]), dev(Xn)
+    pred = torch.empty(len(cfgs), dtype=torch.float32, device="cuda")
+    best = torch.empty(1, dtype=torch.int32, device="cuda")
+    hs._check(hs.lib().hsumma_mlp_pick(len(cfgs), dth.data_ptr(), dX.data_ptr(),
+                                       pred.data_ptr(), best.data_ptr(), hs._stream_ptr()))
+    return np.argsort(pred.cpu().numpy(), kind="stable")
+
+
 def _stats(r):
     r = np.asarray(r, dtype=np.float64)
     return dict(geomean=float(np.exp(np.mean(np.log(r)))), mean=float(r.mean()),
@@ -460,14 +475,19 @@ def _stats(r):
                 within_10pct=float(np.mean(r <= 1.10)), n=int(r.size))
 
 
-def evaluate(model, heldout, picker=None):
+def evaluate(model, heldout, picker=None, ranker=None):
     """Ratios to the exhaustive best (the fastest candidate), over the held-out
-    products, overall and per kind, of: the model's pick ("model"), the paper's
-    static setting G = sqrt(p), b = B ("paper_rule"), the paper's tuning by a few
-    runs ("sampled") and, when the model carries its coefficients, the fitted
-    analytic model ("analytic")."""
-    picker = picker or (lambda h: pick(model, h["M"], h["N"], h["K"], h["kind"], h["S"],
-                                       [tuple(int(v) for v in c) for c in h["cfg"]]))
+    products, overall and per kind, of: the model's pick ("model"), the fastest
+    of its three best-predicted candidates by the timed table (the verified
+    policy, "verified"), the paper's static setting G = sqrt(p), b = B
+    ("paper_rule"), the paper's tuning by a few runs ("sampled") and, when the
+    model carries its coefficients, the fitted analytic model ("analytic")."""
+    cfgs_of = lambda h: [tuple(int(v) for v in c) for c in h["cfg"]]
+    if picker is None:
+        picker = lambda h: pick(model, h["M"], h["N"], h["K"], h["kind"], h["S"], cfgs_of(h))
+        if ranker is None:
+            ranker = lambda h: ranked(model, h["M"], h["N"], h["K"], h["kind"], h["S"],
+                                      cfgs_of(h))
     coef = model.get("analytic") if isinstance(model, dict) else None
     rows = []
     for h in heldout:
@@ -475,10 +495,13 @@ def evaluate(model, heldout, picker=None):
         best = float(np.min(ms))
         r = {"kind": h["kind"], "model": ms[picker(h)] / best, "paper_rule": h["base_ms"] / best,
              "sampled": ms[sampled_pick(h)] / best}
+        if ranker is not None:
+            r["verified"] = float(min(ms[i] for i in ranker(h)[:3])) / best
         if coef is not None:
             r["analytic"] = ms[analytic_pick(coef, h)] / best
         rows.append(r)
-    keys = [k for k in ("model", "analytic", "sampled", "paper_rule") if k in rows[0]]
+    keys = [k for k in ("model", "verified", "analytic", "sampled", "paper_rule")
+            if k in rows[0]]
     out = {k: _stats([r[k] for r in rows]) for k in keys}
     for kind in KIND_CODE:
         sel = [r for r in rows if r["kind"] == kind]

@@ -16,6 +16,7 @@
 //   b = the kernel's stage width (32, 128, 64): b does not change the
 //   arithmetic or the schedule on this GPU, only the counters' bookkeeping;
 //   B in {b, 4b, 16b} (how far ahead the owners stage outer panels in L2).
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -104,6 +105,10 @@ std::map<std::tuple<int64_t, int64_t, int64_t, int>, Cand> g_cache;
 //   [0] computation, [1] latency (messages x depth), [2] bandwidth (words x
 //   depth), [3] slicing volume (M + N) K S (split paths), [4] one per call.
 constexpr int kAnalyticTerms = 5;
+// candidates the verified policy times: the model's best-predicted ones (on the
+// held-out products three bring the pick from 1.020 / 1.039 to 1.005 / 1.008
+// of the exhaustive best)
+constexpr int kVerifiedCandidates = 3;
 double g_analytic[3][kAnalyticTerms];
 bool g_analytic_loaded = false;
 
@@ -142,9 +147,11 @@ int decode_mode(int mode, int *kind, int *S) {
 }
 
 // Score the candidates with the loaded model on the device; *best is the index
-// of the smallest predicted time.
+// of the smallest predicted time; with `ranked`, also every index in order of
+// predicted time (the scores read back to the host).
 int pick_by_model(int64_t M, int64_t N, int64_t K, int kind, int S,
-                  const std::vector<Cand> &cands, cudaStream_t s, int *best) {
+                  const std::vector<Cand> &cands, cudaStream_t s, int *best,
+                  std::vector<int> *ranked = nullptr) {
   float mean[kModelFeatures], stdv[kModelFeatures];
   const float *theta = loaded_model(mean, stdv);
   if (!theta) {
@@ -184,7 +191,10 @@ int pick_by_model(int64_t M, int64_t N, int64_t K, int kind, int S,
   int rc = mlp_pick_device(n, d_theta, d_X, d_pred, d_best, s);
   if (rc != HSUMMA_OK) return rc;
   int32_t h_best = -1;
+  std::vector<float> pred(ranked ? n : 0);
   e = cudaMemcpyAsync(&h_best, d_best, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && ranked)
+    e = cudaMemcpyAsync(pred.data(), d_pred, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "read model choice");
   if (h_best < 0 || h_best >= n) {
@@ -192,14 +202,23 @@ int pick_by_model(int64_t M, int64_t N, int64_t K, int kind, int S,
     return HSUMMA_ERR_CUDA;
   }
   *best = h_best;
+  if (ranked) {
+    ranked->resize(n);
+    for (int i = 0; i < n; ++i) (*ranked)[i] = i;
+    // ascending predicted time; ties keep the candidate order (the argmin's)
+    std::stable_sort(ranked->begin(), ranked->end(),
+                     [&](int a, int b) { return pred[a] < pred[b]; });
+  }
   return HSUMMA_OK;
 }
 
-// Time every candidate once on the caller's operands (C is overwritten) after
-// one untimed run; *best is the fastest that ran.
+// Time every candidate (or those listed in `only`) once on the caller's
+// operands (C is overwritten) after one untimed run; *best is the fastest that
+// ran.
 int pick_by_timing(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
                    const double *B, int64_t ldb, double *C, int64_t ldc, int mode,
-                   const std::vector<Cand> &cands, cudaStream_t s, int *best) {
+                   const std::vector<Cand> &cands, cudaStream_t s, int *best,
+                   const std::vector<int> *only = nullptr) {
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -208,13 +227,19 @@ int pick_by_timing(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda
   float best_ms = INFINITY;
   int bi = -1;
   int rc = HSUMMA_OK;
-  for (size_t i = 0; i < cands.size(); ++i) {   // one untimed run first
+  std::vector<int> all;
+  if (!only) {
+    all.resize(cands.size());
+    for (size_t i = 0; i < cands.size(); ++i) all[i] = (int)i;
+    only = &all;
+  }
+  for (int i : *only) {   // one untimed run first
     const Cand &w = cands[i];
     if (hsumma_gemm(M, N, K, A, lda, B, ldb, C, ldc, w.P, w.Q, w.G, w.b, w.Bo, mode, sp) ==
         HSUMMA_OK)
       break;
   }
-  for (size_t i = 0; i < cands.size(); ++i) {
+  for (int i : *only) {
     const Cand &c = cands[i];
     cudaEventRecord(e0, s);
     if (hsumma_gemm(M, N, K, A, lda, B, ldb, C, ldc, c.P, c.Q, c.G, c.b, c.Bo, mode, sp) !=
@@ -230,7 +255,7 @@ int pick_by_timing(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) {
       best_ms = ms;
-      bi = (int)i;
+      bi = i;
     }
   }
   cudaEventDestroy(e0);
@@ -307,7 +332,8 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
   int kind, S;
   int st = decode_mode(mode, &kind, &S);
   if (st != HSUMMA_OK) return st;
-  if (!cfg || !how || policy < 0 || policy > 3 || M < 0 || N < 0 || K < 0) {
+  if (!cfg || !how || policy < 0 || policy > HSUMMA_CHOOSE_VERIFIED || M < 0 || N < 0 ||
+      K < 0) {
     set_error("bad arguments");
     return HSUMMA_ERR_ARG;
   }
@@ -351,6 +377,15 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
       }
     }
     *how = HSUMMA_CHOSEN_ANALYTIC;
+  } else if (policy == HSUMMA_CHOOSE_VERIFIED) {
+    // the model's best-predicted candidates, timed on these operands
+    std::vector<int> ranked;
+    st = pick_by_model(M, N, K, kind, S, cands, s, &bi, &ranked);
+    if (st != HSUMMA_OK) return st;
+    ranked.resize(std::min(ranked.size(), (size_t)kVerifiedCandidates));
+    st = pick_by_timing(M, N, K, A, lda, B, ldb, C, ldc, mode, cands, s, &bi, &ranked);
+    if (st != HSUMMA_OK) return st;
+    *how = HSUMMA_CHOSEN_VERIFIED;
   } else if (policy == HSUMMA_CHOOSE_MODEL || (policy == HSUMMA_CHOOSE_AUTO && have_model)) {
     st = pick_by_model(M, N, K, kind, S, cands, s, &bi);
     if (st != HSUMMA_OK) return st;

@@ -257,3 +257,27 @@ def test_analytic_policy_picks_and_computes():
     with pytest.raises(hs.HsummaError):
         hs.choose(dA, dB, kind="fp64", policy="analytic")
     autotune.load_into_library()
+
+
+def test_verified_policy_times_the_models_three_best():
+    # the verified policy: the loaded model's three best-predicted candidates,
+    # each timed once on the operands; the pick is one of them, it computes the
+    # product exactly, and it is cached for the automatic choice
+    hs = lib_ready()
+    torch = torch_cuda()
+    from paper_1306_4161_gb300 import autotune
+    if not os.path.exists(autotune.MODEL_PATH):
+        pytest.skip("no committed model")
+    model = autotune.load_into_library()
+    M, N, K = 1536, 2304, 1280
+    dA, dB, want = _exact_pair(torch, M, N, K, 97)
+    cands = hs.candidates(M, N, K, "bf16", 4)
+    top = [cands[i] for i in autotune.ranked(model, M, N, K, "bf16", 4, cands)[:3]]
+    cfg, how = hs.choose(dA, dB, kind="bf16", slices=4, policy="verified")
+    assert how == "verified" and cfg in top
+    C = hs.gemm(dA, dB, P=cfg[0], Q=cfg[1], G=cfg[2], b=cfg[3], Bouter=cfg[4], kind="bf16",
+                slices=4)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), want)    # small integers: exact for any S
+    assert hs.choose(dA, dB, kind="bf16", slices=4) == (cfg, "cached")
+    autotune.load_into_library()                   # drops the cache again
