@@ -11,6 +11,8 @@
 // 2^w t does not change a round-half-to-even decision).
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "internal.h"
 #include "ptx.cuh"
 #include "../../include/hsumma.h"
@@ -104,62 +106,91 @@ __global__ void exponents_cols_kernel(const double *__restrict__ B, int64_t ldb,
 }
 
 // The digits of one value, slice by slice.  With F = floor(|x| 2^-e 2^64)
-// (below 2^63, since the exponent scan makes |x| 2^-e < 1/2) and Y_s =
-// RN(|x| 2^-e 2^(W s)) (ties to even), digit s is t_s = Y_s - 2^W Y_(s-1).
-// Writing Y_s = q_s + c_s with q_s = floor(F / 2^(p+1)), p = 63 - W s, and c_s
-// the rounding increment, and since q_(s-1) = floor(q_s / 2^W):
-//   t_s = (q_s mod 2^W) + c_s - 2^W c_(s-1),
-// where q_s mod 2^W is the W-bit field of F above bit p and
-//   c_s = (bit p of F) and (any lower bit of F, or a bit dropped below F,
-//                           or bit p + 1 of F)          (round half to even).
-// Bit p is the same for every value of a slice, so a digit costs a shift, a
-// comparison, a few masks and no branch ("any lower bit" is tz < p, tz the
-// trailing zero count of F, -1 when bits were dropped below F).  W S <= 63
-// (bf16: S <= 7; int8: S <= 8).  A negative x has the negated digits
-// (rounding to nearest is symmetric).
+// (below 2^63, since the exponent scan makes |x| 2^-e < 1/2) and
+// Y_s = RN(|x| 2^-e 2^(W s)) (ties to even), digit s is t_s = Y_s - 2^W Y_(s-1).
+// Y_s is F / 2^(p+1), p = 63 - W s, rounded to nearest even; the bits below the
+// rounding bit p only matter as "any of them set", so
+//   Y_s = (F + 2^p - 1 + bit p+1 of F) >> (p + 1)
+// provided that a bit dropped below F (a value far below the row's largest)
+// still counts: it is or-ed into bit 0 of F, which is never a digit or rounding
+// bit (p >= 7, since W S <= 56).  F is held as two 32-bit words Fh:Fl.  For
+// p >= 33 the low word only matters as that same "any bit" flag, so it is folded
+// into bit 0 of the high word (Fhs) and the digit takes one 32-bit add and shift;
+// for p <= 31 the add runs over both words.  Y_s and 2^W Y_(s-1) are only needed
+// modulo 2^32, since their difference is small.  A negative x has the negated
+// digits (rounding to nearest is symmetric).  Bit p is the same for every value
+// of a slice, so a digit costs a few integer instructions and no branch.
 struct DigitGen {
-  unsigned long long F;
-  int tz;            // trailing zeros of F; -1 if |x| 2^-e 2^64 is not an integer; 64 if 0
-  bool neg;
-  int cprev;         // c_(s-1)
+  uint32_t Fh, Fl;   // F = Fh 2^32 + Fl, with dropped bits or-ed into bit 0 of Fl
+  uint32_t Fhs;      // Fh with "Fl != 0" or-ed into bit 0
+  uint32_t Yprev;    // Y_(s-1) modulo 2^32
+  int sgn;           // +1 or -1
 
-  __device__ __forceinline__ void init(double x, int e) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    neg = (bits >> 63) != 0;
-    const int E = (int)((bits >> 52) & 0x7FF);
-    unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
-    int lsb;        // binary exponent of m's least significant bit
-    if (E > 0) {
-      m |= 1ull << 52;
-      lsb = E - 1075;
+  // eb = e + 1011: then |x| 2^-e 2^64 = m 2^sh with sh = max(E, 1) - eb, for
+  // the significand m (hidden bit included) and the biased exponent E of x.
+  __device__ __forceinline__ void init(double x, int eb) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int E = (int)((hi >> 20) & 0x7FFu);
+    const uint32_t mhi = (hi & 0xFFFFFu) | (E ? 0x100000u : 0u);
+    const int sh = max(E, 1) - eb;
+    sgn = ((int)hi >> 31) | 1;
+    if ((unsigned)sh < 32u) {
+      // every normal value of a finite row (sh <= 10): nothing is dropped
+      Fh = __funnelshift_l(lo, mhi, (unsigned)sh);
+      Fl = lo << sh;
     } else {
-      lsb = -1074;
+      const uint2 F = shift_rare(mhi, lo, sh);
+      Fh = F.x;
+      Fl = F.y;
     }
-    const int sh = lsb - e + 64;     // |x| 2^-e 2^64 = m 2^sh
-    bool sticky;                     // bits of m dropped below F
-    if (sh >= 0) {
-      F = m << (sh < 63 ? sh : 63);  // exact (the guard only keeps the shift defined)
-      sticky = false;
-    } else if (sh > -64) {
-      F = m >> -sh;
-      sticky = (m << (64 + sh)) != 0;
-    } else {
-      F = 0;
-      sticky = m != 0;
-    }
-    tz = sticky ? -1 : (F ? __ffsll((long long)F) - 1 : 64);
-    cprev = 0;
+    Fhs = Fh | (Fl != 0u ? 1u : 0u);
+    Yprev = 0u;
   }
 
-  // digit s for p = 63 - W s (the same for every value)
-  template <int W>
-  __device__ __forceinline__ int next(int p) {
-    const uint32_t win = (uint32_t)(F >> p);    // bit 0: rounding bit; bits 1..W: field
-    const int field = (int)((win >> 1) & ((1u << W) - 1u));
-    const int c = (int)(win & 1u) & ((int)(tz < p) | (field & 1));
-    const int t = field + c - (cprev << W);
-    cprev = c;
-    return neg ? -t : t;
+  // sh < 0 (values more than 2^11 below the row's largest) or sh >= 32 (tiny
+  // subnormals, whose significand then fits the low word; also whatever a
+  // non-finite input gives, which the exponent scan has reported): returns
+  // (Fh, Fl) with the dropped bits or-ed into bit 0 of Fl
+  static __device__ __noinline__ uint2 shift_rare(uint32_t mhi, uint32_t lo, int sh) {
+    uint32_t h, l, dropped;
+    if (sh >= 32) {
+      h = __funnelshift_lc(0u, lo, (unsigned)(sh - 32));    // lo << (sh - 32), 0 past 63
+      l = 0u;
+      dropped = 0u;
+    } else if (sh > -32) {
+      const unsigned r = (unsigned)(-sh);                   // 1..31
+      h = mhi >> r;
+      l = __funnelshift_r(lo, mhi, r);
+      dropped = lo << (32u - r);
+    } else if (sh > -64) {
+      const unsigned r = (unsigned)(-sh) - 32u;             // 0..31
+      h = 0u;
+      l = mhi >> r;
+      dropped = lo | __funnelshift_lc(0u, mhi, 32u - r);    // the low r bits of mhi
+    } else {
+      h = 0u;
+      l = 0u;
+      dropped = mhi | lo;
+    }
+    return make_uint2(h, l | (dropped != 0u ? 1u : 0u));
+  }
+
+  // the signed digit s (1-based); W S <= 56, so p = 63 - W s >= 7
+  template <int W, int s>
+  __device__ __forceinline__ int next() {
+    constexpr int p = 63 - W * s;
+    static_assert(p >= 7, "at most 56 digit bits");
+    uint32_t Y;
+    if constexpr (p >= 33) {
+      constexpr int q = p - 32;
+      Y = (Fhs + ((1u << q) - 1u) + ((Fhs >> (q + 1)) & 1u)) >> (q + 1);
+    } else {
+      const unsigned long long F = ((unsigned long long)Fh << 32) | Fl;
+      Y = (uint32_t)((F + ((1ull << p) - 1ull) + ((F >> (p + 1)) & 1ull)) >> (p + 1));
+    }
+    const int t = (int)(Y - (Yprev << W));
+    Yprev = Y;
+    return t * sgn;
   }
 };
 
@@ -173,11 +204,10 @@ __device__ __forceinline__ float small_int_to_float(int t) {
 template <int KIND>
 __device__ __forceinline__ void store8(void *dst, const int (&t)[8]) {
   if (KIND == HSUMMA_INT8_SLICES) {
+    // low bytes of t[0..3] (t[4..7]) by byte permutes: two pairs, then the pairs
     uint2 v;
-    v.x = (uint32_t)(uint8_t)t[0] | ((uint32_t)(uint8_t)t[1] << 8) |
-          ((uint32_t)(uint8_t)t[2] << 16) | ((uint32_t)(uint8_t)t[3] << 24);
-    v.y = (uint32_t)(uint8_t)t[4] | ((uint32_t)(uint8_t)t[5] << 8) |
-          ((uint32_t)(uint8_t)t[6] << 16) | ((uint32_t)(uint8_t)t[7] << 24);
+    v.x = __byte_perm(__byte_perm(t[0], t[1], 0x0040), __byte_perm(t[2], t[3], 0x0040), 0x5410);
+    v.y = __byte_perm(__byte_perm(t[4], t[5], 0x0040), __byte_perm(t[6], t[7], 0x0040), 0x5410);
     *reinterpret_cast<uint2 *>(dst) = v;
   } else {
     uint4 v;
@@ -189,6 +219,19 @@ __device__ __forceinline__ void store8(void *dst, const int (&t)[8]) {
       w[h] = *reinterpret_cast<uint32_t *>(&b);
     }
     *reinterpret_cast<uint4 *>(dst) = v;
+  }
+}
+
+// Slices s..S of eight values, slice s at base + (s - 1) plane (the slice
+// index is a template argument, so each digit's bit position is a constant).
+template <int KIND, int W, int s, int S>
+__device__ __forceinline__ void store_digits(DigitGen (&g)[8], uint8_t *base, int64_t plane) {
+  if constexpr (s <= S) {
+    int t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = g[u].template next<W, s>();
+    store8<KIND>(base + (s - 1) * plane, t);
+    store_digits<KIND, W, s + 1, S>(g, base, plane);
   }
 }
 
@@ -206,7 +249,7 @@ __global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restri
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= M * groups) return;
   const int64_t i = gid / groups, k0 = (gid % groups) * 8;
-  const int ei = e[i];
+  const int eb = e[i] + 1011;
   double x[8];
   const double *a = A + i * lda + k0;
   if (k0 + 7 < K && (reinterpret_cast<uintptr_t>(a) & 15) == 0) {
@@ -222,16 +265,9 @@ __global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restri
   }
   DigitGen g[8];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) g[u].init(x[u], ei);
+  for (int u = 0; u < 8; ++u) g[u].init(x[u], eb);
   uint8_t *base = reinterpret_cast<uint8_t *>(out) + (i * Kp + k0) * EB;
-  const int64_t plane = M * Kp * EB;
-#pragma unroll
-  for (int s = 1; s <= S; ++s) {
-    int t[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) t[u] = g[u].next<W>(63 - W * s);
-    store8<KIND>(base + (s - 1) * plane, t);
-  }
+  store_digits<KIND, W, 1, S>(g, base, M * Kp * EB);
 }
 
 // B slices, transposed: Bs[t][j][k].  A block covers 32 columns x 64 k; warp
@@ -255,22 +291,21 @@ __global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restri
   const int64_t j = (int64_t)jb * 32 + (w & 1) * 16 + (lane >> 1);
   const int64_t k0 = (int64_t)kb * 64 + (w >> 1) * 16 + (lane & 1) * 8;
   if (j >= N) return;
-  const int fj = f[j];
+  const int eb = f[j] + 1011;
   double x[8];
+  const double *b = B + k0 * ldb + j;
+  if (k0 + 7 < K) {
 #pragma unroll
-  for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? B[(k0 + u) * ldb + j] : 0.0;
+    for (int u = 0; u < 8; ++u) x[u] = __ldg(b + u * ldb);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? __ldg(b + u * ldb) : 0.0;
+  }
   DigitGen g[8];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) g[u].init(x[u], fj);
+  for (int u = 0; u < 8; ++u) g[u].init(x[u], eb);
   uint8_t *base = reinterpret_cast<uint8_t *>(out) + (j * Kp + k0) * EB;
-  const int64_t plane = N * Kp * EB;
-#pragma unroll
-  for (int s = 1; s <= S; ++s) {
-    int t[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) t[u] = g[u].next<W>(63 - W * s);
-    store8<KIND>(base + (s - 1) * plane, t);
-  }
+  store_digits<KIND, W, 1, S>(g, base, N * Kp * EB);
 }
 
 // RN(X 2^k) for a 128-bit integer X, ties to even, subnormals and overflow
@@ -315,13 +350,12 @@ __device__ __noinline__ double round_scaled_i128(__int128 X, int k) {
   return __longlong_as_double((long long)bits);
 }
 
-// The same for X that fits in 64 bits and a normal result (the common case):
-// 64-bit integer work only; anything else goes to the general routine.
-__device__ __forceinline__ double round_scaled(__int128 X, int k) {
-  const long long lo = (long long)X;
-  if ((__int128)lo == X && lo != 0) {
-    const bool neg = lo < 0;
-    const unsigned long long m = neg ? 0ull - (unsigned long long)lo : (unsigned long long)lo;
+// The same for a 64-bit X: 64-bit integer work when the result is normal (the
+// common case); anything else goes to the general routine.
+__device__ __forceinline__ double round_scaled64(long long X, int k) {
+  if (X != 0) {
+    const bool neg = X < 0;
+    const unsigned long long m = neg ? 0ull - (unsigned long long)X : (unsigned long long)X;
     const int nb = 64 - __clzll((long long)m);
     const int drop = nb - 53;
     unsigned long long q;
@@ -345,6 +379,12 @@ __device__ __forceinline__ double round_scaled(__int128 X, int k) {
       return __longlong_as_double((long long)bits);
     }
   }
+  return round_scaled_i128((__int128)X, k);
+}
+
+__device__ __forceinline__ double round_scaled(__int128 X, int k) {
+  const long long lo = (long long)X;
+  if ((__int128)lo == X) return round_scaled64(lo, k);
   return round_scaled_i128(X, k);
 }
 
@@ -355,6 +395,11 @@ __device__ __forceinline__ double round_scaled(__int128 X, int k) {
 // segment plane of every diagonal is loaded before any arithmetic, so that
 // all S loads of a thread are in flight at once; further segment planes (K
 // beyond one segment) follow one diagonal at a time.
+// With one segment plane per diagonal, X fits in 64 bits whenever |D_2| <= T2:
+// the host derives T2 from the int32 range of the other diagonals, so that
+// |D_2| 2^(w (S-1)) + sum_(d>2) 2^31 2^(w (S+1-d)) < 2^63 (every partial sum of
+// Horner's rule is bounded by the same sum).  The diagonal sums the products
+// give are far inside that bound; other values take the 128-bit path.
 // (four resident blocks per SM keep more loads in flight; the kernels of 7 and
 // 8 slices need more than the 64 registers that leaves)
 template <int W, int S>
@@ -362,7 +407,8 @@ __global__ void __launch_bounds__(256, S <= 6 ? 4 : 3) recombine_kernel(const in
                                                         int64_t M, int64_t N,
                                                         const int32_t *__restrict__ e,
                                                         const int32_t *__restrict__ f,
-                                                        double *__restrict__ C, int64_t ldc) {
+                                                        double *__restrict__ C, int64_t ldc,
+                                                        int64_t T2) {
   const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   const int64_t i = blockIdx.y;
   if (j0 >= N) return;
@@ -381,24 +427,37 @@ __global__ void __launch_bounds__(256, S <= 6 ? 4 : 3) recombine_kernel(const in
   int first[S][4];
 #pragma unroll
   for (int d = 0; d < S; ++d) load4(D + (int64_t)(d * nseg) * plane + off, first[d]);
-  __int128 X[4] = {0, 0, 0, 0};
-#pragma unroll
-  for (int d = 0; d < S; ++d) {
-    long long Dd[4] = {first[d][0], first[d][1], first[d][2], first[d][3]};
-    // the segment planes of a diagonal sum exactly in 64 bits
-    for (int g = 1; g < nseg; ++g) {
-      int v[4];
-      load4(D + (int64_t)(d * nseg + g) * plane + off, v);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) Dd[u] += v[u];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) X[u] = (X[u] << W) + (__int128)Dd[u];
-  }
   const int k = e[i] - W * (S + 1);
   double out[4];
+  bool narrow = nseg == 1;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) out[u] = j0 + u < N ? round_scaled(X[u], k + f[j0 + u]) : 0.0;
+  for (int u = 0; u < 4; ++u) narrow = narrow && llabs((long long)first[0][u]) <= T2;
+  if (narrow) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      unsigned long long X = (unsigned long long)(long long)first[0][u];
+#pragma unroll
+      for (int d = 1; d < S; ++d) X = (X << W) + (unsigned long long)(long long)first[d][u];
+      out[u] = j0 + u < N ? round_scaled64((long long)X, k + f[j0 + u]) : 0.0;
+    }
+  } else {
+    __int128 X[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < S; ++d) {
+      long long Dd[4] = {first[d][0], first[d][1], first[d][2], first[d][3]};
+      // the segment planes of a diagonal sum exactly in 64 bits
+      for (int g = 1; g < nseg; ++g) {
+        int v[4];
+        load4(D + (int64_t)(d * nseg + g) * plane + off, v);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) Dd[u] += v[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) X[u] = (X[u] << W) + (__int128)Dd[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out[u] = j0 + u < N ? round_scaled(X[u], k + f[j0 + u]) : 0.0;
+  }
   double *dst = C + i * ldc + j0;
   if (full && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
     reinterpret_cast<double2 *>(dst)[0] = make_double2(out[0], out[1]);
@@ -410,10 +469,24 @@ __global__ void __launch_bounds__(256, S <= 6 ? 4 : 3) recombine_kernel(const in
   }
 }
 
+// T2 of the kernel above: the largest |D_2| for which X stays below 2^63 when
+// every other diagonal holds any int32; 2^31 admits every int32 (S = 1), and
+// -1 admits none (the other diagonals alone can pass 2^63: bf16 with S >= 6).
+int64_t recombine_narrow_bound(int W, int S) {
+  if (S <= 1) return 2147483648LL;
+  long double rest = 0.0L;
+  for (int d = 3; d <= S + 1; ++d) rest += ldexpl(2147483648.0L, W * (S + 1 - d));
+  const long double room = ldexpl(1.0L, 63) - 1.0L - rest;
+  if (room < 0.0L) return -1;
+  const long double t = floorl(room / ldexpl(1.0L, W * (S - 1)));
+  return t >= 2147483648.0L ? 2147483648LL : (int64_t)t;
+}
+
 template <int W, int S>
 void recombine_launch(dim3 grid, cudaStream_t s, const int32_t *D, int nseg, int64_t M,
                       int64_t N, const int32_t *e, const int32_t *f, double *C, int64_t ldc) {
-  recombine_kernel<W, S><<<grid, 256, 0, s>>>(D, nseg, M, N, e, f, C, ldc);
+  static const int64_t T2 = recombine_narrow_bound(W, S);
+  recombine_kernel<W, S><<<grid, 256, 0, s>>>(D, nseg, M, N, e, f, C, ldc, T2);
   count_launch();
 }
 

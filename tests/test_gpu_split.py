@@ -53,6 +53,56 @@ def test_exponents_and_slices_bit_exact(kind):
     assert np.all(got_b[:, :, K:] == 0)
 
 
+def bit_patterns(M, K, seed):
+    """Rows mixing the cases the digit arithmetic treats apart: values far below
+    the row's largest (bits dropped below the 64-bit fixed-point form), raw
+    random finite bit patterns, subnormals, exact ties at digit boundaries,
+    signed zeros, rows scaled into the subnormal range and all-zero rows."""
+    rng = np.random.default_rng(seed)
+    A = np.empty((M, K))
+    for i in range(M):
+        c = rng.random(K)
+        row = rng.uniform(-1, 1, K) * np.exp2(rng.integers(-80, 3, K).astype(float))
+        raw = rng.integers(0, 2 ** 63, K, dtype=np.int64).view(np.float64)
+        raw[~np.isfinite(raw)] = 1.0
+        raw *= np.where(rng.random(K) < 0.5, -1.0, 1.0)
+        sub = (rng.integers(0, 2 ** 52, K, dtype=np.int64) >> rng.integers(0, 52, K)).view(np.float64)
+        tie = (rng.integers(1, 600, K) + 0.5) * np.exp2(rng.integers(-70, -8, K).astype(float))
+        special = rng.choice(np.array([0.0, -0.0, 0.5 - 2.0 ** -60, 2.0 ** -1074, -(2.0 ** -1074),
+                                       2.0 ** -1022]), K)
+        row = np.where(c < 0.55, row, np.where(c < 0.65, raw, np.where(c < 0.75, sub, np.where(
+            c < 0.9, tie * np.sign(rng.uniform(-1, 1, K)), special))))
+        if i % 7 == 3:
+            row = row * 2.0 ** -1000
+        if i % 11 == 5:
+            row[:] = 0.0
+        A[i] = row
+    return A
+
+
+@pytest.mark.parametrize("kind", ["bf16", "int8"])
+def test_slices_bit_patterns(kind):
+    # every branch of the slicing arithmetic (shifts by less than 0, 0..31 and
+    # 32 or more bits; dropped and sticky bits; ties) against the oracle's digits
+    hs = lib_ready()
+    torch = torch_cuda()
+    M, N, K = 96, 80, 200
+    A = bit_patterns(M, K, 41)
+    B = bit_patterns(N, K, 42).T.copy()
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    e, f = hs.split_exponents(dA, dB)
+    S = 8 if kind == "int8" else 7
+    As, Bs = hs.split_slices(dA, dB, e, f, kind, S)
+    hs.sync()
+    w = split.SLICE_BITS[kind]
+    e_o, f_o = split.row_exponents(A), split.col_exponents(B)
+    assert np.array_equal(e.cpu().numpy(), e_o) and np.array_equal(f.cpu().numpy(), f_o)
+    got_a = As.float().cpu().numpy()[:, :, :K]
+    got_b = Bs.float().cpu().numpy()[:, :, :K]
+    assert np.array_equal(got_a, split.split_rows(A, e_o, S, w))
+    assert np.array_equal(got_b, np.transpose(split.split_cols(B, f_o, S, w), (0, 2, 1)))
+
+
 def test_nonfinite_is_reported():
     hs = lib_ready()
     torch = torch_cuda()
@@ -147,6 +197,34 @@ def test_recombine_special_values():
     assert np.array_equal(np.isinf(got), np.isinf(want))
     fin = np.isfinite(want)
     assert np.array_equal(got[fin], want[fin])
+
+
+@pytest.mark.parametrize("kind,S", [("bf16", 5), ("bf16", 6), ("int8", 6), ("int8", 7)])
+def test_recombine_64_and_128_bit_paths(kind, S):
+    # one segment plane per diagonal (K = 64): most entries take the 64-bit
+    # path; |D_2| near 2^31 and the int32 extremes in the other diagonals force
+    # the 128-bit one (bf16 S = 6 and int8 S = 7 always take it), alone and
+    # next to 64-bit entries in the same group of four columns
+    hs = lib_ready()
+    torch = torch_cuda()
+    M, N = 9, 37
+    rng = np.random.default_rng(S * 10 + len(kind))
+    D = rng.integers(-2 ** 24, 2 ** 24, size=(S, 1, M, N)).astype(np.int32)
+    D[0, 0, 1, 5] = 2 ** 31 - 1
+    D[0, 0, 2, 0:4] = -(2 ** 31)
+    D[0, 0, 3, 9] = 2 ** 28 + 12345
+    D[1:, 0, 4, :] = 2 ** 31 - 1
+    D[1:, 0, 5, :] = -(2 ** 31)
+    D[0, 0, 6, 12:16] = 2 ** 27 - 1
+    e = rng.integers(-40, 40, M).astype(np.int32)
+    f = rng.integers(-40, 40, N).astype(np.int32)
+    dD = torch.from_numpy(D).cuda()
+    de, df = torch.from_numpy(e).cuda(), torch.from_numpy(f).cuda()
+    C = hs.split_recombine(dD, de, df, M, N, 64, kind, S)
+    hs.sync()
+    w = split.SLICE_BITS[kind]
+    want = split.recombine({d: D[d - 2, 0].astype(np.int64) for d in range(2, S + 2)}, e, f, S, w)
+    assert np.array_equal(C.cpu().numpy(), want)
 
 
 def test_accuracy_within_bound_bf16_S5():
