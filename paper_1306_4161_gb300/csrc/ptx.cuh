@@ -194,6 +194,21 @@ __device__ __forceinline__ void cluster_sync() {
           : "memory");
 }
 
+// 64-bit load from the shared memory of cluster CTA `rank` at the address that
+// `addr` has in this CTA.
+__device__ __forceinline__ unsigned long long ld_shared_cluster_u64(uint32_t addr,
+                                                                  uint32_t rank) {
+  unsigned long long v;
+  asm volatile(
+      "{\n\t.reg .b32 ra;\n\t"
+      "mapa.shared::cluster.u32 ra, %1, %2;\n\t"
+      "ld.shared::cluster.u64 %0, [ra];\n\t}"
+      : "=l"(v)
+      : "r"(addr), "r"(rank)
+      : "memory");
+  return v;
+}
+
 // Named barrier among `nthreads` threads (a multiple of 32).
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");

@@ -69,22 +69,29 @@ __global__ void exponents_rows_kernel(const double *__restrict__ A, int64_t lda,
   }
 }
 
-// columns of B: a block covers 64 columns (32 lanes x 2), its 8 warps split k
+// columns of B: a block covers 64 columns (32 lanes x 2) and one of the
+// gridDim.y slices of k, its 8 warps splitting that slice; the gridDim.y blocks
+// of a column group form one cluster (1 x gridDim.y), and its first CTA
+// reduces their maxima through distributed shared memory.  Every thread
+// reaches both cluster barriers.
 __global__ void exponents_cols_kernel(const double *__restrict__ B, int64_t ldb, int64_t K,
                                       int64_t N, int32_t *__restrict__ f, int *status) {
   __shared__ unsigned long long part[8][64];
+  __shared__ unsigned long long colmax[64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t j0 = (int64_t)blockIdx.x * 64 + 2 * lane;
+  const int64_t kc = (K + gridDim.y - 1) / gridDim.y;
+  const int64_t kb = (int64_t)blockIdx.y * kc, ke = kb + kc < K ? kb + kc : K;
   unsigned long long m0 = 0, m1 = 0;
   const bool pairs = ((reinterpret_cast<uintptr_t>(B) | (uintptr_t)(ldb * 8)) & 15) == 0;
   if (j0 + 1 < N && pairs) {
-    for (int64_t k = warp; k < K; k += 8) {
+    for (int64_t k = kb + warp; k < ke; k += 8) {
       const double2 v = *reinterpret_cast<const double2 *>(B + k * ldb + j0);
       m0 = max(m0, absbits(v.x));
       m1 = max(m1, absbits(v.y));
     }
   } else {
-    for (int64_t k = warp; k < K; k += 8) {
+    for (int64_t k = kb + warp; k < ke; k += 8) {
       if (j0 < N) m0 = max(m0, absbits(B[k * ldb + j0]));
       if (j0 + 1 < N) m1 = max(m1, absbits(B[k * ldb + j0 + 1]));
     }
@@ -96,6 +103,14 @@ __global__ void exponents_cols_kernel(const double *__restrict__ B, int64_t ldb,
     unsigned long long m = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) m = max(m, part[w][threadIdx.x]);
+    colmax[threadIdx.x] = m;
+  }
+  const bool split = gridDim.y > 1;
+  if (split) cluster_sync();         // every CTA's colmax is written
+  if (threadIdx.x < 64 && cluster_ctarank() == 0) {
+    unsigned long long m = colmax[threadIdx.x];
+    for (uint32_t r = 1; r < gridDim.y; ++r)
+      m = max(m, ld_shared_cluster_u64(smem_u32(&colmax[threadIdx.x]), r));
     const int64_t j = (int64_t)blockIdx.x * 64 + threadIdx.x;
     if (j < N) {
       bool nf = false;
@@ -103,6 +118,7 @@ __global__ void exponents_cols_kernel(const double *__restrict__ B, int64_t ldb,
       if (nf) record_error(status, HSUMMA_ERR_NONFINITE, kSiteNonFinite);
     }
   }
+  if (split) cluster_sync();         // the first CTA has read every colmax
 }
 
 // The digits of one value, slice by slice.  With F = floor(|x| 2^-e 2^64)
@@ -549,7 +565,25 @@ int launch_split_exponents(int64_t M, int64_t N, int64_t K, const double *A, int
     count_launch();
   }
   if (N > 0) {
-    exponents_cols_kernel<<<(unsigned)ceil_div(N, 64), 256, 0, s>>>(B, ldb, K, N, f, status);
+    // k split over a cluster of up to 8 CTAs per column group, enough for
+    // about four CTAs per SM (152 SMs) when N is small
+    const int64_t nbx = ceil_div(N, 64);
+    int ks = (int)ceil_div(4 * 152, nbx);
+    ks = ks < 1 ? 1 : (ks > 8 ? 8 : ks);
+    if (ks > K) ks = K > 1 ? (int)K : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nbx, (unsigned)ks, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = (unsigned)ks;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e2 = cudaLaunchKernelEx(&cfg, exponents_cols_kernel, B, ldb, K, N, f, status);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "launch exponent scan (columns)");
     count_launch();
   }
   cudaError_t err = cudaGetLastError();

@@ -103,6 +103,23 @@ def test_slices_bit_patterns(kind):
     assert np.array_equal(got_b, np.transpose(split.split_cols(B, f_o, S, w), (0, 2, 1)))
 
 
+@pytest.mark.parametrize("K,N", [(1, 1), (3, 65), (7, 200), (130, 64), (1000, 130), (4099, 7)])
+def test_column_exponents_split_over_k(K, N):
+    # the column scan splits k over a cluster of up to 8 CTAs (fewer when K is
+    # smaller); the largest entry of a column sits in any of the slices
+    hs = lib_ready()
+    torch = torch_cuda()
+    rng = np.random.default_rng(K + N)
+    B = rng.uniform(-1, 1, (K, N)) * np.exp2(rng.integers(-30, 30, (K, N)).astype(float))
+    B[rng.integers(0, K, N), np.arange(N)] = 2.0 ** 40 * rng.uniform(0.5, 1, N)
+    A = np.ones((2, K))
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    e, f = hs.split_exponents(dA, dB)
+    hs.sync()
+    assert np.array_equal(f.cpu().numpy(), split.col_exponents(B))
+    assert np.array_equal(e.cpu().numpy(), split.row_exponents(A))
+
+
 def test_nonfinite_is_reported():
     hs = lib_ready()
     torch = torch_cuda()
