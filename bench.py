@@ -93,9 +93,11 @@ def multi_gpu_line(world: int):
 
 def timeline_summary(tl, n):
     """One host-buffer call's pipeline, from its timed phases: the device time
-    of the block products, when the first product started (the exposed copy-in),
-    the time after the last one (the exposed copy-out), the products' waits
-    for data in between, and the host-link rates the copies ran at."""
+    of the block products (each from the arrival of its column block of B, so
+    the first includes the wait for A's first row block), when the first one
+    started (the exposed copy-in), the time after the last one (the exposed
+    copy-out), the products' waits for data in between, and the host-link
+    rates the copies ran at."""
     prod = sorted((a, b) for nm, r, c, a, b in tl if nm == "product")
     cin = [(a, b) for nm, r, c, a, b in tl if nm in ("B in", "A in")]
     cout = [(a, b) for nm, r, c, a, b in tl if nm == "C out"]
@@ -105,7 +107,7 @@ def timeline_summary(tl, n):
     busy_in = sum(b - a for a, b in cin)
     busy_out = sum(b - a for a, b in cout)
     return {"products_ms": round(sum(b - a for a, b in prod), 2),
-            "first_product_at_ms": round(prod[0][0], 2),
+            "first_block_at_ms": round(prod[0][0], 2),
             "waits_between_ms": round(waits, 2),
             "after_last_product_ms": round(max(b for a, b in cout) - prod[-1][1], 2),
             "h2d_gbps": round(2 * 8 * n * n / busy_in / 1e6, 1) if busy_in > 0 else None,

@@ -399,14 +399,17 @@ int hsumma_stage_times(double *h_ms, int *h_calls);
 /* hsumma_gemm_host runs a product of at least two blocks as a pipeline: C is
  * cut into R row blocks (R in {4, 3, 2}, R | P, R | I) and Cb column blocks
  * (Cb in {2, 1}, Cb | Q, Cb | J), each block keeping the product's groups;
- * B_0 and A_0 are copied in first, and each block product starts once its
- * A_r and B_c are on the device while the rest copy in and the finished
+ * B_0 and A_0 are copied in first; each block's work starts once its B_c is
+ * on the device (the split path scans and slices B_c there, at its first use)
+ * and its product once A_r is too, while the rest copy in and the finished
  * blocks of C copy out.
  * Timeline of the last hsumma_gemm_host call, when that call ran with stage
  * timing on and was pipelined (otherwise *h_count = 0): *h_count phases, in
  * this order: the copies of B_c in (c < Cb), the copies of A_r in (r < R),
- * the block products (r-major: C_00, C_01, C_10, ...), the copies of the
- * blocks of C out (same order).  For phase i, h_ms[2 i] and h_ms[2 i + 1] are
+ * the block products (r-major: C_00, C_01, C_10, ...; each from the moment
+ * its B_c is on the device, so the first includes the wait for A_0), the
+ * copies of the blocks of C out (same order).  For phase i, h_ms[2 i] and
+ * h_ms[2 i + 1] are
  * its start and end in milliseconds after the call's first event (CUDA events
  * on the stream that ran the phase); at most max values are written (at most
  * 22 phases).  hsumma_host_timeline_blocks gives R and Cb of that call (0 and

@@ -597,8 +597,8 @@ static cudaError_t pipeline_events(bool timed) {
 // A and C and the Cb column blocks of B and C.  The copy-in stream brings B_0,
 // A_0, then the other column blocks of B, then the other row blocks of A; the
 // caller's stream, for the split path, scans and slices each column block of
-// B once when it has arrived and each row block of A before its first
-// product, and runs the products row block by row block (C_00, C_01, C_10, ...),
+// B once when it has arrived (before it waits for the row block of A it meets
+// first) and each row block of A before its first product, and runs the products row block by row block (C_00, C_01, C_10, ...),
 // each after the copies it needs; each finished block of C goes back on the
 // copy-out stream while the next one computes.  The first product thus waits
 // only for A_0 and B_0.  Every element is computed as in the unblocked product
@@ -708,13 +708,15 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
       st = make_plan(mr, nc, K, full.P / R, full.Q / Cb, full.G / (R * Cb), full.b, full.Bo,
                      kind, full.cyc, &g);
       if (st != HSUMMA_OK) return st;
-      // this block's operands: A_r, and B_c (scanned and sliced at its first use)
-      e = cudaStreamWaitEvent(s, evA(r), 0);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, evB(c), 0);
+      // this block's operands: B_c (scanned and sliced at its first use, while
+      // A_r may still be arriving), then A_r
+      e = cudaStreamWaitEvent(s, evB(c), 0);
       if (e == cudaSuccess) e = mark(ph_prod + r * Cb + c, 0, s);
-      if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(operands)");
+      if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(B block)");
       double *Crc = dC + r0 * ldc + c0;
       if (kind == HSUMMA_FP64) {
+        e = cudaStreamWaitEvent(s, evA(r), 0);
+        if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(A block)");
         st = launch_fp64_hsumma(g, Ar, lda, dB + c0, ldb, Crc, ldc, s);
       } else {
         void *Bsc = Bs + c * bs_stride;
@@ -725,6 +727,8 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
             st = launch_split_slices(0, nc, K, nullptr, 1, dB + c0, ldb, nullptr, f_cols + c0,
                                      kind, S, nullptr, Bsc, s);
         }
+        e = cudaStreamWaitEvent(s, evA(r), 0);
+        if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(A block)");
         if (st == HSUMMA_OK && c == 0) {
           st = launch_split_exponents(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, s);
           if (st == HSUMMA_OK)

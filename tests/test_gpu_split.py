@@ -465,9 +465,9 @@ def test_a_wait_that_runs_out_is_reported_and_cleared():
     ("fp64", 0, 16, 16, 16, "smallint"),   # 4 x 4 clusters
 ])
 def test_host_entry_pipelined_in_two_dimensions(kind, S, P, Q, G, dist):
-    # 4 row blocks x 2 column blocks: B_0 and A_0 first, each block product
-    # after its own operands; the timeline lists every phase in order and C is
-    # the unblocked product bit for bit
+    # 4 row blocks x 2 column blocks: B_0 and A_0 first, each block after its
+    # own operands; the timeline lists every phase in order and C is the
+    # unblocked product bit for bit
     hs = lib_ready()
     torch = torch_cuda()
     M, N = 2048, 1032          # ragged column blocks (the second one is shorter)
@@ -490,8 +490,10 @@ def test_host_entry_pipelined_in_two_dimensions(kind, S, P, Q, G, dist):
     assert prods == [(r, c) for r in range(4) for c in range(2)]
     assert len(tl) == 2 + 4 + 2 * 8
     t = {(nm, r, c): (a, e) for nm, r, c, a, e in tl}
-    # the first product waits for A_0 and B_0 only
-    assert t[("product", 0, 0)][0] >= max(t[("B in", -1, 0)][1], t[("A in", 0, -1)][1]) - 1e-3
+    # the first block starts once B_0 is in (its scan and slicing overlap A_0's
+    # copy) and cannot finish before A_0 is in
+    assert t[("product", 0, 0)][0] >= t[("B in", -1, 0)][1] - 1e-3
+    assert t[("product", 0, 0)][1] >= t[("A in", 0, -1)][1] - 1e-3
     if kind == "fp64":
         want = (A.numpy().astype(np.int64) @ B.numpy().astype(np.int64)).astype(np.float64)
     else:
