@@ -13,6 +13,8 @@
 //   group counts G in {1, p/16, p/8, p/4, p/2, p} (p = PQ) that factor as
 //   I | P, J | Q, one per distinct realised cluster shape (flat, or a cluster
 //   of the group's CTAs);
+//   bf16 with an odd P > 1: also P + 1 processor rows with the groups that
+//   run on CTA pairs (2 x 1 and 2 x 2), since an odd P admits none;
 //   b = the kernel's stage width (32, 128, 64): b does not change the
 //   arithmetic or the schedule on this GPU, only the counters' bookkeeping;
 //   B in {b, 4b, 16b} (how far ahead the owners stage outer panels in L2).
@@ -47,29 +49,38 @@ void enumerate(int64_t M, int64_t N, int kind, std::vector<Cand> &out) {
   int tm, tn, b;
   path_shape(kind, &tm, &tn, &b);
   std::vector<std::pair<int64_t, int64_t>> grids;
+  // one grid's candidates: a G per distinct realised cluster shape (only the
+  // CTA-pair shapes 2 x 1 and 2 x 2 when pairs_only)
+  auto add_grid = [&](int64_t P, int64_t Q, bool pairs_only) {
+    if (P > 65535 || Q > 65535 || P * Q > (int64_t)1 << 30) return;
+    for (auto &g : grids)
+      if (g.first == P && g.second == Q) return;
+    grids.emplace_back(P, Q);
+    const int64_t p = P * Q;
+    std::vector<std::pair<int, int>> shapes;
+    for (int64_t div : {p, (int64_t)16, (int64_t)8, (int64_t)4, (int64_t)2, (int64_t)1}) {
+      if (p % div) continue;
+      const int G = (int)(p / div);  // p / p = 1 first, then p/16 ... p
+      int I, J, cm, cn;
+      if (hsumma_group_shape((int)P, (int)Q, G, &I, &J, &cm, &cn) != HSUMMA_OK) continue;
+      if (pairs_only && !(cm == 2 && (cn == 1 || cn == 2))) continue;
+      bool dup = false;
+      for (auto &s : shapes) dup |= s.first == cm && s.second == cn;
+      if (dup) continue;
+      shapes.emplace_back(cm, cn);
+      for (int r : {1, 4, 16}) out.push_back({(int)P, (int)Q, G, b, r * b});
+    }
+  };
   for (int fm = 1; fm <= 2; ++fm)
     for (int fn = 1; fn <= 2; ++fn) {
       int64_t P = ceil_div(M, (int64_t)fm * tm), Q = ceil_div(N, (int64_t)fn * tn);
       if (P < 1) P = 1;
       if (Q < 1) Q = 1;
-      if (P > 65535 || Q > 65535 || P * Q > (int64_t)1 << 30) continue;
-      bool seen = false;
-      for (auto &g : grids) seen |= g.first == P && g.second == Q;
-      if (seen) continue;
-      grids.emplace_back(P, Q);
-      const int64_t p = P * Q;
-      std::vector<std::pair<int, int>> shapes;
-      for (int64_t div : {p, (int64_t)16, (int64_t)8, (int64_t)4, (int64_t)2, (int64_t)1}) {
-        if (p % div) continue;
-        const int G = (int)(p / div);  // p / p = 1 first, then p/16 ... p
-        int I, J, cm, cn;
-        if (hsumma_group_shape((int)P, (int)Q, G, &I, &J, &cm, &cn) != HSUMMA_OK) continue;
-        bool dup = false;
-        for (auto &s : shapes) dup |= s.first == cm && s.second == cn;
-        if (dup) continue;
-        shapes.emplace_back(cm, cn);
-        for (int r : {1, 4, 16}) out.push_back({(int)P, (int)Q, G, b, r * b});
-      }
+      add_grid(P, Q, false);
+      // bf16: an odd P admits no CTA pairs (two processor rows each); one more
+      // processor row makes them possible at the cost of a slightly
+      // shorter block (M / (P + 1) rows on a 128-row tile)
+      if (kind == HSUMMA_BF16_SLICES && P > 1 && (P & 1)) add_grid(P + 1, Q, true);
     }
 }
 

@@ -19,6 +19,7 @@ from paper_1306_4161_gb300 import _build, autotune
 
 SHAPES = [(16384, 16384, 16384, "bf16", 5), (1024, 1024, 1024, "fp64", 0),
           (1152, 7552, 2048, "int8", 4), (128, 128, 128, "fp64", 0), (3000, 200, 64, "bf16", 3),
+          (1152, 3328, 1024, "bf16", 4), (6784, 3968, 7680, "bf16", 6),
           (8192, 1024, 4096, "int8", 8), (5000, 7000, 3000, "fp64", 0)]
 TILE = {"fp64": (128, 128, 32), "int8": (128, 128, 128), "bf16": (128, 256, 64)}
 
@@ -32,19 +33,26 @@ def built():
 def test_candidates_follow_the_group_rule(M, N, K, kind, S):
     tm, tn, b = TILE[kind]
     cands = hs.candidates(M, N, K, kind, S)
-    assert 1 <= len(cands) <= 72
+    assert 1 <= len(cands) <= 96
     assert len(set(cands)) == len(cands)
     grids = {(math.ceil(M / (fm * tm)), math.ceil(N / (fn * tn))) for fm in (1, 2) for fn in (1, 2)}
+    # bf16: an odd P also gets P + 1 rows, with the CTA-pair groups only (2 x 1
+    # groups always exist there: G = (P + 1) Q / 2)
+    extra = {(P + 1, Q) for P, Q in grids if kind == "bf16" and P > 1 and P % 2} - grids
+    assert cands[0][:2] == (math.ceil(M / tm), math.ceil(N / tn))
     shapes = {}
     for P, Q, G, bb, Bo in cands:
-        assert (P, Q) in grids
+        assert (P, Q) in grids | extra
         assert bb == b and Bo in (b, 4 * b, 16 * b)
         ij = gsched.group_shape(P, Q, G)
         assert ij is not None, (P, Q, G)
         assert (P * Q) // G in (1, 2, 4, 8, 16, P * Q)
         cl = gsched.cluster_shape(P, Q, ij[0], ij[1], limit=16)
         assert hs.group_shape(P, Q, G) == (*ij, *cl)
+        if (P, Q) in extra:
+            assert cl in ((2, 1), (2, 2)), (P, Q, G, cl)
         shapes.setdefault((P, Q), {}).setdefault(cl, set()).add(G)
+    assert extra <= set(shapes)
     for (P, Q), by_shape in shapes.items():
         for cl, gs_ in by_shape.items():
             assert len(gs_) == 1, (P, Q, cl, gs_)     # one G per realised cluster shape
