@@ -397,16 +397,17 @@ int hsumma_stage_timing(int enable);
 int hsumma_stage_times(double *h_ms, int *h_calls);
 
 /* hsumma_gemm_host runs a product of at least two blocks as a pipeline: C is
- * cut into R row blocks (R in {4, 3, 2}, R | P, R | I) and Cb column blocks
- * (Cb in {2, 1}, Cb | Q, Cb | J), each block keeping the product's groups;
- * B_0 and A_0 are copied in first; each block's work starts once its B_c is
- * on the device (the split path scans and slices B_c there, at its first use)
- * and its product once A_r is too, while the rest copy in and the finished
- * blocks of C copy out.
+ * cut into R row blocks (R in {4, 3, 2}, R | P, R | I; blocks of other sizes
+ * for products on persistent CTA pairs, see hsumma_host_row_blocks) and Cb
+ * column blocks (Cb in {2, 1}, Cb | Q, Cb | J), each block keeping the
+ * product's groups; B_0 and A_0 are copied in first; each block's work starts
+ * once its B_c is on the device (the split path scans and slices B_c there,
+ * at its first use) and its product once A_r is too, while the rest copy in
+ * and the finished blocks of C copy out.
  * Timeline of the last hsumma_gemm_host call, when that call ran with stage
  * timing on and was pipelined (otherwise *h_count = 0): *h_count phases, in
  * this order: the copies of B_c in (c < Cb), the copies of A_r in (r < R),
- * the block products (r-major: C_00, C_01, C_10, ...; each from the moment
+ * the block products (indexed r-major: C_00, C_01, C_10, ...; each from the moment
  * its B_c is on the device, so the first includes the wait for A_0), the
  * copies of the blocks of C out (same order).  For phase i, h_ms[2 i] and
  * h_ms[2 i + 1] are
@@ -416,6 +417,31 @@ int hsumma_stage_times(double *h_ms, int *h_calls);
  * 0 when there is no timeline). */
 int hsumma_host_timeline(double *h_ms, int max, int *h_count);
 int hsumma_host_timeline_blocks(int *rows, int *cols);
+
+/* The row blocks of the last hsumma_gemm_host call (timed or not): their count
+ * in *h_count (0 if that call was not pipelined) and the first row of each in
+ * h_row0[0 .. min(count, max) - 1].  Uniform blocks of P/R processor rows,
+ * except for bf16 products whose blocks run on persistent CTA pairs (2 x 1 or
+ * 2 x 2 groups, block layout): there every block after the first spans a
+ * whole number of rounds of the resident pair clusters, and the first block
+ * takes the remaining rows (it is copied in and computed first; the second
+ * row block is then copied before the other column blocks of B, and the
+ * block products run in the order their operands arrive).  Returns
+ * HSUMMA_ERR_ARG on a null pointer. */
+int hsumma_host_row_blocks(int64_t *h_row0, int max, int *h_count);
+
+/* The round-aligned row blocks that rule gives for a grid of P processor rows
+ * (pairs of rows: P even), Qc processor columns per column block, CTA pairs
+ * of cn in {1, 2} columns and `resident` clusters: t = the least number of
+ * tile rows (pairs of processor rows) whose (Qc / cn) t pair tiles are a
+ * multiple of `resident`; blocks of t tile rows (of a multiple of t when
+ * more than 4 blocks would result), the remainder first.  Writes the
+ * processor rows of each block to procs[0 .. min(count, max) - 1] and their
+ * count (2 to 4) to *h_count, or 0 when no split of at least two blocks
+ * exists (P odd, t >= P / 2).  Host arithmetic only.  Returns HSUMMA_ERR_ARG
+ * on a null pointer or an argument out of range. */
+int hsumma_host_row_rounds(int P, int Qc, int cn, int resident, int *procs, int max,
+                           int *h_count);
 
 /* ---- Peak microbenchmarks (roofline denominators) ---- */
 

@@ -82,6 +82,9 @@ _SIGS = {
     "hsumma_stage_times": ([_vp, ctypes.POINTER(ctypes.c_int)], _i32),
     "hsumma_host_timeline": ([_vp, _i32, ctypes.POINTER(ctypes.c_int)], _i32),
     "hsumma_host_timeline_blocks": ([ctypes.POINTER(ctypes.c_int)] * 2, _i32),
+    "hsumma_host_row_blocks": ([_vp, _i32, ctypes.POINTER(ctypes.c_int)], _i32),
+    "hsumma_host_row_rounds": ([_i32, _i32, _i32, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_int)],
+                               _i32),
     "hsumma_candidates": ([_i64, _i64, _i64, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_int)],
                           _i32),
     "hsumma_features": ([_i64, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
@@ -394,6 +397,24 @@ def stage_times():
     n = ctypes.c_int()
     _check(lib().hsumma_stage_times(ms, ctypes.byref(n)))
     return list(ms), n.value
+
+
+def host_row_blocks() -> list[int]:
+    """First row of each row block of the last gemm_host call ([] if it was
+    not pipelined)."""
+    r0 = (ctypes.c_int64 * 8)()
+    n = ctypes.c_int()
+    _check(lib().hsumma_host_row_blocks(r0, 8, ctypes.byref(n)))
+    return [int(r0[i]) for i in range(min(n.value, 8))]
+
+
+def host_row_rounds(P: int, Qc: int, cn: int, resident: int) -> list[int]:
+    """Processor rows of the round-aligned row blocks the host pipeline uses
+    for products on persistent CTA pairs ([] when no such split exists)."""
+    pr = (ctypes.c_int * 8)()
+    n = ctypes.c_int()
+    _check(lib().hsumma_host_row_rounds(P, Qc, cn, resident, pr, 8, ctypes.byref(n)))
+    return [int(pr[i]) for i in range(min(n.value, 8))]
 
 
 def host_timeline():

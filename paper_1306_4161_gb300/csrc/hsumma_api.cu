@@ -1,5 +1,6 @@
 // C ABI of libhsumma: argument checks, group resolution (Section III), the
 // choice of kernels, the device error word, counters and workspace.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -581,6 +582,41 @@ static int host_col_blocks(int64_t N, int Q, int J, int64_t Nt) {
   return C;
 }
 
+// Row blocks in whole rounds, for products whose block products run on
+// persistent CTA pairs (bf16, 2 x 1 or 2 x 2 groups, block layout): a block of
+// Pr processor rows is (Pr / 2) (Qc / cn) pair tiles, swept in rounds of the
+// resident clusters, so a block of t tile rows, t the least with t (Qc / cn) a
+// multiple of the resident count, wastes no part of a round.  The blocks are
+// the remainder of the tile rows first (small: it arrives soonest and starts
+// the pipeline), then whole multiples of t, at most kMaxHostBlocks in all.
+// Fills procs[] (processor rows per block) and returns the block count, or 0
+// when no such split of at least two blocks exists.
+static int host_row_rounds(int P, int Qc, int cn, int resident, int *procs) {
+  if (resident < 1 || P % 2 || Qc % cn) return 0;
+  const int u = Qc / cn, T = P / 2;          // pair tiles per tile row, tile rows
+  int g = resident, h = u;
+  while (h) {
+    const int x = g % h;
+    g = h;
+    h = x;
+  }
+  int step = resident / g;                   // tile rows per whole number of rounds
+  if (step >= T) return 0;
+  int k = T / step, rem = T % step;
+  const int room = kMaxHostBlocks - (rem ? 1 : 0);
+  if (k > room) {
+    step *= (k + room - 1) / room;
+    k = T / step;
+    rem = T % step;
+  }
+  const int nb = k + (rem ? 1 : 0);
+  if (nb < 2 || nb > kMaxHostBlocks) return 0;
+  int i = 0;
+  if (rem) procs[i++] = 2 * rem;
+  while (i < nb) procs[i++] = 2 * step;
+  return nb;
+}
+
 // The pipeline's events, created on first use and kept until hsumma_finalize:
 // ordering events always, timing events when `timed`.
 static cudaError_t pipeline_events(bool timed) {
@@ -607,8 +643,8 @@ static cudaError_t pipeline_events(bool timed) {
 // on, timing events bracket every phase (the timeline of hsumma_host_timeline).
 static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA, int64_t lda,
                                const double *hB, int64_t ldb, double *hC, int64_t ldc,
-                               const GridPlan &full, int R, int Cb, int kind, int S, double *dA,
-                               double *dB, double *dC, cudaStream_t s) {
+                               const GridPlan &full, int R, const int *procs, int Cb, int kind,
+                               int S, double *dA, double *dB, double *dC, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (!g_state.copy_in) e = cudaStreamCreateWithFlags(&g_state.copy_in, cudaStreamNonBlocking);
   if (e == cudaSuccess && !g_state.copy_out)
@@ -622,10 +658,22 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   e = pipeline_events(timed);
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate(pipeline)");
   cudaStream_t ci = g_state.copy_in, co = g_state.copy_out;
-  const int64_t rows = (int64_t)(full.P / R) * full.Mt;
+  // row block r: processor rows procs[r], matrix rows [row0[r], row0[r] + row_count(r))
+  int64_t row0[kMaxHostBlocks + 1];
+  row0[0] = 0;
+  for (int r = 0; r < R; ++r) row0[r + 1] = row0[r] + (int64_t)procs[r] * full.Mt;
+  int64_t rows = 0;                          // the longest row block
+  for (int r = 0; r < R; ++r) rows = (int64_t)procs[r] * full.Mt > rows ? (int64_t)procs[r] * full.Mt : rows;
   const int64_t cols = (int64_t)(full.Q / Cb) * full.Nt;
-  auto row_count = [&](int r) { return (M - r * rows) < rows ? (M - r * rows) : rows; };
+  auto row_count = [&](int r) {
+    const int64_t end = row0[r + 1] < M ? row0[r + 1] : M;
+    return end - row0[r];
+  };
   auto col_count = [&](int c) { return (N - c * cols) < cols ? (N - c * cols) : cols; };
+  // A small first row block (rows in whole rounds) is followed by the second
+  // row block before the other column blocks of B, and the block products run
+  // in the order their operands arrive (r-major among equals)
+  const bool small_first = R > 1 && procs[0] < procs[1];
   // ordering events: [0] the caller's earlier work, [1] all copied back,
   // [2 + c] B_c copied, [2 + Cb + r] A_r copied, [2 + Cb + R + (r Cb + c)] C_rc computed
   cudaEvent_t *ev = g_state.pipe_ev;
@@ -658,7 +706,7 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
     return x;
   };
   auto copy_a = [&](int r) {
-    const int64_t r0 = r * rows;
+    const int64_t r0 = row0[r];
     cudaError_t x = mark(ph_a + r, 0, ci);
     if (x == cudaSuccess)
       x = cudaMemcpy2DAsync(dA + r0 * lda, lda * 8, hA + r0 * lda, lda * 8, K * 8, row_count(r),
@@ -667,46 +715,65 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
     if (x == cudaSuccess) x = cudaEventRecord(evA(r), ci);
     return x;
   };
-  if (e == cudaSuccess) e = copy_b(0);
-  if (e == cudaSuccess) e = copy_a(0);
-  for (int c = 1; c < Cb && e == cudaSuccess; ++c) e = copy_b(c);
-  for (int r = 1; r < R && e == cudaSuccess; ++r) e = copy_a(r);
+  // arrival rank of each operand block, in the order the copies are issued
+  int rank_a[kMaxHostBlocks], rank_b[kMaxHostColBlocks], nrank = 0;
+  auto in_b = [&](int c) { rank_b[c] = nrank++; return copy_b(c); };
+  auto in_a = [&](int r) { rank_a[r] = nrank++; return copy_a(r); };
+  if (e == cudaSuccess) e = in_b(0);
+  if (e == cudaSuccess) e = in_a(0);
+  if (small_first && e == cudaSuccess) e = in_a(1);
+  for (int c = 1; c < Cb && e == cudaSuccess; ++c) e = in_b(c);
+  for (int r = small_first ? 2 : 1; r < R && e == cudaSuccess; ++r) e = in_a(r);
   if (e != cudaSuccess) return fail(e, "copy operands in");
+  int order[kMaxHostBlocks * kMaxHostColBlocks], nord = 0;
+  for (int r = 0; r < R; ++r)
+    for (int c = 0; c < Cb; ++c) order[nord++] = r * Cb + c;
+  auto ready = [&](int rc) {
+    const int ra = rank_a[rc / Cb], rb = rank_b[rc % Cb];
+    return ra > rb ? ra : rb;
+  };
+  std::stable_sort(order, order + nord, [&](int x, int y) { return ready(x) < ready(y); });
 
-  // split-path workspace for one block: e (rows), f (all N), A slices of one
-  // row block, B slices of every column block, the diagonal sums of one block
+  // split-path workspace: e (all M), f (all N), the A slices of every row
+  // block and the B slices of every column block (each sliced once, at its
+  // first use), the diagonal sums of one block (the block products run one
+  // after another on the caller's stream)
   int32_t *e_rows = nullptr, *f_cols = nullptr, *D = nullptr;
   uint8_t *As = nullptr, *Bs = nullptr;
-  size_t bs_stride = 0;
+  size_t as_stride = 0, bs_stride = 0;
   int st = HSUMMA_OK;
   if (kind != HSUMMA_FP64) {
     const int64_t Kp = ceil_div(K, 64) * 64;
     const size_t eb = kind == HSUMMA_INT8_SLICES ? 1 : 2;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    as_stride = al((size_t)S * rows * Kp * eb);
     bs_stride = al((size_t)S * cols * Kp * eb);
-    const size_t need = al(rows * 4) + al(N * 4) + al((size_t)S * rows * Kp * eb) +
-                        Cb * bs_stride + al((size_t)S * split_planes(K, S, kind) * rows * cols * 4);
+    const size_t need = al(M * 4) + al(N * 4) + R * as_stride + Cb * bs_stride +
+                        al((size_t)S * split_planes(K, S, kind) * rows * cols * 4);
     st = ensure_workspace(need);
     if (st != HSUMMA_OK) return st;
     uint8_t *ws = reinterpret_cast<uint8_t *>(g_state.workspace);
     e_rows = reinterpret_cast<int32_t *>(ws);
-    ws += al(rows * 4);
+    ws += al(M * 4);
     f_cols = reinterpret_cast<int32_t *>(ws);
     ws += al(N * 4);
     As = ws;
-    ws += al((size_t)S * rows * Kp * eb);
+    ws += R * as_stride;
     Bs = ws;
     ws += Cb * bs_stride;
     D = reinterpret_cast<int32_t *>(ws);
   }
-  for (int r = 0; r < R; ++r) {
-    const int64_t r0 = r * rows, mr = row_count(r);
+  bool b_sliced[kMaxHostColBlocks] = {}, a_sliced[kMaxHostBlocks] = {};
+  const int grow = full.P / full.I;          // processor rows of a group
+  for (int oi = 0; oi < nord; ++oi) {
+    const int r = order[oi] / Cb, c = order[oi] % Cb;
+    const int64_t r0 = row0[r], mr = row_count(r);
     const double *Ar = dA + r0 * lda;
-    for (int c = 0; c < Cb; ++c) {
+    {
       const int64_t c0 = c * cols, nc = col_count(c);
       GridPlan g;
-      st = make_plan(mr, nc, K, full.P / R, full.Q / Cb, full.G / (R * Cb), full.b, full.Bo,
-                     kind, full.cyc, &g);
+      st = make_plan(mr, nc, K, procs[r], full.Q / Cb, (procs[r] / grow) * (full.J / Cb),
+                     full.b, full.Bo, kind, full.cyc, &g);
       if (st != HSUMMA_OK) return st;
       // this block's operands: B_c (scanned and sliced at its first use, while
       // A_r may still be arriving), then A_r
@@ -720,7 +787,8 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
         st = launch_fp64_hsumma(g, Ar, lda, dB + c0, ldb, Crc, ldc, s);
       } else {
         void *Bsc = Bs + c * bs_stride;
-        if (r == 0) {
+        if (!b_sliced[c]) {
+          b_sliced[c] = true;
           st = launch_split_exponents(0, nc, K, nullptr, 1, dB + c0, ldb, nullptr, f_cols + c0,
                                       s);
           if (st == HSUMMA_OK)
@@ -729,15 +797,18 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
         }
         e = cudaStreamWaitEvent(s, evA(r), 0);
         if (e != cudaSuccess) return fail(e, "cudaStreamWaitEvent(A block)");
-        if (st == HSUMMA_OK && c == 0) {
-          st = launch_split_exponents(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, s);
+        void *Asr = As + r * as_stride;
+        int32_t *er = e_rows + r0;
+        if (st == HSUMMA_OK && !a_sliced[r]) {
+          a_sliced[r] = true;
+          st = launch_split_exponents(mr, 0, K, Ar, lda, nullptr, 1, er, nullptr, s);
           if (st == HSUMMA_OK)
-            st = launch_split_slices(mr, 0, K, Ar, lda, nullptr, 1, e_rows, nullptr, kind, S, As,
+            st = launch_split_slices(mr, 0, K, Ar, lda, nullptr, 1, er, nullptr, kind, S, Asr,
                                      nullptr, s);
         }
-        if (st == HSUMMA_OK) st = launch_split_diagonals(g, kind, S, As, Bsc, D, s);
+        if (st == HSUMMA_OK) st = launch_split_diagonals(g, kind, S, Asr, Bsc, D, s);
         if (st == HSUMMA_OK)
-          st = launch_split_recombine(mr, nc, K, kind, S, D, e_rows, f_cols + c0, Crc, ldc, s);
+          st = launch_split_recombine(mr, nc, K, kind, S, D, er, f_cols + c0, Crc, ldc, s);
       }
       if (st != HSUMMA_OK) return st;
       e = mark(ph_prod + r * Cb + c, 1, s);
@@ -755,11 +826,15 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, evDone, 0);
   if (e != cudaSuccess) return fail(e, "join copy streams");
   st = hsumma_sync(reinterpret_cast<void *>(s));
-  if (timed) {
+  {
     std::lock_guard<std::mutex> lock(g_stage_mu);
-    g_state.timeline_phases = st == HSUMMA_OK ? ph_out + R * Cb : 0;
-    g_state.timeline_rows = R;
-    g_state.timeline_cols = Cb;
+    if (timed) {
+      g_state.timeline_phases = st == HSUMMA_OK ? ph_out + R * Cb : 0;
+      g_state.timeline_rows = R;
+      g_state.timeline_cols = Cb;
+    }
+    g_state.host_row_blocks = R;
+    for (int r = 0; r < R; ++r) g_state.host_row0[r] = row0[r];
   }
   return st;
 }
@@ -774,6 +849,7 @@ int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t 
   {
     std::lock_guard<std::mutex> lock(g_stage_mu);
     g_state.timeline_phases = 0;   // set again by a timed pipelined call
+    g_state.host_row_blocks = 0;   // set again by a pipelined call
   }
   int st = check_matrix_args(M, N, K, hA, lda, hB, ldb, hC, ldc);
   if (st != HSUMMA_OK) return st;
@@ -811,18 +887,39 @@ int hsumma_gemm_host(int64_t M, int64_t N, int64_t K, const double *hA, int64_t 
                                                 (lda % 2) == 0);
     int R = host_row_blocks(M, P, full.I, full.Mt);
     int Cb = host_col_blocks(N, Q, full.J, full.Nt);
-    // every block must resolve to the same groups and clusters as the product
-    auto keeps_groups = [&](int r, int c) {
+    // every block must resolve to the same groups and clusters as the product:
+    // a block of Pr processor rows and Q / c columns has (Pr / group rows)
+    // (J / c) groups
+    const int grow = P / full.I;
+    auto keeps_rows = [&](int Pr, int c) {
+      if (Pr % grow || full.J % c) return false;
       int I, J, cm, cn;
-      return resolve_groups(P / r, Q / c, full.G / (r * c), g_state.cluster_limit, &I, &J, &cm,
-                            &cn) == HSUMMA_OK &&
-             I * r == full.I && J * c == full.J && cm == full.cm && cn == full.cn;
+      return resolve_groups(Pr, Q / c, (Pr / grow) * (full.J / c), g_state.cluster_limit, &I,
+                            &J, &cm, &cn) == HSUMMA_OK &&
+             I == Pr / grow && J == full.J / c && cm == full.cm && cn == full.cn;
     };
-    if (Cb > 1 && !keeps_groups(R, Cb)) Cb = 1;
-    if (R > 1 && !keeps_groups(R, Cb)) R = 1;
+    if (Cb > 1 && !keeps_rows(P / R, Cb)) Cb = 1;
+    if (R > 1 && !keeps_rows(P / R, Cb)) R = 1;
+    int procs[kMaxHostBlocks];
+    for (int r = 0; r < R; ++r) procs[r] = P / R;
+    // block products on persistent CTA pairs: row blocks in whole rounds
+    const bool pairs = kind == HSUMMA_BF16_SLICES && g_state.bf16_pair && full.cm == 2 &&
+                       (full.cn == 1 || full.cn == 2) && !full.cyc &&
+                       (g_state.pair_launch & HSUMMA_PAIR_PERSISTENT);
+    int resident = 0;
+    if (pairs && exact_ok && pair_resident_clusters(full.cn, &resident) == HSUMMA_OK) {
+      int pr[kMaxHostBlocks];
+      const int nr = host_row_rounds(P, Q / Cb, full.cn, resident, pr);
+      bool ok = nr >= 2;
+      for (int r = 0; r < nr && ok; ++r) ok = keeps_rows(pr[r], Cb);
+      if (ok) {
+        R = nr;
+        for (int r = 0; r < R; ++r) procs[r] = pr[r];
+      }
+    }
     if (R * Cb > 1 && exact_ok && tma_ok)
-      return gemm_host_pipelined(M, N, K, hA, lda, hB, ldb, hC, ldc, full, R, Cb, kind, S, dA,
-                                 dB, dC, s);
+      return gemm_host_pipelined(M, N, K, hA, lda, hB, ldb, hC, ldc, full, R, procs, Cb, kind,
+                                 S, dA, dB, dC, s);
   }
   cudaError_t e;
   if (M && K) {
@@ -1040,6 +1137,34 @@ int hsumma_host_timeline_blocks(int *rows, int *cols) {
   std::lock_guard<std::mutex> lock(g_stage_mu);
   *rows = g_state.timeline_phases ? g_state.timeline_rows : 0;
   *cols = g_state.timeline_phases ? g_state.timeline_cols : 0;
+  return HSUMMA_OK;
+}
+
+int hsumma_host_row_rounds(int P, int Qc, int cn, int resident, int *procs, int max,
+                           int *count) {
+  if (!count || (max > 0 && !procs)) {
+    set_error("null output pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  if (P < 1 || Qc < 1 || (cn != 1 && cn != 2) || resident < 1) {
+    set_error("bad arguments (P=%d Qc=%d cn=%d resident=%d)", P, Qc, cn, resident);
+    return HSUMMA_ERR_ARG;
+  }
+  int pr[kMaxHostBlocks];
+  const int n = host_row_rounds(P, Qc, cn, resident, pr);
+  *count = n;
+  for (int r = 0; r < n && r < max; ++r) procs[r] = pr[r];
+  return HSUMMA_OK;
+}
+
+int hsumma_host_row_blocks(int64_t *row0, int max, int *count) {
+  if (!count || (max > 0 && !row0)) {
+    set_error("null output pointer");
+    return HSUMMA_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  *count = g_state.host_row_blocks;
+  for (int r = 0; r < g_state.host_row_blocks && r < max; ++r) row0[r] = g_state.host_row0[r];
   return HSUMMA_OK;
 }
 

@@ -55,6 +55,8 @@ struct DeviceState {
   cudaEvent_t pipe_tev[kHostTimelineEvents] = {};
   int timeline_phases = 0;                   // phases the last timed call recorded
   int timeline_rows = 0, timeline_cols = 0;  // and its row and column blocks
+  int host_row_blocks = 0;                   // row blocks of the last pipelined call
+  int64_t host_row0[kMaxHostBlocks] = {};    // and the first row of each
 };
 
 DeviceState &state();
@@ -118,6 +120,9 @@ int launch_split_int8(const GridPlan &g, int S, const void *As, const void *Bs, 
 int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void *Bs,
                            int32_t *D, cudaStream_t s);
 int bf16_cluster_limit(int *limit);
+// Clusters of the CTA-pair kernel (CN = 1: 2 x 1 groups, 2: 2 x 2) resident
+// on the device at once.
+int pair_resident_clusters(int CN, int *clusters);
 int int8_cluster_limit(int *limit);
 int launch_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, const int32_t *D,
                            const int32_t *e, const int32_t *f, double *C, int64_t ldc,

@@ -474,6 +474,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 }  // namespace
 
+// Clusters of the pair kernel (2 CN CTAs) that fit on the device at once,
+// queried once per CN and kept.
+int pair_resident_clusters(int CN, int *clusters) {
+  int &res = state().pair_resident[CN == 2 ? 2 : 1];
+  if (res == 0) {
+    auto kern = CN == 2 ? bf16_pair_kernel<2, false> : bf16_pair_kernel<1, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair smem)");
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3((unsigned)(2 * CN), 1, 1);
+    q.blockDim = dim3(NTHREADS, 1, 1);
+    q.dynamicSmemBytes = SMEM_BYTES;
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = (unsigned)(2 * CN);
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &q);
+    if (e != cudaSuccess || n < 1) {
+      set_error("cudaOccupancyMaxActiveClusters(pair kernel): %s (%d clusters)",
+                cudaGetErrorString(e), n);
+      return HSUMMA_ERR_CUDA;
+    }
+    res = n;
+  }
+  *clusters = res;
+  return HSUMMA_OK;
+}
+
 int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void *Bs, int32_t *D,
                            cudaStream_t s) {
   if (g.cm != 2 || (g.cn != 1 && g.cn != 2) || g.P % 2 || g.Q % g.cn) {
@@ -522,25 +555,9 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   int nclusters = ntiles;
   if (policy & HSUMMA_PAIR_PERSISTENT) {
     // one cluster per resident slot, each sweeping tiles L = cid, cid + ncl, ...
-    int &res = state().pair_resident[CN];
-    if (res == 0) {
-      cudaLaunchConfig_t q = {};
-      q.gridDim = dim3((unsigned)(2 * CN), 1, 1);
-      q.blockDim = dim3(NTHREADS, 1, 1);
-      q.dynamicSmemBytes = SMEM_BYTES;
-      cudaLaunchAttribute qa[1];
-      qa[0].id = cudaLaunchAttributeClusterDimension;
-      qa[0].val.clusterDim.x = (unsigned)(2 * CN);
-      qa[0].val.clusterDim.y = 1;
-      qa[0].val.clusterDim.z = 1;
-      q.attrs = qa;
-      q.numAttrs = 1;
-      e = cudaOccupancyMaxActiveClusters(&res, kern, &q);
-      if (e != cudaSuccess || res < 1) {
-        res = 0;
-        return cuda_fail(e, "cudaOccupancyMaxActiveClusters(pair kernel)");
-      }
-    }
+    int res = 0;
+    const int st = pair_resident_clusters(CN, &res);
+    if (st != HSUMMA_OK) return st;
     nclusters = ntiles < res ? ntiles : res;
   }
   cfg.gridDim = dim3((unsigned)(2 * CN * nclusters), 1, 1);

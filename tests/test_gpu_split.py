@@ -500,3 +500,38 @@ def test_host_entry_pipelined_in_two_dimensions(kind, S, P, Q, G, dist):
         want = split.split_gemm(A.numpy(), B.numpy(), S, kind)
     assert np.array_equal(hC, want)
     assert np.all(big[:, N:] == 7.0)
+
+
+def test_host_entry_row_blocks_in_whole_rounds():
+    # bf16 on persistent CTA pairs (2 x 1 groups): the row blocks after the
+    # first span whole rounds of the resident pair clusters and the first
+    # takes the remaining tile rows; with 40 x 8 processors, two column blocks
+    # of 4 and 76 resident clusters that is 2 + 38 processor rows (256 + 4864
+    # rows).  A_1 is copied before B_1, and C matches the oracle bit for bit
+    # on sampled entries (every block border among them).
+    hs = lib_ready()
+    torch_cuda()
+    import torch
+    M, N, K, S = 5120, 2048, 320, 3
+    A = torch.from_numpy(workloads.matrix(M, K, 91, "wide")).pin_memory()
+    B = torch.from_numpy(workloads.matrix(K, N, 92, "wide")).pin_memory()
+    hC = torch.empty((M, N), dtype=torch.float64).pin_memory()
+    hs.stage_timing(True)
+    try:
+        hs.gemm_host(A, B, hC, P=40, Q=8, G=160, b=64, Bouter=128, kind="bf16", slices=S)
+        tl = hs.host_timeline()
+    finally:
+        hs.stage_timing(False)
+    row0 = hs.host_row_blocks()
+    assert len(row0) >= 2 and row0[0] == 0
+    assert all(r % 256 == 0 for r in row0) and row0 == sorted(row0)
+    sizes = [b - a for a, b in zip(row0, row0[1:] + [M])]
+    assert sizes[0] < sizes[1] and all(s == sizes[1] for s in sizes[1:-1])
+    t = {(nm, r, c): (a, e) for nm, r, c, a, e in tl}
+    assert t[("A in", 1, -1)][1] <= t[("B in", -1, 1)][0] + 1e-3
+    rows, cols = sample_entries(M, N, 64, 93)
+    edges = np.array([min(M - 1, max(0, r + d)) for r in row0 for d in (-1, 0, 1)])
+    rows = np.concatenate([rows, edges])
+    cols = np.concatenate([cols, np.resize(np.array([0, 1023, 1024, 2047]), len(edges))])
+    want = split.split_entries(A.numpy(), B.numpy(), rows, cols, S, "bf16")
+    assert np.array_equal(hC.numpy()[rows, cols], want)
