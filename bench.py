@@ -385,6 +385,10 @@ def run_table(sections):
 PROFILE_CASES = {
     # bf16 S = 5 on CTA pairs (2 x 1 groups): one persistent launch at this size
     "pair6144": (6144, dict(P=48, Q=24, G=576, b=64, Bouter=512, kind="bf16", slices=5)),
+    # the same with the benchmark's launch policy at n = 16384: one persistent
+    # launch per diagonal (five launches a product)
+    "pair6144_diag": (6144, dict(P=48, Q=24, G=576, b=64, Bouter=512, kind="bf16", slices=5,
+                                 launch=("per_diagonal", True))),
     # bf16 S = 5 on single CTAs, flat (64-processor software groups)
     "diag6144": (6144, dict(P=48, Q=24, G=18, b=64, Bouter=1024, kind="bf16", slices=5)),
     # int8 S = 5, flat
@@ -402,7 +406,10 @@ def run_profile_case(name):
     import paper_1306_4161_gb300 as hs
     import workloads
     n, cfg = PROFILE_CASES[name]
+    cfg = dict(cfg)
     hs.init(0)
+    if "launch" in cfg:
+        hs.pair_launch(*cfg.pop("launch"))
     A = workloads.matrix_torch(n, n, 1002, "uniform", device="cuda")
     B = workloads.matrix_torch(n, n, 2002, "uniform", device="cuda")
     C = torch.empty((n, n), dtype=torch.float64, device="cuda")

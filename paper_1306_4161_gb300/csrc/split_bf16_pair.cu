@@ -45,6 +45,9 @@
 // 4..11 drain their CTA's 128 rows into exact int32 planes (a warp reads the
 // tensor-memory lanes of its quarter, warp mod 4; warps 4..7 and 8..11 cover
 // the 128 rows for the two column halves).
+#include <utility>
+#include <vector>
+
 #include "internal.h"
 #include "ptx.cuh"
 #include "tc05.cuh"
@@ -69,6 +72,9 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC2 = idesc_bf16_f32(2 * TM, TN);
 
+// Tail schedule of a persistent launch: at most this many clusters and items.
+constexpr int kMaxPairClusters = 160, kMaxTailItems = 640;
+
 struct PairParams {
   int32_t *D;
   int64_t M, N, K, Kpad, Mt, Nt, Kq, Kp;
@@ -76,7 +82,32 @@ struct PairParams {
   int d_lo, d_hi;                // the diagonals (slice pairs s + t = d) of this launch
   unsigned long long *counters;
   int *status;
+  // work items: the tiles below `whole`, round robin over the clusters, each
+  // with every diagonal of the launch; then cluster cid's tail items
+  // [tail_off[cid], tail_off[cid + 1]), one tile and one diagonal each
+  int whole;
+  int16_t tail_off[kMaxPairClusters + 1];
+  int32_t tail_L[kMaxTailItems];
+  int8_t tail_d[kMaxTailItems];
 };
+
+// Work item i of cluster cid (of ncl): tile L and diagonals [dlo, dhi]; false
+// past the cluster's last item.
+__device__ __forceinline__ bool pair_item(const PairParams &p, int cid, int ncl, int i, int *L,
+                                          int *dlo, int *dhi) {
+  const int nw = p.whole > cid ? (p.whole - cid + ncl - 1) / ncl : 0;
+  if (i < nw) {
+    *L = cid + i * ncl;
+    *dlo = p.d_lo;
+    *dhi = p.d_hi;
+    return true;
+  }
+  const int k = p.tail_off[cid] + (i - nw);
+  if (k >= p.tail_off[cid + 1]) return false;
+  *L = p.tail_L[k];
+  *dlo = *dhi = p.tail_d[k];
+  return true;
+}
 
 __device__ __forceinline__ int64_t span(int64_t lo, int64_t hi, int64_t a, int64_t b) {
   const int64_t x = a > lo ? a : lo, y = b < hi ? b : hi;
@@ -121,7 +152,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bf16_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmApf,
-                     const __grid_constant__ CUtensorMap tmBpf, const PairParams p) {
+                     const __grid_constant__ CUtensorMap tmBpf,
+                     const __grid_constant__ PairParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -140,7 +172,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint16_t all_mask = (uint16_t)((1u << (2 * CN)) - 1u);
   const uint16_t pair_mask = (uint16_t)(3u << lead);
   const uint16_t row_mask = CN == 2 ? (uint16_t)((1u << ry) | (1u << (ry + 2))) : (uint16_t)1u;
-  const int ncx = p.Q / CN, ncy = p.P / 2, ntiles = ncx * ncy;
+  const int ncx = p.Q / CN, ncy = p.P / 2;
   const int ncl = (int)gridDim.x / (2 * CN), cid = (int)blockIdx.x / (2 * CN);
 
   if (threadIdx.x == 0) {
@@ -179,7 +211,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       unsigned long long a_ld = 0, a_dl = 0, b_ld = 0, pf = 0, nops = 0;
       uint32_t stage = 0, phase = 0;
       bool ok = true;
-      for (int L = cid; L < ntiles && ok; L += ncl) {
+      int L, dlo, dhi;
+      for (int it = 0; ok && pair_item(p, cid, ncl, it, &L, &dlo, &dhi); ++it) {
         int r, c;
         tile_proc<CN>(L, ncx, ncy, ry, px, &r, &c);
         for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
@@ -196,7 +229,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // its block and the matrix); every slice pair delivers them over all K
             const int64_t a_rows = span(row_lo, row_hi, am0, am0 + TM / CN);
             const int64_t b_cols = span(col_lo, col_hi, nh, nh + HN);
-            for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
+            for (int d = dlo; d <= dhi && ok; ++d) {
               for (int s = 1; s < d && ok; ++s) {
                 const int t = d - s;
                 a_ld += (unsigned long long)(a_rows * p.K);
@@ -217,12 +250,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int64_t o = kh / p.Bo;
                     int ns = s + 1, nd = d;
                     if (ns >= nd) { ++nd; ns = 1; }
-                    const bool first = (d == p.d_lo && s == 1 && o == 0);
+                    const bool first = (d == dlo && s == 1 && o == 0);
                     for (int w = first ? 0 : 1; w <= 1; ++w) {
                       int64_t q = o + w;
                       int ps = s, pt = t;
                       if (q >= nout) {
-                        if (nd > p.d_hi) break;
+                        if (nd > dhi) break;
                         q = 0;
                         ps = ns;
                         pt = nd - ns;
@@ -304,14 +337,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // panels that lie inside Kpad in the last stage of a pair (2 unless the
       // panel count is odd)
       const int last_panels = (int)((p.Kpad - (int64_t)(nkb - 1) * BKS) / PK);
-      for (int L = cid; L < ntiles && ok; L += ncl) {
+      int L, dlo, dhi;
+      for (int it = 0; ok && pair_item(p, cid, ncl, it, &L, &dlo, &dhi); ++it) {
         int r, c;
         tile_proc<CN>(L, ncx, ncy, ry, px, &r, &c);
         for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
           if (tile_skipped(cyc, r - ry, mi, p.P, TM, p.M)) continue;
           for (int ni = 0; ni < p.nsub_n && ok; ++ni) {
             if (tile_skipped(cyc, c - px, ni, p.Q, TN, p.N)) continue;
-            for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
+            for (int d = dlo; d <= dhi && ok; ++d) {
               const int nst = (d - 1) * nkb;
               int kb = 0;   // stage within the pair
               for (int st = 0; st < nst; ++st, ++gst) {
@@ -374,7 +408,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int h = (warp - 4) >> 2;          // column half of the 256-column tile
     uint32_t nchunk = 0;
     bool ok = true;
-    for (int L = cid; L < ntiles && ok; L += ncl) {
+    int L, dlo, dhi;
+    for (int it = 0; ok && pair_item(p, cid, ncl, it, &L, &dlo, &dhi); ++it) {
       int r, c;
       tile_proc<CN>(L, ncx, ncy, ry, px, &r, &c);
       for (int mi = 0; mi < p.nsub_m && ok; ++mi) {
@@ -388,7 +423,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tile_rows(cyc, c, ni, p.Q, p.Nt, TN, p.N, &t0, &col_lo, &col_hi);
           const int64_t n0 = t0 + h * 128;
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
-          for (int d = p.d_lo; d <= p.d_hi && ok; ++d) {
+          for (int d = dlo; d <= dhi && ok; ++d) {
             const int nst = (d - 1) * nkb;
             const int nseg_d = (nst + SEGST - 1) / SEGST;
             for (int seg = 0; seg < p.nseg && ok; ++seg) {
@@ -474,6 +509,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 }  // namespace
 
+// Tail of a persistent one-launch product: the tiles past the last whole round
+// (ntiles mod C of them, C resident clusters) would leave most clusters idle
+// in a last part-filled round.  Instead each of those tiles is cut into one
+// item per diagonal d (d - 1 slice pairs, its own planes, so no two clusters
+// write the same sums), and the items go largest first to the cluster with
+// the least work (every cluster starts with its whole tiles, S(S+1)/2 slice
+// pairs each).  Fills p's tail items and returns true when that shortens the
+// launch's longest cluster; leaves p as it is otherwise.
+static bool tail_schedule(int ntiles, int C, int S, PairParams *p) {
+  const int q = ntiles / C, rt = ntiles % C, W = S * (S + 1) / 2;
+  if (rt == 0 || S < 2 || C > kMaxPairClusters || rt * S > kMaxTailItems) return false;
+  std::vector<int> load(C, q * W);
+  std::vector<std::vector<std::pair<int, int>>> items(C);
+  for (int d = S + 1; d >= 2; --d)
+    for (int t = 0; t < rt; ++t) {
+      int best = 0;
+      for (int c = 1; c < C; ++c)
+        if (load[c] < load[best]) best = c;
+      load[best] += d - 1;
+      items[best].emplace_back(q * C + t, d);
+    }
+  int longest = 0;
+  for (int c = 0; c < C; ++c) longest = load[c] > longest ? load[c] : longest;
+  if (longest >= (q + 1) * W) return false;
+  p->whole = q * C;
+  int k = 0;
+  for (int c = 0; c < C; ++c) {
+    p->tail_off[c] = (int16_t)k;
+    for (auto &it : items[c]) {
+      p->tail_L[k] = it.first;
+      p->tail_d[k] = (int8_t)it.second;
+      ++k;
+    }
+  }
+  p->tail_off[C] = (int16_t)k;
+  return true;
+}
+
 // Clusters of the pair kernel (2 CN CTAs) that fit on the device at once,
 // queried once per CN and kept.
 int pair_resident_clusters(int CN, int *clusters) {
@@ -552,25 +625,6 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   cudaLaunchConfig_t cfg = {};
   const int ntiles = (g.P / 2) * (g.Q / CN);
   const int policy = state().pair_launch;
-  int nclusters = ntiles;
-  if (policy & HSUMMA_PAIR_PERSISTENT) {
-    // one cluster per resident slot, each sweeping tiles L = cid, cid + ncl, ...
-    int res = 0;
-    const int st = pair_resident_clusters(CN, &res);
-    if (st != HSUMMA_OK) return st;
-    nclusters = ntiles < res ? ntiles : res;
-  }
-  cfg.gridDim = dim3((unsigned)(2 * CN * nclusters), 1, 1);
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = (unsigned)(2 * CN);
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
   // Long products run one launch per diagonal.  The hardware starts a cluster
   // whenever one finishes, so over many rounds of tiles the clusters resident
   // together drift apart, and with tiles of all S (S+1) / 2 slice pairs the L2
@@ -589,6 +643,29 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
       split == HSUMMA_PAIR_LAUNCH_PER_DIAGONAL ||
       (split == HSUMMA_PAIR_LAUNCH_AUTO && resident > 0 && ntiles >= 24 * resident &&
        (int64_t)(S * (S + 1) / 2) * Kpad >= 15 * 16384);
+  p.whole = ntiles;
+  int nclusters = ntiles;
+  if (policy & HSUMMA_PAIR_PERSISTENT) {
+    // one cluster per resident slot, each sweeping tiles L = cid, cid + ncl, ...
+    int res = 0;
+    const int st = pair_resident_clusters(CN, &res);
+    if (st != HSUMMA_OK) return st;
+    nclusters = ntiles < res ? ntiles : res;
+    // one launch for all diagonals: the part-filled last round is spread
+    // over every resident cluster
+    if (!per_diagonal && tail_schedule(ntiles, res, S, &p)) nclusters = res;
+  }
+  cfg.gridDim = dim3((unsigned)(2 * CN * nclusters), 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)(2 * CN);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
   for (int d = 2; d <= S + 1;) {
     p.d_lo = d;
     p.d_hi = per_diagonal ? d : S + 1;
