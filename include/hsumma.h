@@ -361,7 +361,9 @@ int hsumma_pair_kernel(int enable);
  *   HSUMMA_PAIR_LAUNCH_PER_DIAGONAL  one launch per diagonal d = s + t;
  * or-ing HSUMMA_PAIR_PERSISTENT launches one cluster per resident cluster
  * slot of the device, each sweeping the group tiles cid, cid + ncl, ...,
- * instead of one cluster per group tile.  After hsumma_init the policy is
+ * instead of one cluster per group tile; a launch for all diagonals then
+ * cuts the tiles past its last whole round into one item per diagonal and
+ * deals them to the least-loaded clusters.  After hsumma_init the policy is
  * HSUMMA_PAIR_LAUNCH_AUTO | HSUMMA_PAIR_PERSISTENT.  A negative value only
  * queries.
  * Returns the previous policy, HSUMMA_ERR_ARG for an unknown one, or
