@@ -526,6 +526,9 @@ def main(argv=None):
     t.add_argument("--steps", type=int, default=6000)
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--seed", type=int, default=4003)
+    t.add_argument("--seeds", type=int, default=1,
+                   help="train from this many initialisations (seed, seed + 10, ...) and keep "
+                        "the one that scores best on the validation products")
     t.add_argument("--val", default=os.path.join(TUNING_DIR, "validation.npz"),
                    help="products with every candidate timed (heldout.npz format) that select "
                         "the checkpoint; '' uses the training products' last 10 %% instead")
@@ -548,7 +551,14 @@ def main(argv=None):
         rows = load_samples(a.data)
         if a.val:
             X, y = sample_features(rows)
-            model = train(X, y, a.steps, a.lr, a.seed, val_products=load_heldout(a.val))
+            val = load_heldout(a.val)
+            model = None
+            for i in range(max(1, a.seeds)):
+                m = train(X, y, a.steps, a.lr, a.seed + 10 * i, val_products=val)
+                m["seed"] = np.int64(a.seed + 10 * i)
+                if model is None or m["val_score"] < model["val_score"]:
+                    model = m
+            print(f"kept seed {int(model['seed'])}: validation {float(model['val_score']):.5f}")
         else:
             tr, va = split_by_product(rows)
             X, y = sample_features(tr)
