@@ -431,7 +431,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end (host buffers) measurement")
-    ap.add_argument("--e2e-calls", type=int, default=5,
+    ap.add_argument("--e2e-calls", type=int, default=9,
                     help="timed host-buffer calls (the e2e value is their median)")
     ap.add_argument("--size", type=int, default=N_SIZE,
                     help="n of the n x n x n product (multiple of 256; default 16384)")
