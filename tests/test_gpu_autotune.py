@@ -232,8 +232,9 @@ def test_model_pick_holds_when_retimed():
         ratios.append(t_pick / t_best)
         del A, B, C
     print("RETIMED", [round(r, 3) for r in ratios])
-    # the committed report's worst pick on the large products is 1.29 x the best,
-    # and a large bf16 product's time varies by several per cent from run to run
+    # the stored ratios of these picks reach 1.10, and a large bf16 product's
+    # time varies by several per cent from run to run (a pick stored at 1.05
+    # has re-timed at 1.25)
     assert max(ratios) <= 1.35
     assert math.exp(np.mean(np.log(ratios))) <= 1.10
 
