@@ -426,9 +426,10 @@ int hsumma_host_timeline_blocks(int *rows, int *cols);
  * except for bf16 products whose blocks run on persistent CTA pairs (2 x 1 or
  * 2 x 2 groups, block layout): there every block after the first spans a
  * whole number of rounds of the resident pair clusters, and the first block
- * takes the remaining rows (it is copied in and computed first; the second
- * row block is then copied before the other column blocks of B, and the
- * block products run in the order their operands arrive).  Returns
+ * takes the remaining rows (it is copied in and computed first; every row
+ * block of A is then copied before the other column blocks of B, and the
+ * block products sweep column block 0 down the row blocks and the next one
+ * back up, so that the last block of C copied out is a small one).  Returns
  * HSUMMA_ERR_ARG on a null pointer. */
 int hsumma_host_row_blocks(int64_t *h_row0, int max, int *h_count);
 

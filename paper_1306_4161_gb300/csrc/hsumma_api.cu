@@ -670,9 +670,7 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
     return end - row0[r];
   };
   auto col_count = [&](int c) { return (N - c * cols) < cols ? (N - c * cols) : cols; };
-  // A small first row block (rows in whole rounds) is followed by the second
-  // row block before the other column blocks of B, and the block products run
-  // in the order their operands arrive (r-major among equals)
+  // a small first row block: the row blocks are in whole rounds (see below)
   const bool small_first = R > 1 && procs[0] < procs[1];
   // ordering events: [0] the caller's earlier work, [1] all copied back,
   // [2 + c] B_c copied, [2 + Cb + r] A_r copied, [2 + Cb + R + (r Cb + c)] C_rc computed
@@ -719,20 +717,33 @@ static int gemm_host_pipelined(int64_t M, int64_t N, int64_t K, const double *hA
   int rank_a[kMaxHostBlocks], rank_b[kMaxHostColBlocks], nrank = 0;
   auto in_b = [&](int c) { rank_b[c] = nrank++; return copy_b(c); };
   auto in_a = [&](int r) { rank_a[r] = nrank++; return copy_a(r); };
-  if (e == cudaSuccess) e = in_b(0);
-  if (e == cudaSuccess) e = in_a(0);
-  if (small_first && e == cudaSuccess) e = in_a(1);
-  for (int c = 1; c < Cb && e == cudaSuccess; ++c) e = in_b(c);
-  for (int r = small_first ? 2 : 1; r < R && e == cudaSuccess; ++r) e = in_a(r);
-  if (e != cudaSuccess) return fail(e, "copy operands in");
   int order[kMaxHostBlocks * kMaxHostColBlocks], nord = 0;
-  for (int r = 0; r < R; ++r)
-    for (int c = 0; c < Cb; ++c) order[nord++] = r * Cb + c;
-  auto ready = [&](int rc) {
-    const int ra = rank_a[rc / Cb], rb = rank_b[rc % Cb];
-    return ra > rb ? ra : rb;
-  };
-  std::stable_sort(order, order + nord, [&](int x, int y) { return ready(x) < ready(y); });
+  if (small_first) {
+    // B_0, every row block of A, then the other column blocks of B; the
+    // products sweep column block 0 down the row blocks and each further
+    // column block back up and down, so the last one is a small first-row
+    // block's (its block of C is the last and shortest copy out)
+    if (e == cudaSuccess) e = in_b(0);
+    for (int r = 0; r < R && e == cudaSuccess; ++r) e = in_a(r);
+    for (int c = 1; c < Cb && e == cudaSuccess; ++c) e = in_b(c);
+    for (int c = 0; c < Cb; ++c)
+      for (int i = 0; i < R; ++i) order[nord++] = (c % 2 ? R - 1 - i : i) * Cb + c;
+  } else {
+    // B_0, A_0, the other column blocks of B, the other row blocks of A; the
+    // products in the order their operands arrive (r-major among equals)
+    if (e == cudaSuccess) e = in_b(0);
+    if (e == cudaSuccess) e = in_a(0);
+    for (int c = 1; c < Cb && e == cudaSuccess; ++c) e = in_b(c);
+    for (int r = 1; r < R && e == cudaSuccess; ++r) e = in_a(r);
+    for (int r = 0; r < R; ++r)
+      for (int c = 0; c < Cb; ++c) order[nord++] = r * Cb + c;
+    auto ready = [&](int rc) {
+      const int ra = rank_a[rc / Cb], rb = rank_b[rc % Cb];
+      return ra > rb ? ra : rb;
+    };
+    std::stable_sort(order, order + nord, [&](int x, int y) { return ready(x) < ready(y); });
+  }
+  if (e != cudaSuccess) return fail(e, "copy operands in");
 
   // split-path workspace: e (all M), f (all N), the A slices of every row
   // block and the B slices of every column block (each sliced once, at its

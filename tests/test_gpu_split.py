@@ -507,7 +507,9 @@ def test_host_entry_row_blocks_in_whole_rounds():
     # first span whole rounds of the resident pair clusters and the first
     # takes the remaining tile rows; with 40 x 8 processors, two column blocks
     # of 4 and 76 resident clusters that is 2 + 38 processor rows (256 + 4864
-    # rows).  A_1 is copied before B_1, and C matches the oracle bit for bit
+    # rows).  Every row block of A is copied before B_1, the products sweep
+    # column block 0 down and column block 1 back up (the small first row
+    # block's product last), and C matches the oracle bit for bit
     # on sampled entries (every block border among them).
     hs = lib_ready()
     torch_cuda()
@@ -528,7 +530,11 @@ def test_host_entry_row_blocks_in_whole_rounds():
     sizes = [b - a for a, b in zip(row0, row0[1:] + [M])]
     assert sizes[0] < sizes[1] and all(s == sizes[1] for s in sizes[1:-1])
     t = {(nm, r, c): (a, e) for nm, r, c, a, e in tl}
-    assert t[("A in", 1, -1)][1] <= t[("B in", -1, 1)][0] + 1e-3
+    R = len(row0)
+    assert t[("A in", R - 1, -1)][1] <= t[("B in", -1, 1)][0] + 1e-3
+    sweep = [(r, 0) for r in range(R)] + [(r, 1) for r in reversed(range(R))]
+    starts = [t[("product", r, c)][0] for r, c in sweep]
+    assert starts == sorted(starts)
     rows, cols = sample_entries(M, N, 64, 93)
     edges = np.array([min(M - 1, max(0, r + d)) for r in row0 for d in (-1, 0, 1)])
     rows = np.concatenate([rows, edges])
