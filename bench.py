@@ -399,9 +399,32 @@ PROFILE_CASES = {
 }
 
 
+def run_mlp_profile():
+    """The cost model's kernels on the committed training set, for a profiler:
+    two training steps (backward, block reduction, Adam; a forward pass over
+    256 samples after each), then the bf16 pick among the benchmark product's
+    candidates (scoring and argmin)."""
+    import paper_1306_4161_gb300 as hs
+    from paper_1306_4161_gb300 import autotune
+    hs.init(0)
+    rows = autotune.load_samples(autotune.TUNING_DIR)
+    X, y = autotune.sample_features(rows)
+    autotune.train(X, y, steps=2, log=lambda *_: None, X_val=X[:256], y_val=y[:256],
+                   check_every=1)
+    model = autotune.read_model()
+    M, N, K, kind, S = autotune.BENCH_PRODUCT
+    cfgs = hs.candidates(M, N, K, kind, S)
+    j = autotune.pick(model, M, N, K, kind, S, cfgs)
+    print(json.dumps({"case": "mlp", "samples": int(X.shape[0]), "candidates": len(cfgs),
+                      "pick": list(cfgs[j])}), flush=True)
+
+
 def run_profile_case(name):
     """Two products of a small case (seeded uniform inputs), for a profiler
     to capture the second; prints the group shape and the counters."""
+    if name == "mlp":
+        run_mlp_profile()
+        return
     import torch
     import paper_1306_4161_gb300 as hs
     import workloads
@@ -439,7 +462,7 @@ def main():
                     help="comma-separated workload numbers 0..3 (4: block against "
                          "block-cyclic layout): print throughput rows of their "
                          "configurations instead of the benchmark line")
-    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES) + ["mlp"],
                     help="run one small case twice (for a profiler) instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:
