@@ -541,3 +541,34 @@ def test_host_entry_row_blocks_in_whole_rounds():
     cols = np.concatenate([cols, np.resize(np.array([0, 1023, 1024, 2047]), len(edges))])
     want = split.split_entries(A.numpy(), B.numpy(), rows, cols, S, "bf16")
     assert np.array_equal(hC.numpy()[rows, cols], want)
+
+
+@pytest.mark.parametrize("kind,S", [("bf16", 3), ("int8", 4)])
+def test_empty_and_zero_k_split_and_host(kind, S):
+    # K = 0 gives C = 0 (every sum empty); M = 0 or N = 0 gives an empty C;
+    # the same through the host-buffer entry
+    hs = lib_ready()
+    torch = torch_cuda()
+    cfg = dict(P=2, Q=2, G=2, b=64, Bouter=128, kind=kind, slices=S)
+    dA = torch.zeros((256, 0), dtype=torch.float64, device="cuda")
+    dB = torch.zeros((0, 512), dtype=torch.float64, device="cuda")
+    C = torch.full((256, 512), 5.0, dtype=torch.float64, device="cuda")
+    hs.gemm(dA, dB, out=C, **cfg)
+    hs.sync()
+    assert torch.all(C == 0)
+    for M, N in ((0, 512), (256, 0)):
+        dA = torch.ones((M, 64), dtype=torch.float64, device="cuda")
+        dB = torch.ones((64, N), dtype=torch.float64, device="cuda")
+        C = hs.gemm(dA, dB, **cfg)
+        hs.sync()
+        assert C.shape == (M, N)
+    hA = torch.zeros((256, 0), dtype=torch.float64).pin_memory()
+    hB = torch.zeros((0, 512), dtype=torch.float64).pin_memory()
+    hC = np.full((256, 512), 5.0)
+    hs.gemm_host(hA, hB, hC, **cfg)
+    assert np.all(hC == 0)
+    # one row and one column: a 1 x 1 C from a 1 x K by K x 1 product
+    A, B, dA, dB = pair(1, 1, 300, 97, "wide")
+    C = hs.gemm(dA, dB, P=1, Q=1, G=1, b=64, Bouter=64, kind=kind, slices=S)
+    hs.sync()
+    assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, S, kind))
