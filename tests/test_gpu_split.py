@@ -572,3 +572,29 @@ def test_empty_and_zero_k_split_and_host(kind, S):
     C = hs.gemm(dA, dB, P=1, Q=1, G=1, b=64, Bouter=64, kind=kind, slices=S)
     hs.sync()
     assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, S, kind))
+
+
+@pytest.mark.parametrize("kind,P,Q,G,pair_kernel", [
+    ("bf16", 4, 2, 4, True),      # 2 x 1 groups on CTA pairs
+    ("bf16", 4, 2, 8, False),     # one CTA per processor
+    ("int8", 4, 4, 4, False),
+])
+def test_one_slice_and_slice_count_limits(kind, P, Q, G, pair_kernel):
+    # S = 1: the single pair (1, 1), one diagonal, bit for bit; S = 0 and one
+    # more than the kind allows are rejected
+    hs = lib_ready()
+    A, B, dA, dB = pair(500, 400, 300, 101, "wide")
+    was = hs.pair_kernel(pair_kernel)
+    try:
+        C = hs.gemm(dA, dB, P=P, Q=Q, G=G, b=64 if kind == "bf16" else 128,
+                    Bouter=128 if kind == "bf16" else 256, kind=kind, slices=1)
+        hs.sync()
+    finally:
+        hs.pair_kernel(was)
+    assert np.array_equal(C.cpu().numpy(), split.split_gemm(A, B, 1, kind))
+    top = 7 if kind == "bf16" else 8
+    for S in (0, top + 1):
+        with pytest.raises(hs.HsummaError) as ei:
+            hs.gemm(dA, dB, P=P, Q=Q, G=G, b=64 if kind == "bf16" else 128,
+                    Bouter=128 if kind == "bf16" else 256, kind=kind, slices=S)
+        assert ei.value.status == -1
