@@ -45,6 +45,13 @@
 // 4..11 drain their CTA's 128 rows into exact int32 planes (a warp reads the
 // tensor-memory lanes of its quarter, warp mod 4; warps 4..7 and 8..11 cover
 // the 128 rows for the two column halves).
+//
+// Work: a persistent launch runs one cluster per resident slot; each sweeps
+// whole group tiles round robin with every diagonal of the launch, and a
+// launch for all diagonals cuts the tiles of its last, part-filled round into
+// one item per diagonal, dealt on the host to the least-loaded clusters (each
+// item writes its own planes, so no sums meet across clusters).  All three
+// roles walk the same item sequence.
 #include <utility>
 #include <vector>
 
