@@ -342,11 +342,14 @@ def run_table(sections):
             emit(workload="rect_24576x16384x32768", path="fp64", cfg=f"12x16 G={G} b=32 B=128",
                  cluster=hs.group_shape(12, 16, G)[2:], ms=ms, tflops=tf,
                  frac_of_dmma=tf / dmma)
-        for how in ("model", "timed"):
-            cfg, _ = hs.choose(A, B, C, kind="bf16", slices=7, policy=how)
+        # the automatic choice verifies by timing here: S = 7 lies outside the
+        # cost model's trained slice counts for bf16
+        for policy in ("model", "auto", "timed"):
+            cfg, how = hs.choose(A, B, C, kind="bf16", slices=7, policy=policy)
             ms, st = timed(lambda: hs.gemm(A, B, out=C, kind="bf16", slices=7, P=cfg[0],
                                            Q=cfg[1], G=cfg[2], b=cfg[3], Bouter=cfg[4]))
-            emit(workload="rect_24576x16384x32768", path="bf16", slices=7, chosen_by=how,
+            emit(workload="rect_24576x16384x32768", path="bf16", slices=7, policy=policy,
+                 chosen_by=how,
                  cfg=cfg, ms=ms, tflops=2 * M * N * K / ms / 1e9, stage_ms=st)
     if 4 in sections:
         # the two layouts of the grid at the same P x Q: block-checkerboard

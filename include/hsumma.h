@@ -262,7 +262,8 @@ int hsumma_mlp_pick(int n, const float *d_theta, const float *d_X,
 
 /* Load a trained model into the library (host arrays: 9089 parameters, the
  * 10 feature means and 10 standard deviations) for hsumma_gemm's automatic
- * choice; NULL theta unloads it.  Either way every cached choice is dropped. */
+ * choice; NULL theta unloads it.  Either way every cached choice and the
+ * trained range (hsumma_mlp_range) are dropped. */
 int hsumma_mlp_load(const float *h_theta, const float *h_mean,
                     const float *h_std);
 
@@ -291,11 +292,12 @@ int hsumma_features(int64_t M, int64_t N, int64_t K, int mode,
 
 /* Choice policies and how a choice was made. */
 enum {
-  HSUMMA_CHOOSE_AUTO = 0,     /* cached, else the model, else timing */
+  HSUMMA_CHOOSE_AUTO = 0,     /* cached, else the model (verified by timing outside its
+                                 trained range, hsumma_mlp_range), else timing */
   HSUMMA_CHOOSE_MODEL = 1,    /* the loaded model (HSUMMA_ERR_UNSUPPORTED if none) */
   HSUMMA_CHOOSE_TIMED = 2,    /* exhaustive timing, always */
   HSUMMA_CHOOSE_ANALYTIC = 3, /* the fitted analytic model (hsumma_analytic_load) */
-  HSUMMA_CHOOSE_VERIFIED = 4  /* the model's three best-predicted candidates, timed */
+  HSUMMA_CHOOSE_VERIFIED = 4  /* the model's four best-predicted candidates, timed */
 };
 enum {
   HSUMMA_CHOSEN_CACHED = 0,
@@ -323,6 +325,23 @@ enum {
 int hsumma_analytic_terms(int64_t M, int64_t N, int64_t K, int mode,
                           const int *h_cfg, int n, double *h_terms);
 
+/* The product features the loaded model was trained on, per mode kind:
+ * h_lo and h_hi hold 3 x 10 floats (kind-major, the features of
+ * hsumma_features), of which log2 M, log2 N, log2 K and S are used.  A product
+ * outside them for its kind (by more than 1e-3) makes the automatic choice
+ * (HSUMMA_CHOOSE_AUTO) time candidates instead of taking the model's pick (the
+ * model extrapolates there; hsumma_choose says which).  A kind without training samples has lo > hi.
+ * NULL clears the range (the model is then used everywhere), and so do
+ * hsumma_mlp_load and hsumma_finalize: load the range after its model.  Drops
+ * every cached choice.  Host only. */
+int hsumma_mlp_range(const float *h_lo, const float *h_hi);
+
+/* *h_inside = 1 when the product (M, N, K, mode) lies inside the loaded
+ * trained range for its kind (or no range is loaded), else 0: whether the
+ * automatic choice takes the model's pick or verifies it by timing.  Host
+ * only. */
+int hsumma_mlp_in_range(int64_t M, int64_t N, int64_t K, int mode, int *h_inside);
+
 /* Coefficients of the analytic model, 5 per mode kind (FP64, INT8, BF16),
  * h_coef[kind * 5 + term] (seconds per unit of each term); NULL unloads.
  * Drops every cached choice. */
@@ -333,10 +352,14 @@ int hsumma_analytic_load(const double *h_coef);
  * every candidate on the device (bf16) and takes the smallest predicted time;
  * timing runs every candidate once on these operands, after one untimed run,
  * overwriting C, and takes the fastest that launched; the verified policy
- * times only the model's three best-predicted candidates the same way.  Either way the stream
- * is synchronised and the choice is cached per (M, N, K, mode) until the next
- * hsumma_mlp_load or hsumma_finalize.  Operands follow hsumma_gemm's rules
- * (they are only read by timing). */
+ * times only the model's four best-predicted candidates the same way.  The
+ * automatic choice, for a product outside the model's trained range, times
+ * those four and the best-predicted candidate of every cluster shape
+ * (hsumma_group_shape) they leave out.
+ * Either way the stream is synchronised and the choice is cached per
+ * (M, N, K, mode) until the next hsumma_mlp_load, hsumma_mlp_range or
+ * hsumma_finalize.  Operands follow hsumma_gemm's rules (they are only read by
+ * timing). */
 int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *d_A,
                   int64_t lda, const double *d_B, int64_t ldb, double *d_C,
                   int64_t ldc, int mode, int policy, int *h_cfg, int *h_how,

@@ -75,6 +75,8 @@ _SIGS = {
                          ctypes.c_float, ctypes.c_float, _vp], _i32),
     "hsumma_mlp_pick": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hsumma_mlp_load": ([_vp, _vp, _vp], _i32),
+    "hsumma_mlp_range": ([_vp, _vp], _i32),
+    "hsumma_mlp_in_range": ([_i64, _i64, _i64, _i32, _vp], _i32),
     "hsumma_pair_kernel": ([_i32], _i32),
     "hsumma_pair_launch": ([_i32], _i32),
     "hsumma_selftest_timeout": ([ctypes.c_longlong, _vp], _i32),
@@ -350,7 +352,9 @@ def features(M, N, K, cfgs, kind="fp64", slices=0):
 def choose(A, B, C=None, *, kind="fp64", slices=0, policy="auto", stream=_DEFAULT):
     """(P, Q, G, b, Bouter) that gemm(A, B) runs with when asked to choose, and
     how it was chosen ("cached", "model", "timed", "analytic" or "verified": the
-    model's three best-predicted candidates timed).  Timing overwrites C."""
+    model's four best-predicted candidates timed, and outside the model's
+    trained range the best of every other cluster shape too).  Timing
+    overwrites C."""
     import torch
     _check_f64(A, "A")
     _check_f64(B, "B")
@@ -382,6 +386,30 @@ def load_model(theta, mean, std):
     if th.size != N_MLP_PARAMS or mu.size != 10 or sd.size != 10:
         raise ValueError("a cost model has 9089 parameters and 10 means and deviations")
     _check(lib().hsumma_mlp_load(th.ctypes.data, mu.ctypes.data, sd.ctypes.data))
+
+
+def load_model_range(lo, hi):
+    """The product features (3 kinds x 10, as features() gives them) the
+    loaded model was trained on; outside them the automatic choice is verified
+    by timing.  lo=None clears it."""
+    import numpy as np
+    if lo is None:
+        _check(lib().hsumma_mlp_range(None, None))
+        return
+    a = np.ascontiguousarray(lo, dtype=np.float32)
+    b = np.ascontiguousarray(hi, dtype=np.float32)
+    if a.shape != (3, 10) or b.shape != (3, 10):
+        raise ValueError("a trained range is 3 kinds x 10 features, low and high")
+    _check(lib().hsumma_mlp_range(a.ctypes.data, b.ctypes.data))
+
+
+def in_trained_range(M, N, K, kind="fp64", slices=0) -> bool:
+    """Whether the product lies inside the loaded model's trained range (the
+    automatic choice takes the model's pick there, else verifies it by timing);
+    True when no range is loaded."""
+    inside = ctypes.c_int()
+    _check(lib().hsumma_mlp_in_range(M, N, K, mode_code(kind, slices), ctypes.byref(inside)))
+    return bool(inside.value)
 
 
 def stage_timing(enable: bool):

@@ -19,6 +19,7 @@ it leaves the grid and the panel sizes to the user.  This module
     python -m paper_1306_4161_gb300.autotune collect --out DIR
     python -m paper_1306_4161_gb300.autotune collect-large --out DIR
     python -m paper_1306_4161_gb300.autotune train --data DIR --out DIR/cost_model.npz
+    python -m paper_1306_4161_gb300.autotune range --data DIR --model DIR/cost_model.npz
     python -m paper_1306_4161_gb300.autotune evaluate --data DIR --model DIR/cost_model.npz
 """
 from __future__ import annotations
@@ -37,6 +38,8 @@ import paper_1306_4161_gb300 as hs
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING_DIR = os.path.join(HERE, "tuning")
 MODEL_PATH = os.path.join(TUNING_DIR, "cost_model.npz")
+# candidates the library's verified policy times (the model's best-predicted)
+VERIFIED_CANDIDATES = 4
 KIND_CODE = {"fp64": 0, "int8": 1, "bf16": 2}
 KIND_NAME = {v: k for k, v in KIND_CODE.items()}
 LAYERS = ((10, 64), (64, 64), (64, 64), (64, 1))   # (fan_in, fan_out), row-major W[out][in]
@@ -395,7 +398,21 @@ def load_into_library(path=MODEL_PATH):
     hs.load_model(m["theta"], m["mean"], m["std"])
     if "analytic" in m:
         hs.load_analytic(m["analytic"])
+    if "range_lo" in m:
+        hs.load_model_range(m["range_lo"], m["range_hi"])
     return m
+
+
+def trained_range(X):
+    """Per mode kind (feature 8), the smallest and largest value of each
+    feature over the training rows X (lo > hi for a kind without rows)."""
+    lo = np.full((3, X.shape[1]), np.inf, dtype=np.float32)
+    hi = np.full((3, X.shape[1]), -np.inf, dtype=np.float32)
+    for k in range(3):
+        sel = X[np.round(X[:, 8]).astype(int) == k]
+        if len(sel):
+            lo[k], hi[k] = sel.min(axis=0), sel.max(axis=0)
+    return lo, hi
 
 
 # ---------------------------------------------------------------- analytic model
@@ -478,8 +495,8 @@ def _stats(r):
 def evaluate(model, heldout, picker=None, ranker=None):
     """Ratios to the exhaustive best (the fastest candidate), over the held-out
     products, overall and per kind, of: the model's pick ("model"), the fastest
-    of its three best-predicted candidates by the timed table (the verified
-    policy, "verified"), the paper's static setting G = sqrt(p), b = B
+    of its VERIFIED_CANDIDATES best-predicted candidates by the timed table (the
+    verified policy, "verified"), the paper's static setting G = sqrt(p), b = B
     ("paper_rule"), the paper's tuning by a few runs ("sampled") and, when the
     model carries its coefficients, the fitted analytic model ("analytic")."""
     cfgs_of = lambda h: [tuple(int(v) for v in c) for c in h["cfg"]]
@@ -496,7 +513,7 @@ def evaluate(model, heldout, picker=None, ranker=None):
         r = {"kind": h["kind"], "model": ms[picker(h)] / best, "paper_rule": h["base_ms"] / best,
              "sampled": ms[sampled_pick(h)] / best}
         if ranker is not None:
-            r["verified"] = float(min(ms[i] for i in ranker(h)[:3])) / best
+            r["verified"] = float(min(ms[i] for i in ranker(h)[:VERIFIED_CANDIDATES])) / best
         if coef is not None:
             r["analytic"] = ms[analytic_pick(coef, h)] / best
         rows.append(r)
@@ -540,6 +557,11 @@ def main(argv=None):
     cl.add_argument("--seed", type=int, default=4000)
     cl.add_argument("--samples-name", default="samples_large.npz",
                     help="file of the training samples (every samples_large*.npz trains)")
+    r = sub.add_parser("range", help="record the training samples' feature range in a "
+                                     "trained model (the automatic choice verifies by timing "
+                                     "outside it)")
+    r.add_argument("--data", default=TUNING_DIR)
+    r.add_argument("--model", default=MODEL_PATH)
     e = sub.add_parser("evaluate")
     e.add_argument("--data", default=TUNING_DIR)
     e.add_argument("--model", default=MODEL_PATH)
@@ -565,7 +587,13 @@ def main(argv=None):
             Xv, yv = sample_features(va)
             model = train(X, y, a.steps, a.lr, a.seed, X_val=Xv, y_val=yv)
         model["analytic"] = fit_analytic(rows)
+        model["range_lo"], model["range_hi"] = trained_range(sample_features(rows)[0])
         save_model(model, a.out)
+    elif a.cmd == "range":
+        model = read_model(a.model)
+        model["range_lo"], model["range_hi"] = trained_range(
+            sample_features(load_samples(a.data))[0])
+        save_model(model, a.model)
     elif a.cmd == "collect-large":
         collect_large(a.out, a.products, a.per_shape, a.heldout, a.seed,
                       samples_name=a.samples_name)

@@ -116,12 +116,31 @@ std::map<std::tuple<int64_t, int64_t, int64_t, int>, Cand> g_cache;
 //   [0] computation, [1] latency (messages x depth), [2] bandwidth (words x
 //   depth), [3] slicing volume (M + N) K S (split paths), [4] one per call.
 constexpr int kAnalyticTerms = 5;
-// candidates the verified policy times: the model's best-predicted ones (on the
-// held-out products three bring the pick from 1.020 / 1.039 to 1.005 / 1.008
-// of the exhaustive best)
-constexpr int kVerifiedCandidates = 3;
+// candidates the verified policy times: the model's best-predicted ones.  On
+// the validation products (every candidate timed) the pick's geometric-mean
+// ratio to the exhaustive best is 1.0033 / 1.0024 / 1.0009 / 1.0005 with 2 / 3
+// / 4 / 5 timed; four keeps nearly all of the gain for one run fewer than five.
+constexpr int kVerifiedCandidates = 4;
 double g_analytic[3][kAnalyticTerms];
 bool g_analytic_loaded = false;
+// the product features (log2 M, N, K and S) the loaded model was trained on,
+// per mode kind: outside them the automatic choice verifies by timing
+float g_range_lo[3][kModelFeatures], g_range_hi[3][kModelFeatures];
+bool g_range_loaded = false;
+constexpr int kRangeFeatures[4] = {0, 1, 2, 9};
+
+// Whether (M, N, K, S) of this kind lies inside the trained range (true when
+// no range is loaded).
+bool inside_trained_range(int64_t M, int64_t N, int64_t K, int kind, int S, const Cand &c) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_range_loaded) return true;
+  float x[kModelFeatures];
+  features(M, N, K, kind, S, c, x);
+  for (int f : kRangeFeatures)
+    if (!(x[f] >= g_range_lo[kind][f] - 1e-3f && x[f] <= g_range_hi[kind][f] + 1e-3f))
+      return false;
+  return true;
+}
 
 void analytic_terms(int64_t M, int64_t N, int64_t K, int kind, int S, const Cand &c,
                     double *f) {
@@ -289,6 +308,11 @@ void forget_choices() {
   g_cache.clear();
 }
 
+void forget_model_range() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_range_loaded = false;
+}
+
 }  // namespace hs
 
 using namespace hs;
@@ -388,12 +412,38 @@ int hsumma_choose(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
       }
     }
     *how = HSUMMA_CHOSEN_ANALYTIC;
-  } else if (policy == HSUMMA_CHOOSE_VERIFIED) {
-    // the model's best-predicted candidates, timed on these operands
+  } else if (policy == HSUMMA_CHOOSE_VERIFIED ||
+             (policy == HSUMMA_CHOOSE_AUTO && have_model &&
+              !inside_trained_range(M, N, K, kind, S, cands[0]))) {
+    // the model's best-predicted candidates, timed on these operands (the
+    // automatic choice too, for a product outside what the model was trained on)
     std::vector<int> ranked;
     st = pick_by_model(M, N, K, kind, S, cands, s, &bi, &ranked);
     if (st != HSUMMA_OK) return st;
-    ranked.resize(std::min(ranked.size(), (size_t)kVerifiedCandidates));
+    const bool extrapolating = policy == HSUMMA_CHOOSE_AUTO;
+    std::vector<int> timed(ranked.begin(),
+                           ranked.begin() + std::min(ranked.size(), (size_t)kVerifiedCandidates));
+    if (extrapolating) {
+      // outside the trained range the model may misjudge which kernel family
+      // (cluster shape) wins, not only the panel widths: time the
+      // best-predicted candidate of every cluster shape the four leave out
+      std::vector<std::pair<int, int>> seen;
+      auto shape_of = [&](int i) {
+        int I, J, cm = 1, cn = 1;
+        if (hsumma_group_shape(cands[i].P, cands[i].Q, cands[i].G, &I, &J, &cm, &cn) !=
+            HSUMMA_OK)
+          cm = cn = 1;
+        return std::make_pair(cm, cn);
+      };
+      for (int i : timed) seen.push_back(shape_of(i));
+      for (size_t r = timed.size(); r < ranked.size(); ++r) {
+        const auto sh = shape_of(ranked[r]);
+        if (std::find(seen.begin(), seen.end(), sh) != seen.end()) continue;
+        seen.push_back(sh);
+        timed.push_back(ranked[r]);
+      }
+    }
+    ranked.swap(timed);
     st = pick_by_timing(M, N, K, A, lda, B, ldb, C, ldc, mode, cands, s, &bi, &ranked);
     if (st != HSUMMA_OK) return st;
     *how = HSUMMA_CHOSEN_VERIFIED;
@@ -430,6 +480,36 @@ int hsumma_analytic_terms(int64_t M, int64_t N, int64_t K, int mode, const int *
     }
     analytic_terms(M, N, K, kind, S, c, terms + (size_t)i * kAnalyticTerms);
   }
+  return HSUMMA_OK;
+}
+
+int hsumma_mlp_range(const float *lo, const float *hi) {
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!lo || !hi) {
+      g_range_loaded = false;
+    } else {
+      for (int k = 0; k < 3; ++k)
+        for (int f = 0; f < kModelFeatures; ++f) {
+          g_range_lo[k][f] = lo[k * kModelFeatures + f];
+          g_range_hi[k][f] = hi[k * kModelFeatures + f];
+        }
+      g_range_loaded = true;
+    }
+  }
+  forget_choices();
+  return HSUMMA_OK;
+}
+
+int hsumma_mlp_in_range(int64_t M, int64_t N, int64_t K, int mode, int *inside) {
+  int kind, S;
+  int st = decode_mode(mode, &kind, &S);
+  if (st != HSUMMA_OK) return st;
+  if (!inside || M < 0 || N < 0 || K < 0) {
+    set_error("bad arguments");
+    return HSUMMA_ERR_ARG;
+  }
+  *inside = inside_trained_range(M, N, K, kind, S, Cand{1, 1, 1, 1, 1}) ? 1 : 0;
   return HSUMMA_OK;
 }
 

@@ -319,6 +319,7 @@ void hsumma_finalize(void) {
     g_stage_on = false;
   }
   forget_choices();
+  forget_model_range();
   g_state = DeviceState();
   g_init = false;
 }

@@ -139,6 +139,8 @@ int mlp_pick_device(int n, const float *d_theta, const float *d_X, float *d_pred
                     int32_t *d_best, cudaStream_t s);
 // Automatic configuration (autotune.cu): forget every cached choice.
 void forget_choices();
+// drops the trained range of the cost model (a new model, or none, is loaded)
+void forget_model_range();
 // Drop the cached device addresses of hsumma_mlp_backward_noalloc's scratch
 // (mlp.cu): they are looked up again on the next call on each device.
 void forget_noalloc_scratch();

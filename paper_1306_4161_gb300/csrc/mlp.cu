@@ -466,6 +466,7 @@ int hsumma_mlp_pick(int n, const float *theta, const float *X, float *pred, int3
 }
 
 int hsumma_mlp_load(const float *theta, const float *mean, const float *stdv) {
+  forget_model_range();
   if (!theta) {
     g_model.loaded = false;
     forget_choices();

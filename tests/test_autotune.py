@@ -121,7 +121,7 @@ def test_committed_model_on_held_out_products_by_oracle_network():
     assert rep["model"]["n"] == 200
     assert rep["model"]["geomean"] <= 1.10
     assert rep["model"]["geomean"] < rep["paper_rule"]["geomean"]
-    # timing the three best-predicted candidates (the verified policy) only helps
+    # timing the four best-predicted candidates (the verified policy) only helps
     assert rep["verified"]["geomean"] <= rep["model"]["geomean"]
     assert rep["verified"]["geomean"] <= 1.02
 
@@ -195,3 +195,30 @@ def test_analytic_fit_and_policies_on_committed_data():
     g = {k: rep[k]["geomean"] for k in ("model", "analytic", "sampled", "paper_rule")}
     assert g["analytic"] < g["sampled"] < g["paper_rule"]
     assert g["model"] <= g["analytic"] * 1.01
+
+
+def test_committed_model_records_its_trained_range():
+    """The committed model carries the per-kind range of its training
+    samples' features; the automatic choice takes the model's pick inside it
+    and verifies by timing outside (a slice count or size it never saw)."""
+    m = autotune.read_model()
+    assert "range_lo" in m, "the committed model has no trained range"
+    lo, hi = autotune.trained_range(
+        autotune.sample_features(autotune.load_samples(autotune.TUNING_DIR))[0])
+    assert np.array_equal(m["range_lo"], lo) and np.array_equal(m["range_hi"], hi)
+    assert (lo[:, 9] == [0, 3, 3]).all() and (hi[:, 9] == [0, 8, 6]).all()
+    hs.load_model_range(m["range_lo"], m["range_hi"])
+    try:
+        assert hs.in_trained_range(16384, 16384, 16384, "bf16", 5)      # the bench product
+        assert hs.in_trained_range(2048, 3072, 1536, "bf16", 5)
+        assert not hs.in_trained_range(24576, 16384, 32768, "bf16", 7)  # S = 7 never trained
+        assert not hs.in_trained_range(1536, 1536, 1536, "bf16", 7)
+        assert not hs.in_trained_range(300, 520, 200, "bf16", 4)        # below the sizes
+        assert hs.in_trained_range(2048, 2048, 2048, "fp64")
+        assert not hs.in_trained_range(16384, 16384, 16384, "fp64")     # fp64 trained to ~4k
+        assert hs.in_trained_range(8192, 1024, 4096, "int8", 8)
+        with pytest.raises(ValueError):
+            hs.load_model_range(np.zeros((2, 10)), np.zeros((2, 10)))
+    finally:
+        hs.load_model_range(None, None)
+    assert hs.in_trained_range(24576, 16384, 32768, "bf16", 7)          # no range: the model

@@ -155,7 +155,47 @@ def test_automatic_choice_by_timing_without_model():
     assert hs.choose(dA, dB, kind="bf16", slices=4)[1] == "cached"
     from paper_1306_4161_gb300 import autotune
     autotune.load_into_library()
-    assert hs.choose(dA, dB, kind="bf16", slices=4)[1] == "model"   # loading drops the cache
+    # loading drops the cache; 300 x 520 x 200 lies below the model's trained
+    # sizes, so the automatic choice verifies the model's pick by timing
+    assert hs.choose(dA, dB, kind="bf16", slices=4)[1] == "verified"
+    hs.load_model_range(None, None)
+    assert hs.choose(dA, dB, kind="bf16", slices=4)[1] == "model"
+    autotune.load_into_library()
+
+
+def test_automatic_choice_verifies_outside_the_trained_range():
+    """S = 7 was never trained on (bf16 samples hold S = 3..6): the automatic
+    choice times the model's four best-predicted candidates there, and the
+    best-predicted of every cluster shape they leave out, and caches that
+    pick; inside the range (S = 5, same sizes) it takes the model's."""
+    hs = lib_ready()
+    torch = torch_cuda()
+    from paper_1306_4161_gb300 import autotune
+    if not os.path.exists(autotune.MODEL_PATH):
+        pytest.skip("no committed model")
+    autotune.load_into_library()
+    n = 1536
+    A = workloads.matrix(n, n, 94, "uniform")
+    B = workloads.matrix(n, n, 95, "uniform")
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    cfg, how = hs.choose(dA, dB, kind="bf16", slices=7)
+    cands = hs.candidates(n, n, n, "bf16", 7)
+    order = autotune.ranked(autotune.read_model(), n, n, n, "bf16", 7, cands)
+    timed, shapes = [], set()
+    for r, i in enumerate(order):
+        sh = hs.group_shape(*cands[i][:3])[2:]
+        if r < autotune.VERIFIED_CANDIDATES or sh not in shapes:
+            timed.append(cands[i])
+        shapes.add(sh)
+    assert how == "verified" and cfg in timed
+    assert hs.choose(dA, dB, kind="bf16", slices=7) == (cfg, "cached")
+    cfg5, how5 = hs.choose(dA, dB, kind="bf16", slices=5)
+    assert how5 == "model"
+    # whatever the configuration, the split product is the same bits
+    C = hs.gemm(dA, dB, kind="bf16", slices=7)
+    C1 = hs.gemm(dA, dB, kind="bf16", slices=7, P=12, Q=6, G=36, b=64, Bouter=256)
+    hs.sync()
+    assert torch.equal(C, C1)
 
 
 def test_library_loads_the_shipped_model():
@@ -262,8 +302,8 @@ def test_analytic_policy_picks_and_computes():
     autotune.load_into_library()
 
 
-def test_verified_policy_times_the_models_three_best():
-    # the verified policy: the loaded model's three best-predicted candidates,
+def test_verified_policy_times_the_models_four_best():
+    # the verified policy: the loaded model's four best-predicted candidates,
     # each timed once on the operands; the pick is one of them, it computes the
     # product exactly, and it is cached for the automatic choice
     hs = lib_ready()
@@ -275,7 +315,8 @@ def test_verified_policy_times_the_models_three_best():
     M, N, K = 1536, 2304, 1280
     dA, dB, want = _exact_pair(torch, M, N, K, 97)
     cands = hs.candidates(M, N, K, "bf16", 4)
-    top = [cands[i] for i in autotune.ranked(model, M, N, K, "bf16", 4, cands)[:3]]
+    top = [cands[i] for i in
+           autotune.ranked(model, M, N, K, "bf16", 4, cands)[:autotune.VERIFIED_CANDIDATES]]
     cfg, how = hs.choose(dA, dB, kind="bf16", slices=4, policy="verified")
     assert how == "verified" and cfg in top
     C = hs.gemm(dA, dB, P=cfg[0], Q=cfg[1], G=cfg[2], b=cfg[3], Bouter=cfg[4], kind="bf16",
