@@ -35,10 +35,10 @@ sys.path.insert(0, ROOT)
 
 N_SIZE = 16384
 METRIC = "FP64-accurate TFLOP/s at n=16384, split-precision vs native FP64, % of roofline"
-SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=512, kind="bf16", slices=5)
+SPLIT = dict(P=128, Q=64, G=4096, b=64, Bouter=512, kind="bf16", slices=4)
 NATIVE = dict(P=128, Q=128, G=8192, b=32, Bouter=128)
 WORKLOAD = ("split_vs_fp64_16384: M=N=K=16384, A,B uniform[-1,1] (SplitMix64 seeds 1002/2002), "
-            "bf16 slices S=5 (15 pair products), virtual grid 128x64 of 128x256 blocks, "
+            "bf16 slices S=4 of 9-bit digits (10 pair products), virtual grid 128x64 of 128x256 blocks, "
             "G=4096 groups of 2x1 (each group one CTA pair: the in-group B broadcast is the "
             "two-SM MMA; persistent clusters, one launch per diagonal), b=64, B=512 "
             "(owner L2 prefetch); "
@@ -56,7 +56,7 @@ def configure(n):
     SPLIT = dict(SPLIT, P=n // 128, Q=n // 256, G=max(1, (n // 128) * (n // 256) // 2))
     NATIVE = dict(NATIVE, P=n // 128, Q=n // 128, G=max(1, (n // 128) ** 2 // 2))
     if n != 16384:
-        WORKLOAD = (f"split_vs_fp64_{n}: M=N=K={n}, bf16 S=5, grid {n // 128}x{n // 256} of "
+        WORKLOAD = (f"split_vs_fp64_{n}: M=N=K={n}, bf16 S={SPLIT['slices']}, grid {n // 128}x{n // 256} of "
                     f"128x256 blocks, G={SPLIT['G']} (2x1 groups, CTA pairs), b=64, "
                     f"B={SPLIT['Bouter']}; native fp64 grid {n // 128}x{n // 128}, "
                     f"G={NATIVE['G']}")
@@ -342,13 +342,12 @@ def run_table(sections):
             emit(workload="rect_24576x16384x32768", path="fp64", cfg=f"12x16 G={G} b=32 B=128",
                  cluster=hs.group_shape(12, 16, G)[2:], ms=ms, tflops=tf,
                  frac_of_dmma=tf / dmma)
-        # the automatic choice verifies by timing here: S = 7 lies outside the
-        # cost model's trained slice counts for bf16
+        # S = 5: the fewest 9-bit slices within 2 K u on these spiked columns
         for policy in ("model", "auto", "timed"):
-            cfg, how = hs.choose(A, B, C, kind="bf16", slices=7, policy=policy)
-            ms, st = timed(lambda: hs.gemm(A, B, out=C, kind="bf16", slices=7, P=cfg[0],
+            cfg, how = hs.choose(A, B, C, kind="bf16", slices=5, policy=policy)
+            ms, st = timed(lambda: hs.gemm(A, B, out=C, kind="bf16", slices=5, P=cfg[0],
                                            Q=cfg[1], G=cfg[2], b=cfg[3], Bouter=cfg[4]))
-            emit(workload="rect_24576x16384x32768", path="bf16", slices=7, policy=policy,
+            emit(workload="rect_24576x16384x32768", path="bf16", slices=5, policy=policy,
                  chosen_by=how,
                  cfg=cfg, ms=ms, tflops=2 * M * N * K / ms / 1e9, stage_ms=st)
     if 4 in sections:
@@ -361,9 +360,11 @@ def run_table(sections):
         for P, Q, G, note in ((128, 64, 4096, "aligned"), (120, 60, 3600, "ragged, many waves"),
                               (12, 12, 72, "ragged, one wave")):
             for layout in ("block", "cyclic"):
-                cfg = dict(P=P, Q=Q, G=G, b=64, Bouter=512, kind="bf16", slices=5, layout=layout)
+                cfg = dict(P=P, Q=Q, G=G, b=64, Bouter=512, kind="bf16", slices=SPLIT["slices"],
+                           layout=layout)
                 ms, st = timed(lambda: hs.gemm(A, B, out=C, **cfg), reps=2)
-                unit = 15 * 2 * n ** 3 / st[2] / 1e9
+                npairs = SPLIT["slices"] * (SPLIT["slices"] + 1) // 2
+                unit = npairs * 2 * n ** 3 / st[2] / 1e9
                 emit(workload="layout_bf16_16384", layout=layout, grid=f"{P}x{Q}", G=G, note=note,
                      cluster=hs.group_shape(P, Q, G)[2:], ms=ms, tflops=2 * n ** 3 / ms / 1e9,
                      stage_ms=st, counters=hs.counters(),
@@ -386,14 +387,14 @@ def run_table(sections):
 # Small cases for profiler captures: (n, configuration).  Each run makes one
 # warm-up product and then the product to capture (ncu -s 1 -c 1).
 PROFILE_CASES = {
-    # bf16 S = 5 on CTA pairs (2 x 1 groups): one persistent launch at this size
-    "pair6144": (6144, dict(P=48, Q=24, G=576, b=64, Bouter=512, kind="bf16", slices=5)),
+    # bf16 S = 4 on CTA pairs (2 x 1 groups): one persistent launch at this size
+    "pair6144": (6144, dict(P=48, Q=24, G=576, b=64, Bouter=512, kind="bf16", slices=4)),
     # the same with the benchmark's launch policy at n = 16384: one persistent
-    # launch per diagonal (five launches a product)
-    "pair6144_diag": (6144, dict(P=48, Q=24, G=576, b=64, Bouter=512, kind="bf16", slices=5,
+    # launch per diagonal (four launches a product)
+    "pair6144_diag": (6144, dict(P=48, Q=24, G=576, b=64, Bouter=512, kind="bf16", slices=4,
                                  launch=("per_diagonal", True))),
-    # bf16 S = 5 on single CTAs, flat (64-processor software groups)
-    "diag6144": (6144, dict(P=48, Q=24, G=18, b=64, Bouter=1024, kind="bf16", slices=5)),
+    # bf16 S = 4 on single CTAs, flat (64-processor software groups)
+    "diag6144": (6144, dict(P=48, Q=24, G=18, b=64, Bouter=1024, kind="bf16", slices=4)),
     # int8 S = 5, flat
     "int8_4096": (4096, dict(P=32, Q=32, G=1, b=128, Bouter=2048, kind="int8", slices=5)),
     # binary64 with 2 x 2 clusters (inner level by multicast), and flat

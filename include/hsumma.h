@@ -55,7 +55,8 @@ typedef enum {
 typedef enum {
   HSUMMA_FP64 = 0,        /* binary64 DGEMM update (Section II-A, Algorithm 1) */
   HSUMMA_INT8_SLICES = 1, /* S int8 slices, 7 bits each, exact int32 sums, S in 1..8 */
-  HSUMMA_BF16_SLICES = 2  /* S bf16 slices, 8 bits each, exact fp32 sums, S in 1..7 */
+  HSUMMA_BF16_SLICES = 2  /* S bf16 slices, 9 bits each (8 for S = 7), exact fp32 sums,
+                             S in 1..7 */
 } hsumma_mode;
 
 #define HSUMMA_MODE(kind, slices) ((int)(kind) | ((int)(slices) << 8))
@@ -167,7 +168,9 @@ int hsumma_split_exponents(int64_t M, int64_t N, int64_t K, const double *d_A,
 
 /* Step 2, slicing: digit s (s = 1..S) of every entry, t_s = rint(r 2^(w s)) -
  * 2^w rint(r 2^(w (s-1))), r = A_ik 2^-e_i (round half to even), written as
- * int8 (kind INT8, w = 7) or bf16 (kind BF16, w = 8).  Layout: d_As is
+ * int8 (kind INT8, w = 7: digits in [-64, 64]) or bf16 (kind BF16, w = 9:
+ * digits in [-256, 256], every one exact in bfloat16; w = 8 for S = 7, since
+ * w S <= 56).  Layout: d_As is
  * S x M x Kp (row-major, Kp = K rounded up to a multiple of 64, zero padded),
  * d_Bs is S x N x Kp (B transposed: row j of slice t holds column j of B). */
 int hsumma_split_slices(int64_t M, int64_t N, int64_t K, const double *d_A,
@@ -177,7 +180,8 @@ int hsumma_split_slices(int64_t M, int64_t N, int64_t K, const double *d_A,
 
 /* Number of int32 planes per diagonal that step 3 writes for this K: a
  * diagonal's exact sum is split into segments whose partial sums stay below
- * 2^31 in magnitude (bf16: 127 x 1024 products, int8: 2^18).  The count
+ * 2^31 in magnitude (bf16: 127 x 2^(26-2w) products -- 127 x 256 for w = 9,
+ * 127 x 1024 for w = 8 -- int8: 2^18).  The count
  * covers the longest diagonal, S pairs of K rounded up to a multiple of 128
  * (the product kernels' stage width); every plane of every diagonal is
  * written, zeros past a diagonal's own segments.  Returns the count (>= 1)
@@ -195,8 +199,9 @@ int hsumma_split_diagonals(int64_t M, int64_t N, int64_t K, int kind, int S,
                            int P, int Q, int G, int b, int Bouter, void *stream);
 
 /* Step 4, recombination: C_ij = RN(2^(e_i + f_j) sum_d D_d,ij 2^(-w d)), the
- * exact sum (128-bit integers) rounded once to binary64, ties to even,
- * subnormal and overflowing results included. */
+ * exact sum (64- or 128-bit integers) rounded once to binary64, ties to even,
+ * subnormal and overflowing results included.  Only the planes of a diagonal
+ * that step 3 can fill are read (the others hold zeros). */
 int hsumma_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S,
                            const int32_t *d_D, const int32_t *d_e,
                            const int32_t *d_f, double *d_C, int64_t ldc,

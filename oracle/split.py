@@ -29,11 +29,24 @@ from fractions import Fraction
 
 import numpy as np
 
-# Slice width w (bits) per slice type: INT8 slices hold digits in [-64, 64],
-# BF16 slices digits in [-128, 128] (every integer of magnitude <= 256 is exact
-# in bfloat16's 8-bit significand).
-SLICE_BITS = {"int8": 7, "bf16": 8}
+# Widest slice width w (bits) per slice type: a digit |t| <= 2^(w-1) must be
+# exact in it.  INT8 holds [-128, 127], so w = 7 (digits in [-64, 64]); every
+# integer of magnitude <= 256 is exact in bfloat16's 8-bit significand, so
+# w = 9 (digits in [-256, 256]).
+SLICE_BITS = {"int8": 7, "bf16": 9}
 SLICE_RANGE = {"int8": (3, 8), "bf16": (3, 6)}
+# The S slices of an operand hold at most this many bits (w S).  This is the
+# library's definition, which the oracle follows: its digit extraction works
+# from a 64-bit fixed-point image of each scaled value and needs the last
+# digit's rounding bit well above the image's bottom.
+MAX_SLICED_BITS = 56
+
+
+def slice_bits(kind: str, S: int) -> int:
+    """The slice width used with S slices of type `kind`: the widest exact one,
+    narrowed where S of them would pass MAX_SLICED_BITS (bf16 with S = 7 takes
+    w = 8)."""
+    return min(SLICE_BITS[kind], MAX_SLICED_BITS // S)
 
 
 def row_exponents(A: np.ndarray) -> np.ndarray:
@@ -123,7 +136,7 @@ def recombine(D: dict, e: np.ndarray, f: np.ndarray, S: int, w: int) -> np.ndarr
 def split_gemm(A: np.ndarray, B: np.ndarray, S: int, kind: str = "bf16",
                return_parts: bool = False):
     """The whole split path on the CPU: C^ ~= A x B from S slices of type `kind`."""
-    w = SLICE_BITS[kind]
+    w = slice_bits(kind, S)
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
     e = row_exponents(A)
@@ -141,7 +154,7 @@ def split_entries(A: np.ndarray, B: np.ndarray, rows, cols, S: int,
                   kind: str = "bf16") -> np.ndarray:
     """C^ at listed entries only (for full-size checks): same steps, restricted
     to the rows of A and columns of B that the entries use."""
-    w = SLICE_BITS[kind]
+    w = slice_bits(kind, S)
     rows = np.asarray(rows, dtype=np.int64)
     cols = np.asarray(cols, dtype=np.int64)
     ur, ir = np.unique(rows, return_inverse=True)

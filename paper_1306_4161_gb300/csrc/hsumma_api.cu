@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <array>
 #include <atomic>
@@ -521,8 +522,8 @@ int hsumma_gemm(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
 
   // split path: exponents, slices, exact diagonal sums, recombination
   // exactness of the recombination: a diagonal's planes sum to at most
-  // S K 2^14 in magnitude, which must fit 63 bits
-  if ((double)S * (double)K * 16384.0 >= 9.0e18) {
+  // S K 2^(2w-2) in magnitude, which must fit 63 bits
+  if ((double)S * (double)K * std::ldexp(1.0, 2 * slice_width(kind, S) - 2) >= 9.0e18) {
     set_error("K = %lld too large for exact slice sums with S = %d", (long long)K, S);
     return HSUMMA_ERR_UNSUPPORTED;
   }

@@ -96,22 +96,44 @@ int launch_split_slices(int64_t M, int64_t N, int64_t K, const double *A, int64_
                         const double *B, int64_t ldb, const int32_t *e,
                         const int32_t *f, int kind, int S, void *As, void *Bs,
                         cudaStream_t s);
+// Slice width w (bits) of S slices of a kind: the widest whose digits
+// (|t| <= 2^(w-1)) the slice type holds exactly -- int8 7 (digits in
+// [-64, 64]), bf16 9 (every integer of magnitude <= 256 is exact in bfloat16)
+// -- capped so that w S <= 56 (the digit extraction works from a 64-bit fixed
+// point image of each scaled value): bf16 with 7 slices takes 8.
+constexpr int kMaxSlicedBits = 56;
+__host__ __device__ constexpr int slice_width(int kind, int S) {
+  return kind == 1 ? 7 : (S > 0 && 9 * S > kMaxSlicedBits ? kMaxSlicedBits / S : 9);
+}
+// bf16 digit products are integers of magnitude <= 2^(2w-2); an fp32
+// accumulator stays exact (an integer <= 2^24) over 2^(26-2w) of them: 256
+// products for w = 9, 1024 for w = 8.  The bf16 kernels drain their
+// accumulators into int32 after at most that many ("chunk").
+__host__ __device__ constexpr int bf16_chunk_products(int w) { return 1 << (26 - 2 * w); }
 // Exact diagonal sums are stored as int32 planes D[d-2][seg][M][N]: a diagonal's
 // sum over its (d-1) K products is cut into segments whose partial sums stay
-// below 2^31 (bf16: 127 chunks of 1024 products of magnitude <= 2^14; int8:
-// 2^18 products of magnitude <= 2^12 per segment).  The product kernels step
-// through k in stages of at most 128 columns, a pair's last stage padded to
-// 128, so the longest diagonal (S pairs) spans S ceil(Kp / 128) 128-column
-// stages; the plane count covers that many, and every kernel writes every
-// plane of every diagonal (zeros past the diagonal's own segments).
+// below 2^31 (bf16: 127 chunks, each summing to at most 2^24 in magnitude;
+// int8: 2^18 products of magnitude <= 2^12 per segment).  The product kernels
+// step through k in stages of at most 128 columns, a pair's last stage padded
+// to 128, so diagonal d (d - 1 pairs) spans (d - 1) ceil(Kp / 128) 128-column
+// stages; the plane count covers the longest (S pairs), and every kernel
+// writes every plane of every diagonal (zeros past the diagonal's own
+// segments).
 constexpr int kSegChunks = 127;
-inline int split_planes(int64_t K, int S, int kind = 2) {
+inline int64_t split_segment_products(int S, int kind) {
+  return kind == 1 ? (int64_t)1 << 18
+                   : (int64_t)kSegChunks * bf16_chunk_products(slice_width(kind, S));
+}
+// the segments of a diagonal whose sum spans `pairs` slice pairs
+inline int split_diagonal_planes(int64_t K, int S, int kind, int pairs) {
   const int64_t Kp = (K + 63) / 64 * 64;
   const int64_t K128 = (Kp + 127) / 128 * 128;
-  const int64_t prods = (int64_t)S * K128;   // longest diagonal: S pairs
-  const int64_t per_seg = kind == 1 ? (int64_t)1 << 18 : (int64_t)kSegChunks * 1024;
-  const int64_t n = (prods + per_seg - 1) / per_seg;
+  const int64_t per_seg = split_segment_products(S, kind);
+  const int64_t n = ((int64_t)pairs * K128 + per_seg - 1) / per_seg;
   return n < 1 ? 1 : (int)n;
+}
+inline int split_planes(int64_t K, int S, int kind = 2) {
+  return split_diagonal_planes(K, S, kind, S);   // the longest diagonal: S pairs
 }
 int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, int32_t *D,
                       cudaStream_t s);

@@ -2,21 +2,23 @@
 //
 // For every C block the kernel forms the exact diagonal sums
 //     D_d = sum_{s+t=d} A_s B_t,   d = 2 .. S+1,
-// of the bf16 digit slices (integers of magnitude <= 128), with the same
+// of the bf16 digit slices (integers of magnitude <= 2^(w-1): 256 for w = 9),
+// with the same
 // HSUMMA data movement as the binary64 kernel: one CTA per virtual processor
 // (Section III), b-wide panels of each slice multicast inside the group
 // cluster (inner level, Figure 4), outer panels staged into L2 by their owners
 // (outer level, Figure 3).  The local update runs as tcgen05.mma
 // (128 x 256 x 16, bf16 x bf16 -> fp32 in tensor memory).
 //
-// Exactness: a product of two digits is an integer of magnitude <= 2^14, so an
-// fp32 accumulator that sums at most 1024 of them per element stays an integer
-// of magnitude <= 2^24 and is exact.  Accumulators are therefore drained into
-// int32 registers after at most 16 k-stages of 64 ("chunk", 1024 products);
-// pairs of the same diagonal are concatenated along k.  A diagonal is cut into
-// segments of 127 * 16 stages (sums <= 127 * 2^24 < 2^31); each segment's exact
-// int32 sums are stored as one plane of the output, D[d-2][seg][i][j], and the
-// recombination adds the planes of a diagonal exactly.
+// Exactness: a product of two digits is an integer of magnitude <= 2^(2w-2),
+// so an fp32 accumulator that sums at most 2^(26-2w) of them per element (256
+// for w = 9, 1024 for w = 8) stays an integer of magnitude <= 2^24 and is
+// exact.  Accumulators are therefore drained into int32 registers after at
+// most that many products ("chunk": 4 or 16 k-stages of 64); pairs of the
+// same diagonal are concatenated along k.  A diagonal is cut into segments of
+// 127 chunks (sums <= 127 * 2^24 < 2^31); each segment's exact int32 sums are
+// stored as one plane of the output, D[d-2][seg][i][j], and the recombination
+// adds the planes of a diagonal exactly.
 //
 // One MMA issuer.  A single issuing thread sustains the full tensor rate (one
 // 128 x 256 x 16 MMA per 128 cycles), so the two accumulators (tensor-memory
@@ -49,10 +51,8 @@ constexpr int TM = 128, TN = 256, BKS = 64, STAGES = 4;
 constexpr int A_BYTES = TM * BKS * 2, B_BYTES = TN * BKS * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int B_REGION = STAGES * A_BYTES;   // ring: all A slots, then all B slots
-constexpr int CH = 16;                 // k-stages per accumulator chunk
 constexpr int NEPI = 8;                // draining warps
 constexpr int NTHREADS = (4 + NEPI) * 32;   // copy warp, MMA warp, two idle warps, drain warps
-constexpr int SEGST = 127 * CH;        // stages per int32 segment
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC = idesc_bf16_f32(TM, TN);
@@ -60,7 +60,8 @@ constexpr uint32_t IDESC = idesc_bf16_f32(TM, TN);
 struct SplitParams {
   int32_t *D;
   int64_t M, N, K, Kpad, Mt, Nt, Kq, Kp;
-  int P, Q, cm, cn, nsub_m, nsub_n, Bo, S, nkb, seg_chunks, nseg;
+  int P, Q, cm, cn, nsub_m, nsub_n, Bo, S, nkb, nseg;
+  int ch, segst;   // k-stages per accumulator chunk (a power of two), per int32 segment
   unsigned long long *counters;
   int *status;
 };
@@ -86,10 +87,10 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
 }
 
 // Does stage `local` (counted from the start of its segment of `seg_len`
-// stages) end a chunk?  A chunk closes after every CH stages of a segment and
-// at its last stage.
-__device__ __forceinline__ bool chunk_end(int local, int seg_len) {
-  return (local + 1) % CH == 0 || local + 1 == seg_len;
+// stages) end a chunk?  A chunk closes after every `ch` stages of a segment
+// and at its last stage.
+__device__ __forceinline__ bool chunk_end(int local, int seg_len, int ch) {
+  return ((local + 1) & (ch - 1)) == 0 || local + 1 == seg_len;
 }
 
 // cluster tile L -> processor row r and column c of this CTA: tiles are
@@ -315,8 +316,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int d = 2; d <= S + 1 && ok; ++d) {
               const int nst = (d - 1) * nkb;
               for (int st = 0; st < nst; ++st, ++gst) {
-                const int seg_lo = st - st % SEGST;
-                const int seg_len = min(nst, seg_lo + SEGST) - seg_lo;
+                const int seg_lo = st - st % p.segst;
+                const int seg_len = min(nst, seg_lo + p.segst) - seg_lo;
                 const int local = st - seg_lo;
                 bool first = false;
                 if (!in_chunk) {
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   mma_commit_mc(smem_u32(&empty[stage]), rel_mask);
                 else
                   mma_commit(smem_u32(&empty[stage]));
-                if (chunk_end(local, seg_len)) {
+                if (chunk_end(local, seg_len, p.ch)) {
                   mma_commit(smem_u32(&acc_full[nchunk & 1u]));
                   ++nchunk;
                   in_chunk = false;
@@ -386,16 +387,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
           for (int d = 2; d <= S + 1 && ok; ++d) {
             const int nst = (d - 1) * nkb;
-            const int nseg_d = (nst + SEGST - 1) / SEGST;
+            const int nseg_d = (nst + p.segst - 1) / p.segst;
             for (int seg = 0; seg < p.nseg && ok; ++seg) {
-              const int seg_len = seg < nseg_d ? min(nst, (seg + 1) * SEGST) - seg * SEGST : 0;
-              int acc[128];
+              const int seg_len =
+                  seg < nseg_d ? min(nst, (seg + 1) * p.segst) - seg * p.segst : 0;
+              uint32_t acc[128];
 #pragma unroll
               for (int i = 0; i < 128; ++i) acc[i] = 0;
               // a plane past this diagonal's segments is written as zeros: the
               // recombination adds every plane of every diagonal
               for (int local = 0; local < seg_len; ++local) {
-                if (!chunk_end(local, seg_len)) continue;
+                if (!chunk_end(local, seg_len, p.ch)) continue;
                 const uint32_t who = nchunk & 1u, par = (nchunk >> 1) & 1u;
                 // the whole warp decides together: tcgen05.ld below is warp-collective
                 const bool got = wait_or_abort(smem_u32(&acc_full[who]), par, &abort_flag, false);
@@ -407,16 +409,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t ta =
                     tmem_base + ((uint32_t)(q * 32) << 16) + who * (uint32_t)TN + h * 128;
                 // two 16-column loads in flight per wait: four round trips
+                float mx = 0.f;
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                   uint32_t v[16], w[16];
                   tmem_ld16(ta + j * 16, v);
                   tmem_ld16(ta + j * 16 + 16, w);
                   tmem_ld_wait();
+                  drain_add16(acc + j * 16, v, mx);
+                  drain_add16(acc + j * 16 + 16, w, mx);
+                }
+                if (__any_sync(0xffffffffu, !(mx < kFastDrainBound))) {
 #pragma unroll
-                  for (int i = 0; i < 16; ++i) {
-                    acc[j * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
-                    acc[j * 16 + 16 + i] += __float2int_rn(__uint_as_float(w[i]));
+                  for (int j = 0; j < 8; j += 2) {
+                    uint32_t v[16], w[16];
+                    tmem_ld16(ta + j * 16, v);
+                    tmem_ld16(ta + j * 16 + 16, w);
+                    tmem_ld_wait();
+                    drain_fix16(acc + j * 16, v);
+                    drain_fix16(acc + j * 16 + 16, w);
                   }
                 }
                 tc_fence_before();
@@ -432,11 +443,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                   for (int i = 0; i < 128; i += 4)
                     *reinterpret_cast<int4 *>(drow + i) =
-                        make_int4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+                        make_int4((int)acc[i], (int)acc[i + 1], (int)acc[i + 2],
+                                  (int)acc[i + 3]);
                 } else {
 #pragma unroll
                   for (int i = 0; i < 128; ++i)
-                    if (i < nvalid) drow[i] = acc[i];
+                    if (i < nvalid) drow[i] = (int32_t)acc[i];
                 }
               }
             }
@@ -516,8 +528,9 @@ int launch_split_bf16(const GridPlan &g, int S, const void *As, const void *Bs, 
   p.Bo = g.Bo;
   p.S = S;
   p.nkb = (int)(Kpad / BKS);
-  p.seg_chunks = kSegChunks;
-  p.nseg = split_planes(g.K, S);
+  p.nseg = split_planes(g.K, S, HSUMMA_BF16_SLICES);
+  p.ch = bf16_chunk_products(slice_width(HSUMMA_BF16_SLICES, S)) / BKS;
+  p.segst = kSegChunks * p.ch;
   p.counters = state().d_counters;
   p.status = state().d_status;
   const bool flat = g.cm * g.cn == 1;

@@ -26,8 +26,9 @@
 // tensor copies).  One issuing thread of the leader runs every MMA: a single
 // thread sustains the full tensor rate (one 256 x 256 x 16 pair MMA per 128
 // cycles), so the two accumulators (tensor-memory columns 0..255 and 256..511
-// of both SMs) are used in turn, a chunk of at most 8 stages (1024 products,
-// the bound of exact fp32 sums) in each: while the drain warps of both CTAs
+// of both SMs) are used in turn, a chunk of at most 2 stages (256 products of
+// digits of 9 bits) or 8 (1024 of 8 bits), the bound of exact fp32 sums, in
+// each: while the drain warps of both CTAs
 // empty one accumulator, the MMAs fill the other.  Each stage's MMA
 // completion releases the stage in both CTAs, each chunk end hands the
 // accumulator to the drain warps, and they return it to the leader.  Every
@@ -71,10 +72,8 @@ constexpr int STAGES = 3;
 constexpr int A_PANEL = TM * PK * 2, B_PANEL = HN * PK * 2;   // 16 KB each
 constexpr int A_BYTES = KZ * A_PANEL, BH_BYTES = KZ * B_PANEL;
 constexpr int STAGE_BYTES = A_BYTES + BH_BYTES;
-constexpr int CH = 8;                  // stages per accumulator chunk (1024 products)
 constexpr int NEPI = 8;                // draining warps per CTA
 constexpr int NTHREADS = (4 + NEPI) * 32;   // copy warp, MMA warp, two idle warps, drain warps
-constexpr int SEGST = 127 * CH;        // stages per int32 segment
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC2 = idesc_bf16_f32(2 * TM, TN);
@@ -86,6 +85,7 @@ struct PairParams {
   int32_t *D;
   int64_t M, N, K, Kpad, Mt, Nt, Kq, Kp;
   int P, Q, nsub_m, nsub_n, Bo, S, nkb, nseg;
+  int ch, segst;                 // stages per accumulator chunk (a power of two), per segment
   int d_lo, d_hi;                // the diagonals (slice pairs s + t = d) of this launch
   unsigned long long *counters;
   int *status;
@@ -133,10 +133,10 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
   }
 }
 
-// a chunk closes after every CH stages of a segment and at its last stage;
+// a chunk closes after every `ch` stages of a segment and at its last stage;
 // chunk n of the launch uses accumulator n mod 2
-__device__ __forceinline__ bool chunk_end(int local, int seg_len) {
-  return (local + 1) % CH == 0 || local + 1 == seg_len;
+__device__ __forceinline__ bool chunk_end(int local, int seg_len, int ch) {
+  return ((local + 1) & (ch - 1)) == 0 || local + 1 == seg_len;
 }
 
 // group tile L -> processor row r and column c of the CTA that is member `ry`
@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               for (int st = 0; st < nst; ++st, ++gst) {
                 const int npan = kb == nkb - 1 ? last_panels : KZ;
                 if (++kb == nkb) kb = 0;
-                const int seg_lo = st - st % SEGST;
-                const int seg_len = min(nst, seg_lo + SEGST) - seg_lo;
+                const int seg_lo = st - st % p.segst;
+                const int seg_len = min(nst, seg_lo + p.segst) - seg_lo;
                 const int local = st - seg_lo;
                 bool first = false;
                 if (!in_chunk) {
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   }
                 }
                 mma2_commit_mc(smem_u32(&empty[stage]), all_mask);
-                if (chunk_end(local, seg_len)) {
+                if (chunk_end(local, seg_len, p.ch)) {
                   mma2_commit_mc(smem_u32(&acc_full[nchunk & 1u]), pair_mask);
                   ++nchunk;
                   in_chunk = false;
@@ -432,16 +432,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t nvalid = imin64(128, imax64(0, col_hi - n0));
           for (int d = dlo; d <= dhi && ok; ++d) {
             const int nst = (d - 1) * nkb;
-            const int nseg_d = (nst + SEGST - 1) / SEGST;
+            const int nseg_d = (nst + p.segst - 1) / p.segst;
             for (int seg = 0; seg < p.nseg && ok; ++seg) {
-              const int seg_len = seg < nseg_d ? min(nst, (seg + 1) * SEGST) - seg * SEGST : 0;
-              int acc[128];
+              const int seg_len =
+                  seg < nseg_d ? min(nst, (seg + 1) * p.segst) - seg * p.segst : 0;
+              uint32_t acc[128];
 #pragma unroll
               for (int i = 0; i < 128; ++i) acc[i] = 0;
               // a plane past this diagonal's segments is written as zeros: the
               // recombination adds every plane of every diagonal
               for (int local = 0; local < seg_len; ++local) {
-                if (!chunk_end(local, seg_len)) continue;
+                if (!chunk_end(local, seg_len, p.ch)) continue;
                 const uint32_t who = nchunk & 1u, par = (nchunk >> 1) & 1u;
                 // warp-uniform decision before the warp-collective tcgen05.ld
                 const bool got = wait_or_abort(smem_u32(&acc_full[who]), par, &abort_flag);
@@ -453,16 +454,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t ta =
                     tmem_base + ((uint32_t)(q * 32) << 16) + who * (uint32_t)TN + h * 128;
                 // two 16-column loads in flight per wait: four round trips
+                float mx = 0.f;
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                   uint32_t v[16], w[16];
                   tmem_ld16(ta + j * 16, v);
                   tmem_ld16(ta + j * 16 + 16, w);
                   tmem_ld_wait();
+                  drain_add16(acc + j * 16, v, mx);
+                  drain_add16(acc + j * 16 + 16, w, mx);
+                }
+                if (__any_sync(0xffffffffu, !(mx < kFastDrainBound))) {
 #pragma unroll
-                  for (int i = 0; i < 16; ++i) {
-                    acc[j * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
-                    acc[j * 16 + 16 + i] += __float2int_rn(__uint_as_float(w[i]));
+                  for (int j = 0; j < 8; j += 2) {
+                    uint32_t v[16], w[16];
+                    tmem_ld16(ta + j * 16, v);
+                    tmem_ld16(ta + j * 16 + 16, w);
+                    tmem_ld_wait();
+                    drain_fix16(acc + j * 16, v);
+                    drain_fix16(acc + j * 16 + 16, w);
                   }
                 }
                 tc_fence_before();
@@ -485,11 +495,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                   for (int i = 0; i < 128; i += 4)
                     *reinterpret_cast<int4 *>(drow + i) =
-                        make_int4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+                        make_int4((int)acc[i], (int)acc[i + 1], (int)acc[i + 2],
+                                  (int)acc[i + 3]);
                 } else {
 #pragma unroll
                   for (int i = 0; i < 128; ++i)
-                    if (i < nvalid) drow[i] = acc[i];
+                    if (i < nvalid) drow[i] = (int32_t)acc[i];
                 }
               }
             }
@@ -622,6 +633,8 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   p.S = S;
   p.nkb = (int)ceil_div(Kpad, BKS);
   p.nseg = split_planes(g.K, S, HSUMMA_BF16_SLICES);
+  p.ch = bf16_chunk_products(slice_width(HSUMMA_BF16_SLICES, S)) / BKS;
+  p.segst = kSegChunks * p.ch;
   p.counters = state().d_counters;
   p.status = state().d_status;
   auto kern = CN == 2 ? (g.cyc ? bf16_pair_kernel<2, true> : bf16_pair_kernel<2, false>)
@@ -642,14 +655,15 @@ int launch_split_bf16_pair(const GridPlan &g, int S, const void *As, const void 
   // which short or few-round products cannot afford.  Measured (ms, one launch
   // against one per diagonal): 1024 tiles x 15 x 16384 k: one launch faster by
   // 1 %; 2048 and 2304 tiles: per diagonal by 0.5-1.5 %; 3072 tiles x 15 x 8192
-  // k: one launch by 1.3 %; 4096 tiles x 15 x 16384 k: per diagonal by 2-4 %.
-  // Rule: per diagonal from 24 rounds and 15 x 16384 k-columns of pairs a tile.
+  // k: one launch by 1.3 %; 4096 tiles x 15 x 16384 k: per diagonal by 2-4 %;
+  // 4096 tiles x 10 x 16384 k (S = 4): per diagonal by 2-5 %.
+  // Rule: per diagonal from 24 rounds and 10 x 16384 k-columns of pairs a tile.
   const int resident = state().sm_count / (2 * CN);
   const int split = policy & 0xf;
   const bool per_diagonal =
       split == HSUMMA_PAIR_LAUNCH_PER_DIAGONAL ||
       (split == HSUMMA_PAIR_LAUNCH_AUTO && resident > 0 && ntiles >= 24 * resident &&
-       (int64_t)(S * (S + 1) / 2) * Kpad >= 15 * 16384);
+       (int64_t)(S * (S + 1) / 2) * Kpad >= 10 * 16384);
   p.whole = ntiles;
   int nclusters = ntiles;
   if (policy & HSUMMA_PAIR_PERSISTENT) {

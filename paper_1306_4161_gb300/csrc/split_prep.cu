@@ -1,7 +1,8 @@
 // Split-precision path, the steps around the tensor-core products:
 //   1. exponent scan   e_i = ilogb(max_k |A_ik|) + 2, f_j over the columns of B
 //   2. slicing         S digits per entry, t_s = RN(r 2^(w s)) - 2^w RN(r 2^(w(s-1))),
-//                      r = a 2^-e (round half to even), as int8 (w = 7) or bf16 (w = 8)
+//                      r = a 2^-e (round half to even), as int8 (w = 7) or bf16 (w = 9;
+//                      8 for S = 7)
 //   4. recombination   C_ij = RN(2^(e_i+f_j) sum_d D_d,ij 2^(-w d)), exact sum in
 //                      128-bit integers, rounded once to binary64
 // All three work on the bit patterns with integer instructions: binary64
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(256) slices_rows_kernel(const double *__restri
                                                           int64_t Kp,
                                                           const int32_t *__restrict__ e,
                                                           void *__restrict__ out) {
-  constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
+  constexpr int W = slice_width(KIND, S);
   constexpr int EB = KIND == HSUMMA_INT8_SLICES ? 1 : 2;
   const int64_t groups = Kp / 8;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(256) slices_cols_kernel(const double *__restri
                                                           int64_t Kp,
                                                           const int32_t *__restrict__ f,
                                                           void *__restrict__ out) {
-  constexpr int W = KIND == HSUMMA_INT8_SLICES ? 7 : 8;
+  constexpr int W = slice_width(KIND, S);
   constexpr int EB = KIND == HSUMMA_INT8_SLICES ? 1 : 2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t njb = (uint32_t)((N + 31) / 32);
@@ -409,18 +410,23 @@ __device__ __forceinline__ double round_scaled(__int128 X, int k) {
 // every plane when the rows are 16-byte aligned (N a multiple of 4), 16-byte
 // stores of C when its row allows, element by element otherwise.  The first
 // segment plane of every diagonal is loaded before any arithmetic, so that
-// all S loads of a thread are in flight at once; further segment planes (K
-// beyond one segment) follow one diagonal at a time.
-// With one segment plane per diagonal, X fits in 64 bits whenever |D_2| <= T2:
-// the host derives T2 from the int32 range of the other diagonals, so that
-// |D_2| 2^(w (S-1)) + sum_(d>2) 2^31 2^(w (S+1-d)) < 2^63 (every partial sum of
-// Horner's rule is bounded by the same sum).  The diagonal sums the products
-// give are far inside that bound; other values take the 128-bit path.
-// (four resident blocks per SM keep more loads in flight; the kernels of 7 and
+// all S loads of a thread are in flight at once; a diagonal's further segment
+// planes (np.n[d] of them in all; the planes past those hold zeros and are
+// not read) are added in 64 bits.
+// X fits in 64 bits whenever |D_2| <= T2: the host derives T2 from the range
+// of the other diagonals (np.n[d] int32 planes each), so that
+// |D_2| 2^(w (S-1)) + sum_(d>2) n_d 2^31 2^(w (S+1-d)) < 2^63 (every partial
+// sum of Horner's rule is bounded by the same sum).  The diagonal sums the
+// products give are far inside that bound; other values take the 128-bit path.
+// (four resident blocks per SM keep more loads in flight; the kernels of 6 to
 // 8 slices need more than the 64 registers that leaves)
+struct DiagPlanes {
+  int n[8];   // segment planes of diagonal d + 2 that the products can fill
+};
+
 template <int W, int S>
-__global__ void __launch_bounds__(256, S <= 6 ? 4 : 3) recombine_kernel(const int32_t *__restrict__ D, int nseg,
-                                                        int64_t M, int64_t N,
+__global__ void __launch_bounds__(256, S <= 5 ? 4 : 3) recombine_kernel(const int32_t *__restrict__ D, int nseg,
+                                                        DiagPlanes np, int64_t M, int64_t N,
                                                         const int32_t *__restrict__ e,
                                                         const int32_t *__restrict__ f,
                                                         double *__restrict__ C, int64_t ldc,
@@ -443,31 +449,46 @@ __global__ void __launch_bounds__(256, S <= 6 ? 4 : 3) recombine_kernel(const in
   int first[S][4];
 #pragma unroll
   for (int d = 0; d < S; ++d) load4(D + (int64_t)(d * nseg) * plane + off, first[d]);
+  // diagonal d's exact sum: its first plane and the rest of its own planes
+  auto diag = [&](int d, long long (&Dd)[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Dd[u] = first[d][u];
+    for (int g = 1; g < np.n[d]; ++g) {
+      int v[4];
+      load4(D + (int64_t)(d * nseg + g) * plane + off, v);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) Dd[u] += v[u];
+    }
+  };
   const int k = e[i] - W * (S + 1);
   double out[4];
-  bool narrow = nseg == 1;
+  long long D2[4];
+  diag(0, D2);
+  bool narrow = true;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) narrow = narrow && llabs((long long)first[0][u]) <= T2;
+  for (int u = 0; u < 4; ++u) narrow = narrow && llabs(D2[u]) <= T2;
   if (narrow) {
+    unsigned long long X[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      unsigned long long X = (unsigned long long)(long long)first[0][u];
+    for (int u = 0; u < 4; ++u) X[u] = (unsigned long long)D2[u];
 #pragma unroll
-      for (int d = 1; d < S; ++d) X = (X << W) + (unsigned long long)(long long)first[d][u];
-      out[u] = j0 + u < N ? round_scaled64((long long)X, k + f[j0 + u]) : 0.0;
+    for (int d = 1; d < S; ++d) {
+      long long Dd[4];
+      diag(d, Dd);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) X[u] = (X[u] << W) + (unsigned long long)Dd[u];
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      out[u] = j0 + u < N ? round_scaled64((long long)X[u], k + f[j0 + u]) : 0.0;
   } else {
-    __int128 X[4] = {0, 0, 0, 0};
+    __int128 X[4];
 #pragma unroll
-    for (int d = 0; d < S; ++d) {
-      long long Dd[4] = {first[d][0], first[d][1], first[d][2], first[d][3]};
-      // the segment planes of a diagonal sum exactly in 64 bits
-      for (int g = 1; g < nseg; ++g) {
-        int v[4];
-        load4(D + (int64_t)(d * nseg + g) * plane + off, v);
+    for (int u = 0; u < 4; ++u) X[u] = D2[u];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) Dd[u] += v[u];
-      }
+    for (int d = 1; d < S; ++d) {
+      long long Dd[4];
+      diag(d, Dd);
 #pragma unroll
       for (int u = 0; u < 4; ++u) X[u] = (X[u] << W) + (__int128)Dd[u];
     }
@@ -486,40 +507,47 @@ __global__ void __launch_bounds__(256, S <= 6 ? 4 : 3) recombine_kernel(const in
 }
 
 // T2 of the kernel above: the largest |D_2| for which X stays below 2^63 when
-// every other diagonal holds any int32; 2^31 admits every int32 (S = 1), and
-// -1 admits none (the other diagonals alone can pass 2^63: bf16 with S >= 6).
-int64_t recombine_narrow_bound(int W, int S) {
-  if (S <= 1) return 2147483648LL;
+// every other diagonal d holds any sum of np.n[d-2] int32 planes; 2^31 admits
+// every int32 plane, and -1 admits none (the other diagonals alone can pass
+// 2^63: bf16 with S = 6).
+int64_t recombine_narrow_bound(int W, int S, const DiagPlanes &np) {
   long double rest = 0.0L;
-  for (int d = 3; d <= S + 1; ++d) rest += ldexpl(2147483648.0L, W * (S + 1 - d));
+  for (int d = 3; d <= S + 1; ++d)
+    rest += np.n[d - 2] * ldexpl(2147483648.0L, W * (S + 1 - d));
   const long double room = ldexpl(1.0L, 63) - 1.0L - rest;
   if (room < 0.0L) return -1;
   const long double t = floorl(room / ldexpl(1.0L, W * (S - 1)));
-  return t >= 2147483648.0L ? 2147483648LL : (int64_t)t;
+  return t >= 9.0e18L ? (int64_t)9000000000000000000LL : (int64_t)t;
 }
 
 template <int W, int S>
-void recombine_launch(dim3 grid, cudaStream_t s, const int32_t *D, int nseg, int64_t M,
-                      int64_t N, const int32_t *e, const int32_t *f, double *C, int64_t ldc) {
-  static const int64_t T2 = recombine_narrow_bound(W, S);
-  recombine_kernel<W, S><<<grid, 256, 0, s>>>(D, nseg, M, N, e, f, C, ldc, T2);
+void recombine_launch(dim3 grid, cudaStream_t s, const int32_t *D, int nseg, const DiagPlanes &np,
+                      int64_t M, int64_t N, const int32_t *e, const int32_t *f, double *C,
+                      int64_t ldc) {
+  const int64_t T2 = recombine_narrow_bound(W, S, np);
+  recombine_kernel<W, S><<<grid, 256, 0, s>>>(D, nseg, np, M, N, e, f, C, ldc, T2);
   count_launch();
 }
 
-template <int W>
+// the slice count as a template argument; the width follows from kind and S
+template <int KIND>
 void recombine_dispatch(int S, dim3 grid, cudaStream_t s, const int32_t *D, int nseg,
-                        int64_t M, int64_t N, const int32_t *e, const int32_t *f, double *C,
-                        int64_t ldc) {
+                        const DiagPlanes &np, int64_t M, int64_t N, const int32_t *e,
+                        const int32_t *f, double *C, int64_t ldc) {
+#define HS_RECOMBINE(SS)                                                                    \
+  recombine_launch<slice_width(KIND, SS), SS>(grid, s, D, nseg, np, M, N, e, f, C, ldc); \
+  break
   switch (S) {
-    case 1: recombine_launch<W, 1>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
-    case 2: recombine_launch<W, 2>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
-    case 3: recombine_launch<W, 3>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
-    case 4: recombine_launch<W, 4>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
-    case 5: recombine_launch<W, 5>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
-    case 6: recombine_launch<W, 6>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
-    case 7: recombine_launch<W, 7>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
-    default: recombine_launch<W, 8>(grid, s, D, nseg, M, N, e, f, C, ldc); break;
+    case 1: HS_RECOMBINE(1);
+    case 2: HS_RECOMBINE(2);
+    case 3: HS_RECOMBINE(3);
+    case 4: HS_RECOMBINE(4);
+    case 5: HS_RECOMBINE(5);
+    case 6: HS_RECOMBINE(6);
+    case 7: HS_RECOMBINE(7);
+    default: HS_RECOMBINE(8);
   }
+#undef HS_RECOMBINE
 }
 
 // One slicing launch with the slice count as a template argument: rows of A
@@ -626,15 +654,20 @@ int launch_split_recombine(int64_t M, int64_t N, int64_t K, int kind, int S, con
                            const int32_t *e, const int32_t *f, double *C, int64_t ldc,
                            cudaStream_t s) {
   const int nseg = split_planes(K, S, kind);
+  DiagPlanes np = {};
+  for (int d = 2; d <= S + 1 && d - 2 < 8; ++d)
+    np.n[d - 2] = split_diagonal_planes(K, S, kind, d - 1);
   // one grid row per matrix row, in bands of at most 65535 rows; a band starts
   // r0 rows in: D, e and C advance by r0 rows, the plane stride stays M N
   for (int64_t r0 = 0; r0 < M; r0 += 65535) {
     const int64_t rows = (M - r0) < 65535 ? (M - r0) : 65535;
     dim3 grid((unsigned)ceil_div(ceil_div(N, 4), 256), (unsigned)rows);
     if (kind == HSUMMA_INT8_SLICES)
-      recombine_dispatch<7>(S, grid, s, D + r0 * N, nseg, M, N, e + r0, f, C + r0 * ldc, ldc);
+      recombine_dispatch<HSUMMA_INT8_SLICES>(S, grid, s, D + r0 * N, nseg, np, M, N, e + r0, f,
+                                             C + r0 * ldc, ldc);
     else
-      recombine_dispatch<8>(S, grid, s, D + r0 * N, nseg, M, N, e + r0, f, C + r0 * ldc, ldc);
+      recombine_dispatch<HSUMMA_BF16_SLICES>(S, grid, s, D + r0 * N, nseg, np, M, N, e + r0, f,
+                                             C + r0 * ldc, ldc);
   }
   cudaError_t err = cudaGetLastError();
   return err == cudaSuccess ? HSUMMA_OK : cuda_fail(err, "launch recombination");

@@ -116,6 +116,35 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Drain of an accumulator chunk into this thread's exact 32-bit sums.  A
+// value x of the chunk (an integer in fp32) with |x| < 2^22 converts by one
+// floating-point add: x + 1.5 * 2^23 lies in (2^23, 2^24), where consecutive
+// integers have consecutive encodings, so its bits are those of 1.5 * 2^23
+// plus x.  drain_add16 adds 16 values that way and keeps the largest |x| in
+// mx; when any lane of the warp saw one of 2^22 or more, the chunk is read
+// again from tensor memory and drain_fix16 replaces every value's add by the
+// float-to-int conversion instruction (which issues at a fraction of the add
+// rate): the sums are exact either way, modulo 2^32 in between.
+constexpr float kFastDrainBound = 4194304.f;   // 2^22
+__device__ __forceinline__ uint32_t drain_fast_bits(float x) {
+  return __float_as_uint(x + 12582912.f) - 0x4B400000u;   // 1.5 * 2^23 and its encoding
+}
+__device__ __forceinline__ void drain_add16(uint32_t *acc, const uint32_t (&v)[16], float &mx) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float x = __uint_as_float(v[i]);
+    mx = fmaxf(mx, fabsf(x));
+    acc[i] += drain_fast_bits(x);
+  }
+}
+__device__ __forceinline__ void drain_fix16(uint32_t *acc, const uint32_t (&v)[16]) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float x = __uint_as_float(v[i]);
+    acc[i] += (uint32_t)__float2int_rn(x) - drain_fast_bits(x);
+  }
+}
+
 // ---- CTA-pair (cta_group::2) forms: one MMA spans two SMs of a cluster (CTA
 // ranks 2k and 2k+1); A is split along M (each CTA supplies 128 rows), B along
 // N (each CTA supplies half of the columns), D rows land in each CTA's own

@@ -51,17 +51,22 @@ def test_workspace_sizes(lib):
     al = lambda x: (x + 255) // 256 * 256
     assert ws == al(300 * 4) + al(520 * 4) + al(5 * 300 * Kp * 2) + al(5 * 520 * Kp * 2) + \
         al(5 * planes * 300 * 520 * 4)
-    # a diagonal of 5 pairs over K = 32768 needs two planes (127 chunks of 1024 each)
-    assert hs.split_planes(32768, "bf16", 5) == 2
+    # bf16 digits of 9 bits (S <= 6): a chunk is 256 products, a segment 127
+    # chunks (32512 products), so a diagonal of 5 pairs over K = 32768 needs six
+    # planes; with 7 slices the digits have 8 bits, a segment is 127 x 1024
+    assert hs.split_planes(32768, "bf16", 5) == 6
+    assert hs.split_planes(16384, "bf16", 4) == 3
     assert hs.split_planes(16384, "bf16", 7) == 1
     assert hs.split_planes(16384, "int8", 8) == 1
 
 
 def test_planes_cover_every_kernel_segment(lib):
     # The product kernels cut a diagonal's exact sum into int32 segments of a
-    # fixed number of k-stages: 1016 stages of 128 columns (bf16 on CTA pairs),
-    # 2032 stages of 64 (bf16 on one CTA) or 2048 of 128 (int8), a pair's last
-    # stage padded to the stage width.  Every segment of the longest diagonal
+    # fixed number of k-stages: 127 chunks of exact fp32 sums for bf16 (a chunk
+    # is 2^(26 - 2w) products: 256 for w = 9, 1024 for w = 8), that is 254 or
+    # 1016 stages of 128 columns (CTA pairs), 508 or 2032 of 64 (one CTA); 2048
+    # stages of 128 for int8; a pair's last stage padded to the stage width.
+    # Every segment of the longest diagonal
     # (S pairs) must have a plane: a kernel writing more would write past the
     # sums' storage.  Odd panel counts (Kp / 64 odd) make the 128-column stages
     # longer than Kp; K = 43328, S = 3 and K = 87360, S = 3 are cases where
@@ -72,15 +77,16 @@ def test_planes_cover_every_kernel_segment(lib):
     for K in Ks:
         Kp = cd(K, 64) * 64
         for S in range(1, 8):
-            for kind, stage, seg in (("bf16", 128, 1016), ("bf16", 64, 2032), ("int8", 128, 2048)):
-                if kind == "int8" and S > 8:
-                    continue
+            chunk = 2 ** (26 - 2 * (9 if S <= 6 else 8))
+            for kind, stage, seg in (("bf16", 128, 127 * chunk // 128),
+                                     ("bf16", 64, 127 * chunk // 64), ("int8", 128, 2048)):
                 planes = hs.split_planes(K, kind, S)
                 segs = cd(S * cd(Kp, stage), seg)
                 assert segs <= planes, (K, S, kind, stage, segs, planes)
                 # and no plane is wasted beyond one for the padding
                 assert planes <= cd(S * Kp, seg * stage) + 1
-    assert hs.split_planes(43328, "bf16", 3) == 2
+    # 3 x 43328 = 129984 <= 4 x 32512 < 3 x 43392 (the 128-column stages)
+    assert hs.split_planes(43328, "bf16", 3) == 5
     assert hs.split_planes(87360, "int8", 3) == 2
 
 

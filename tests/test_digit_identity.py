@@ -7,7 +7,7 @@ which must equal the oracle's digits t_s = RN(r 2^(ws)) - 2^w RN(r 2^(w(s-1)))
 (r = x 2^-e, round half to even).  This restates the kernels' integer steps
 bit for bit (32-bit window, trailing-zero test) and compares them with
 oracle.split on random values over the whole exponent range, subnormals,
-zeros, and exact ties at every slice boundary, for both slice widths."""
+zeros, and exact ties at every slice boundary, for every slice width."""
 import random
 import struct
 
@@ -56,7 +56,7 @@ def awkward_rows(seed):
     for _ in range(300):
         ex = rnd.randint(-1070, 1000)
         rows.append([rnd.uniform(-1, 1) * 2.0 ** (ex + rnd.randint(-70, 0)) for _ in range(16)])
-    for w in (7, 8):
+    for w in (7, 8, 9):
         for s in range(1, 9):
             q = 2.0 ** (-2 - w * s)            # a tie at slice s of a row whose maximum is 0.49
             rows.append([0.49, 0.25 + q, -(0.25 + q), 0.25 + 3 * q, 0.125 + q / 2, 0.0, -0.0,
@@ -68,9 +68,9 @@ def awkward_rows(seed):
     return np.array(rows)
 
 
-@pytest.mark.parametrize("kind,S", [("bf16", 7), ("int8", 8)])
+@pytest.mark.parametrize("kind,S", [("bf16", 6), ("bf16", 7), ("int8", 8)])
 def test_kernel_digit_identity_equals_oracle(kind, S):
-    w = split.SLICE_BITS[kind]
+    w = split.slice_bits(kind, S)
     A = awkward_rows(11 + w)
     e = split.row_exponents(A)
     ref = split.split_rows(A, e, S, w)          # S x M x K

@@ -62,7 +62,10 @@ def test_error_per_slice_count_at_16384(dist):
             assert errs[(kind, S + 1)] <= errs[(kind, S)] * 1.01 + 1e-3 * tol, (kind, S)
     if dist == "uniform":
         assert errs[("fp64", 0)] <= tol
-        assert errs[("bf16", 5)] <= tol and errs[("int8", 6)] <= tol
+        # bf16 digits of 9 bits: four slices meet the bound (the benchmark's)
+        assert errs[("bf16", 4)] <= tol and errs[("int8", 6)] <= tol
+    else:
+        assert errs[("bf16", 5)] <= tol
 
 
 def test_rectangular_spiked_columns_both_paths():
@@ -77,10 +80,14 @@ def test_rectangular_spiked_columns_both_paths():
     hs.gemm(dA, dB, out=C, P=12, Q=16, G=48, b=32, Bouter=128)      # the 12 x 16 grid
     hs.sync()
     e_native = split.max_rel_error(gather(C), ref, absab)
-    # 2 x 1 groups on CTA pairs, as in the benchmark
-    hs.gemm(dA, dB, out=C, kind="bf16", slices=7, P=192, Q=64, G=6144, b=64, Bouter=2048)
-    hs.sync()
-    e_split = split.max_rel_error(gather(C), ref, absab)
-    print("RECT", f"native {e_native:.3e} bf16 S=7 {e_split:.3e} tol {tol:.3e}")
+    # 2 x 1 groups on CTA pairs, as in the benchmark: S = 5 (digits of 9 bits)
+    # and S = 7 (8 bits)
+    e_split = {}
+    for S in (5, 7):
+        hs.gemm(dA, dB, out=C, kind="bf16", slices=S, P=192, Q=64, G=6144, b=64, Bouter=512)
+        hs.sync()
+        e_split[S] = split.max_rel_error(gather(C), ref, absab)
+    print("RECT", f"native {e_native:.3e} bf16 S=5 {e_split[5]:.3e} S=7 {e_split[7]:.3e} "
+          f"tol {tol:.3e}")
     assert e_native <= tol
-    assert e_split <= tol
+    assert e_split[5] <= tol and e_split[7] <= tol

@@ -1,8 +1,8 @@
 """Launch policies of the CTA-pair bf16 kernel (GPU): one launch for all slice
 pairs, one launch per diagonal, and persistent clusters that sweep several
 group tiles each give the oracle's exact diagonal sums and the closed-form
-counters; and the benchmark's own launch (n = 16384, S = 5, 2 x 1 groups,
-B = 2048, one launch per diagonal by the library's rule) gives the oracle's
+counters; and the benchmark's own launch (n = 16384, S = 4, 2 x 1 groups,
+B = 512, one launch per diagonal by the library's rule) gives the oracle's
 C bit for bit on sampled entries."""
 import numpy as np
 import pytest
@@ -22,7 +22,7 @@ def _oracle_diagonals(A, B, S):
     key = (A.shape, B.shape, S, A[:2].tobytes(), B[:, :2].tobytes())
     if key in _ORACLE:
         return _ORACLE[key]
-    w = split.SLICE_BITS["bf16"]
+    w = split.slice_bits("bf16", S)
     e, f = split.row_exponents(A), split.col_exponents(B)
     _ORACLE.clear()
     _ORACLE[key] = split.diagonal_products(split.split_rows(A, e, S, w),
@@ -77,16 +77,18 @@ def test_pair_launch_rejects_unknown_policy():
     assert hs.pair_launch() == ("auto", True)            # unchanged, the default
 
 
-def test_bench_launch_bit_exact_at_16384():
+@pytest.mark.parametrize("S", [4, 5])
+def test_bench_launch_bit_exact_at_16384(S):
     # bench.py's split step as it runs: M = N = K = 16384, uniform[-1, 1], bf16
-    # S = 5, a 128 x 64 grid of 128 x 256 blocks, G = 4096 groups of 2 x 1 (one
-    # CTA pair each), b = 64, B = 512; persistent pair clusters, and at this
-    # size the library's rule makes one launch per diagonal (exponent scan 2,
-    # slicing 2, products 5, recombination 1 launches).  Sampled entries,
-    # including every corner and tile border, bit for bit against the oracle.
+    # S = 4 (S = 5 beside it), a 128 x 64 grid of 128 x 256 blocks, G = 4096
+    # groups of 2 x 1 (one CTA pair each), b = 64, B = 512; persistent pair
+    # clusters, and at this size the library's rule makes one launch per
+    # diagonal (exponent scan 2, slicing 2, products S, recombination 1
+    # launches).  Sampled entries, including every corner and tile border, bit
+    # for bit against the oracle.
     hs = lib_ready()
     torch = torch_cuda()
-    n, S = 16384, 5
+    n = 16384
     assert hs.pair_launch() == ("auto", True) and hs.pair_kernel() is True
     dA = workloads.matrix_torch(n, n, 1002, "uniform", device="cuda")
     dB = workloads.matrix_torch(n, n, 2002, "uniform", device="cuda")
@@ -107,14 +109,18 @@ def test_bench_launch_bit_exact_at_16384():
 
 
 @pytest.mark.parametrize("kind,S,K,P,Q,G,pair_kernel", [
-    ("bf16", 3, 43328, 2, 1, 1, True),    # CTA pair: diagonal 4 has two segments
-    ("bf16", 3, 43328, 2, 1, 2, False),   # one CTA each: every diagonal one segment
+    ("bf16", 3, 43328, 2, 1, 1, True),    # CTA pair: diagonal 4 has five segments
+    ("bf16", 3, 43328, 2, 1, 2, False),   # one CTA each: diagonal 4 has four
+    ("bf16", 3, 16384, 2, 1, 1, True),    # diagonal 2 has one segment, 3 and 4 two
     ("int8", 3, 87360, 2, 2, 4, False),   # int8: diagonal 4 has two segments
 ])
 def test_planes_past_a_diagonals_segments_are_zero(kind, S, K, P, Q, G, pair_kernel):
-    # K large enough for two int32 planes per diagonal; the shorter diagonals
-    # fill only the first, and the kernels must write the second as zeros (the
-    # recombination adds every plane).  The sums' buffer starts out dirty.
+    # K large enough for several int32 planes per diagonal; the shorter
+    # diagonals fill only their first ones, and the kernels must write the rest
+    # as zeros (a caller of step 3 may add every plane).  The sums' buffer
+    # starts out dirty.  (The 128-column stages of the CTA pairs pad a pair's
+    # odd last panel: at K = 43328 that gives diagonal 4 one segment more than
+    # the 64-column stages of one CTA.)
     import ctypes
     hs = lib_ready()
     torch = torch_cuda()
@@ -123,7 +129,7 @@ def test_planes_past_a_diagonals_segments_are_zero(kind, S, K, P, Q, G, pair_ker
     e, f = hs.split_exponents(dA, dB)
     As, Bs = hs.split_slices(dA, dB, e, f, kind, S)
     planes = hs.split_planes(K, kind, S)
-    assert planes == 2
+    assert planes == {43328: 5, 16384: 2, 87360: 2}[K]
     D = torch.full((S, planes, M, N), 0x3f3f3f3f, dtype=torch.int32, device="cuda")
     was = hs.pair_kernel(pair_kernel)
     try:
@@ -133,12 +139,24 @@ def test_planes_past_a_diagonals_segments_are_zero(kind, S, K, P, Q, G, pair_ker
         hs.sync(None)
     finally:
         hs.pair_kernel(was)
-    w = split.SLICE_BITS[kind]
+    w = split.slice_bits(kind, S)
     ee, ff = split.row_exponents(A), split.col_exponents(B)
     want = split.diagonal_products(split.split_rows(A, ee, S, w), split.split_cols(B, ff, S, w),
                                    S, w)
     Dg = D.to(torch.int64).sum(dim=1).cpu().numpy()
     for d in range(2, S + 2):
         assert np.array_equal(Dg[d - 2], want[d]), d
-    # the first diagonal's sum fits one plane: its second plane is all zero
-    assert int(D[0, 1].abs().max()) == 0
+    # each diagonal's own segments: (d - 1) pairs of the kernel's k-stages,
+    # segments of 127 exact fp32 chunks (bf16: 2^(26 - 2w) products each) or of
+    # 2^18 products (int8); every plane past them is zero
+    stage = 64 if kind == "bf16" and not pair_kernel else 128
+    seg = 127 * 2 ** (26 - 2 * w) // stage if kind == "bf16" else 2 ** 18 // stage
+    nk = -(-(-(-K // 64) * 64) // stage)
+    zero_planes = 0
+    for d in range(2, S + 2):
+        own = -(-((d - 1) * nk) // seg)
+        assert own <= planes
+        if own < planes:
+            assert int(D[d - 2, own:].abs().max()) == 0, d
+            zero_planes += planes - own
+    assert zero_planes > 0

@@ -41,7 +41,7 @@ def test_exponents_and_slices_bit_exact(kind):
     S = 8 if kind == "int8" else 7
     As, Bs = hs.split_slices(dA, dB, e, f, kind, S)
     hs.sync()
-    w = split.SLICE_BITS[kind]
+    w = split.slice_bits(kind, S)
     Ad = split.split_rows(A, e_o, S, w)
     Bd = split.split_cols(B, f_o, S, w)
     Kp = As.shape[2]
@@ -94,7 +94,7 @@ def test_slices_bit_patterns(kind):
     S = 8 if kind == "int8" else 7
     As, Bs = hs.split_slices(dA, dB, e, f, kind, S)
     hs.sync()
-    w = split.SLICE_BITS[kind]
+    w = split.slice_bits(kind, S)
     e_o, f_o = split.row_exponents(A), split.col_exponents(B)
     assert np.array_equal(e.cpu().numpy(), e_o) and np.array_equal(f.cpu().numpy(), f_o)
     got_a = As.float().cpu().numpy()[:, :, :K]
@@ -160,25 +160,32 @@ def test_bf16_diagonals_exact(M, N, K, P, Q, G, S):
         assert c[k] == v, (k, c[k], v)
 
 
-def test_bf16_exact_at_the_fp32_bound():
-    # every digit at its largest magnitude: products 2^14, chunk sums reach
-    # exactly 2^24 -- the fp32 accumulator must still be exact
+@pytest.mark.parametrize("S", [2, 7])
+@pytest.mark.parametrize("P", [1, 2])
+def test_bf16_exact_at_the_fp32_bound(S, P):
+    # every digit at its largest magnitude 2^(w-1) (256 with w = 9 at S = 2,
+    # 128 with w = 8 at S = 7): products 2^(2w-2), chunk sums reach exactly
+    # 2^24 -- the fp32 accumulator must still be exact, and the drain's
+    # add-based conversion (exact below 2^22) must give way to the conversion
+    # instruction.  P = 1: one CTA; P = 2: one CTA pair.
     hs = lib_ready()
     torch = torch_cuda()
     M, N, K = 256, 256, 2048
-    A = np.full((M, K), 0.5 - 2.0 ** -20)          # r 2^8 rounds to 128
+    w = split.slice_bits("bf16", S)
+    A = np.full((M, K), 0.5 - 2.0 ** -20)          # r 2^w rounds to 2^(w-1)
     A[1::2] *= -1.0
     B = np.full((K, N), 0.5 - 2.0 ** -20)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     e, f = hs.split_exponents(dA, dB)
-    As, Bs = hs.split_slices(dA, dB, e, f, "bf16", 2)
-    assert As.float().abs().max().item() == 128.0
-    D = hs.split_diagonals(As, Bs, M, N, K, "bf16", 2, P=1, Q=1, G=1, b=64, Bouter=64)
+    As, Bs = hs.split_slices(dA, dB, e, f, "bf16", S)
+    assert As.float().abs().max().item() == 2.0 ** (w - 1)
+    D = hs.split_diagonals(As, Bs, M, N, K, "bf16", S, P=P, Q=1, G=1, b=64, Bouter=64)
     hs.sync()
-    _, parts = split.split_gemm(A, B, 2, "bf16", return_parts=True)
+    _, parts = split.split_gemm(A, B, S, "bf16", return_parts=True)
     Dg = D.to(torch.int64).sum(dim=1).cpu().numpy()
-    assert np.array_equal(Dg[0], parts["D"][2])
-    assert np.array_equal(Dg[1], parts["D"][3])
+    assert abs(int(parts["D"][2][0, 0])) == K * 4 ** (w - 1)
+    for d in range(2, S + 2):
+        assert np.array_equal(Dg[d - 2], parts["D"][d]), d
 
 
 @pytest.mark.parametrize("kind,S,dist", [("bf16", 3, "uniform"), ("bf16", 5, "wide"),
@@ -209,7 +216,7 @@ def test_recombine_special_values():
     C = hs.split_recombine(dD, de, df, M, N, 64, "bf16", S)
     hs.sync()
     Dd = {d: D[d - 2, 0].astype(np.int64) for d in range(2, S + 2)}
-    want = split.recombine(Dd, e, f, S, 8)
+    want = split.recombine(Dd, e, f, S, split.slice_bits("bf16", S))
     got = C.cpu().numpy()
     assert np.array_equal(np.isinf(got), np.isinf(want))
     fin = np.isfinite(want)
@@ -239,7 +246,7 @@ def test_recombine_64_and_128_bit_paths(kind, S):
     de, df = torch.from_numpy(e).cuda(), torch.from_numpy(f).cuda()
     C = hs.split_recombine(dD, de, df, M, N, 64, kind, S)
     hs.sync()
-    w = split.SLICE_BITS[kind]
+    w = split.slice_bits(kind, S)
     want = split.recombine({d: D[d - 2, 0].astype(np.int64) for d in range(2, S + 2)}, e, f, S, w)
     assert np.array_equal(C.cpu().numpy(), want)
 

@@ -57,6 +57,39 @@ def test_tie_rounds_to_even():
     assert D[:, 0, 0].tolist() == [64, 0, 0]
     assert D[:, 0, 1].tolist() == [2, 128, 0]
     assert D[:, 0, 2].tolist() == [4, -128, 0]
+    # the same with w = 9 (bf16 up to six slices): 0.25 * 512 = 128;
+    # 2.5 -> 2 with remainder +0.5 -> 256; 3.5 -> 4 with remainder -0.5 -> -256,
+    # the extreme digits 2^(w-1) that bfloat16 still holds exactly
+    A9 = np.array([[0.25, 2.5 / 512.0, 3.5 / 512.0]])
+    D9 = split.split_rows(A9, split.row_exponents(A9), 3, 9)
+    assert D9[:, 0, 0].tolist() == [128, 0, 0]
+    assert D9[:, 0, 1].tolist() == [2, 256, 0]
+    assert D9[:, 0, 2].tolist() == [4, -256, 0]
+
+
+def test_slice_widths():
+    # the widest width whose digits (|t| <= 2^(w-1)) the slice type holds,
+    # capped so that w S <= 56
+    assert [split.slice_bits("bf16", S) for S in range(1, 8)] == [9, 9, 9, 9, 9, 9, 8]
+    assert [split.slice_bits("int8", S) for S in range(1, 9)] == [7] * 8
+    for S in range(1, 8):
+        w = split.slice_bits("bf16", S)
+        assert w * S <= 56
+        # every digit magnitude up to 2^(w-1) survives a round trip through
+        # bfloat16 (8 significant bits: truncate the binary64 pattern to its top
+        # 16 bits after round to nearest even), and 2^(w-1) + 1 would not
+        for t in range(2 ** (w - 1) + 1):
+            assert _bf16(float(t)) == float(t)
+    assert _bf16(257.0) != 257.0
+    assert 2 ** (split.slice_bits("int8", 1) - 1) <= 127 < 2 ** split.slice_bits("int8", 1)
+
+
+def _bf16(x: float) -> float:
+    """x rounded to bfloat16 (round to nearest, ties to even), by the float32
+    bit pattern: bfloat16 is the top 16 bits of a float32."""
+    b = int(np.array(x, dtype=np.float32).view(np.uint32))
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return float(np.array(b, dtype=np.uint32).view(np.float32))
 
 
 @pytest.mark.parametrize("kind,S", [("int8", 1), ("int8", 3), ("bf16", 1), ("bf16", 4)])
@@ -67,10 +100,10 @@ def test_small_integers_exact_for_any_S(kind, S):
     assert np.array_equal(C, native.dgemm(A, B))
 
 
-@pytest.mark.parametrize("kind,S", [("bf16", 7), ("int8", 8)])
+@pytest.mark.parametrize("kind,S", [("bf16", 6), ("bf16", 7), ("int8", 8)])
 def test_identity_right_factor_returns_A(kind, S):
     # B = I: f_j = 2, the only nonzero digit of column j is 2^(w-2) at row j, so
-    # C^ = 2^e_i sum_s t_s 2^-ws, the first S digits of A; w S >= 56 > 53 bits
+    # C^ = 2^e_i sum_s t_s 2^-ws, the first S digits of A; w S >= 54 > 53 bits
     # relative to the row maximum captures A exactly
     A = workloads.matrix(17, 12, 61, "uniform")
     C = split.split_gemm(A, np.eye(12), S, kind)
@@ -92,7 +125,8 @@ def test_truncation_changes_with_S():
     e = split.row_exponents(A)
     for S in (2, 3, 4):
         C = split.split_gemm(A, np.eye(8), S, "bf16")
-        bound = 0.5 * 2.0 ** (e[:, None].astype(float) - 8 * S)
+        w = split.slice_bits("bf16", S)
+        bound = 0.5 * 2.0 ** (e[:, None].astype(float) - w * S)
         assert np.all(np.abs(C - A) <= bound * (1 + 2.0 ** -50) + np.abs(A) * 2.0 ** -53)
 
 
@@ -168,7 +202,7 @@ def _exact_from_digits(A, B, S, kind, square=False):
     pairs (all S^2 of them if `square`, else s + t <= S + 1) of
     a_s[i,k] b_t[k,j] 2^(e_i + f_j - w (s + t)), rounded once (float(Fraction) is
     correctly rounded, ties to even)."""
-    w = split.SLICE_BITS[kind]
+    w = split.slice_bits(kind, S)
     e, f = split.row_exponents(A), split.col_exponents(B)
     Ad, Bd = split.split_rows(A, e, S, w), split.split_cols(B, f, S, w)
     M, K = A.shape
