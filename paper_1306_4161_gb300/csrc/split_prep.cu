@@ -449,34 +449,56 @@ __global__ void __launch_bounds__(256, S <= 5 ? 4 : 3) recombine_kernel(const in
   int first[S][4];
 #pragma unroll
   for (int d = 0; d < S; ++d) load4(D + (int64_t)(d * nseg) * plane + off, first[d]);
-  // diagonal d's exact sum: its first plane and the rest of its own planes
-  auto diag = [&](int d, long long (&Dd)[4]) {
+  // D_2 whole (its further planes, if any), which decides the width
+  long long D2[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) Dd[u] = first[d][u];
-    for (int g = 1; g < np.n[d]; ++g) {
-      int v[4];
-      load4(D + (int64_t)(d * nseg + g) * plane + off, v);
+  for (int u = 0; u < 4; ++u) D2[u] = first[0][u];
+  for (int g = 1; g < np.n[0]; ++g) {
+    int v[4];
+    load4(D + (int64_t)g * plane + off, v);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) Dd[u] += v[u];
+    for (int u = 0; u < 4; ++u) D2[u] += v[u];
+  }
+  int gmax = 1;
+#pragma unroll
+  for (int d = 1; d < S; ++d) gmax = np.n[d] > gmax ? np.n[d] : gmax;
+  // X is linear in the planes: Horner's rule over the first planes, then each
+  // further round g adds sum_(d>2) plane_g(D_d) 2^(w (S+1-d)), the round's
+  // loads all in flight together (every partial sum is bounded as X is)
+  auto round_g = [&](int g, int (&v)[S][4]) {
+#pragma unroll
+    for (int d = 1; d < S; ++d) {
+      if (g < np.n[d]) {
+        load4(D + (int64_t)(d * nseg + g) * plane + off, v[d]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[d][u] = 0;
+      }
     }
   };
   const int k = e[i] - W * (S + 1);
   double out[4];
-  long long D2[4];
-  diag(0, D2);
   bool narrow = true;
 #pragma unroll
   for (int u = 0; u < 4; ++u) narrow = narrow && llabs(D2[u]) <= T2;
   if (narrow) {
     unsigned long long X[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) X[u] = (unsigned long long)D2[u];
+    for (int u = 0; u < 4; ++u) {
+      X[u] = (unsigned long long)D2[u];
 #pragma unroll
-    for (int d = 1; d < S; ++d) {
-      long long Dd[4];
-      diag(d, Dd);
+      for (int d = 1; d < S; ++d) X[u] = (X[u] << W) + (unsigned long long)(long long)first[d][u];
+    }
+    for (int g = 1; g < gmax; ++g) {
+      int v[S][4];
+      round_g(g, v);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) X[u] = (X[u] << W) + (unsigned long long)Dd[u];
+      for (int u = 0; u < 4; ++u) {
+        unsigned long long Y = 0;
+#pragma unroll
+        for (int d = 1; d < S; ++d) Y = (Y << W) + (unsigned long long)(long long)v[d][u];
+        X[u] += Y;
+      }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -484,13 +506,21 @@ __global__ void __launch_bounds__(256, S <= 5 ? 4 : 3) recombine_kernel(const in
   } else {
     __int128 X[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) X[u] = D2[u];
+    for (int u = 0; u < 4; ++u) {
+      X[u] = D2[u];
 #pragma unroll
-    for (int d = 1; d < S; ++d) {
-      long long Dd[4];
-      diag(d, Dd);
+      for (int d = 1; d < S; ++d) X[u] = (X[u] << W) + (__int128)first[d][u];
+    }
+    for (int g = 1; g < gmax; ++g) {
+      int v[S][4];
+      round_g(g, v);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) X[u] = (X[u] << W) + (__int128)Dd[u];
+      for (int u = 0; u < 4; ++u) {
+        __int128 Y = 0;
+#pragma unroll
+        for (int d = 1; d < S; ++d) Y = (Y << W) + (__int128)v[d][u];
+        X[u] += Y;
+      }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) out[u] = j0 + u < N ? round_scaled(X[u], k + f[j0 + u]) : 0.0;
