@@ -41,11 +41,13 @@
 // released in all four CTAs once both pairs' MMAs have read it (the commits of
 // both leaders, multicast to the cluster).
 //
-// Roles (384 threads per CTA): warp 0 issues the copies, warp 1 issues the MMAs
-// (leader only) and owns its CTA's tensor memory, warps 2 and 3 idle, warps
-// 4..11 drain their CTA's 128 rows into exact int32 planes (a warp reads the
-// tensor-memory lanes of its quarter, warp mod 4; warps 4..7 and 8..11 cover
-// the 128 rows for the two column halves).
+// Roles (320 threads per CTA): warp 0 issues the copies, warp 1 issues the MMAs
+// (leader only) and owns its CTA's tensor memory, warps 2..9 drain their CTA's
+// 128 rows into exact int32 planes (a warp reads the tensor-memory lanes of
+// its quarter, warp mod 4; warps 2..5 and 6..9 cover the 128 rows for the two
+// column halves).  Ten warps leave 200 registers a thread, room for a drain
+// warp's 128 sums and three 16-column loads in flight (12 warps with two idle
+// ones, two loads in flight: 1-2 % slower with 9-bit digits).
 //
 // Work: a persistent launch runs one cluster per resident slot; each sweeps
 // whole group tiles round robin with every diagonal of the launch, and a
@@ -73,7 +75,7 @@ constexpr int A_PANEL = TM * PK * 2, B_PANEL = HN * PK * 2;   // 16 KB each
 constexpr int A_BYTES = KZ * A_PANEL, BH_BYTES = KZ * B_PANEL;
 constexpr int STAGE_BYTES = A_BYTES + BH_BYTES;
 constexpr int NEPI = 8;                // draining warps per CTA
-constexpr int NTHREADS = (4 + NEPI) * 32;   // copy warp, MMA warp, two idle warps, drain warps
+constexpr int NTHREADS = (2 + NEPI) * 32;   // copy warp, MMA warp, drain warps
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC2 = idesc_bf16_f32(2 * TM, TN);
@@ -409,10 +411,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-  } else if (warp >= 4) {
+  } else if (warp >= 2) {
     // ---------------- drain (both CTAs): this SM's 128 rows -> exact int32 planes ----------------
     const int q = warp & 3;                 // tensor-memory lane quarter of this warp
-    const int h = (warp - 4) >> 2;          // column half of the 256-column tile
+    const int h = (warp - 2) >> 2;          // column half of the 256-column tile
     uint32_t nchunk = 0;
     bool ok = true;
     int L, dlo, dhi;
@@ -453,16 +455,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_after();
                 const uint32_t ta =
                     tmem_base + ((uint32_t)(q * 32) << 16) + who * (uint32_t)TN + h * 128;
-                // two 16-column loads in flight per wait: four round trips
+                // three 16-column loads in flight per wait: three round trips
                 float mx = 0.f;
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                  uint32_t v[16], w[16];
-                  tmem_ld16(ta + j * 16, v);
-                  tmem_ld16(ta + j * 16 + 16, w);
+                for (int j = 0; j < 8; j += 3) {
+                  uint32_t v[3][16];
+#pragma unroll
+                  for (int r = 0; r < 3; ++r)
+                    if (j + r < 8) tmem_ld16(ta + (j + r) * 16, v[r]);
                   tmem_ld_wait();
-                  drain_add16(acc + j * 16, v, mx);
-                  drain_add16(acc + j * 16 + 16, w, mx);
+#pragma unroll
+                  for (int r = 0; r < 3; ++r)
+                    if (j + r < 8) drain_add16(acc + (j + r) * 16, v[r], mx);
                 }
                 if (__any_sync(0xffffffffu, !(mx < kFastDrainBound))) {
 #pragma unroll
