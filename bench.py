@@ -67,18 +67,26 @@ def flops(n=None):
     return 2.0 * n ** 3
 
 
-def measured_traffic(kernel="bf16_pair_kernel"):
-    """DRAM bytes per launch from the committed ncu record, only while the
-    kernel's source is the one the counters were taken on (else None)."""
+def traffic_record(kernel="bf16_pair_kernel"):
+    """(DRAM bytes per product stage from the committed ncu record, whether
+    the kernel's sources -- its file and the device headers it includes -- are
+    still the ones the counters were taken on); (None, False) without one."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != rec["sha256_prefix"]:
-            return None
-        return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec["dram_bytes_read"] + rec["dram_bytes_write"], \
+            h.hexdigest()[:16] == rec["sha256_prefix"]
     except Exception:
-        return None
+        return None, False
+
+
+def measured_traffic(kernel="bf16_pair_kernel"):
+    """The record's bytes, only while the kernel is unchanged since (else None)."""
+    value, current = traffic_record(kernel)
+    return value if current else None
 
 
 MULTI_GPU_UNAVAILABLE = ("single-GPU library: its cluster kernels deliver panels by TMA "
@@ -561,6 +569,10 @@ def main():
                 "traffic": measured_traffic() if N_SIZE == 16384 else None,
                 "traffic_unit": "bytes per product stage (ncu dram read + write), scaled from "
                                 "a capture at n = 6144 (profiles/traffic.json)"}
+    if N_SIZE == 16384 and roofline["traffic"] is None:
+        # the last capture, taken on an earlier build of the kernel (the same
+        # copy schedule, or not: see the record's note)
+        roofline["traffic_previous_capture"] = traffic_record()[0]
     breakdown_ms = {"exponent_scan": dur[0], "slicing": dur[1], "diagonal_products": dur[2],
                     "recombination": dur[3]}
 

@@ -129,12 +129,20 @@ constexpr float kFastDrainBound = 4194304.f;   // 2^22
 __device__ __forceinline__ uint32_t drain_fast_bits(float x) {
   return __float_as_uint(x + 12582912.f) - 0x4B400000u;   // 1.5 * 2^23 and its encoding
 }
+// Two values per step: one packed add (add.f32x2) converts both, one
+// three-input max tracks them, against one add and one max per value (1-3 %
+// faster products at 16384^3 with 9-bit digits, where a chunk is 2 stages).
 __device__ __forceinline__ void drain_add16(uint32_t *acc, const uint32_t (&v)[16], float &mx) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const float x = __uint_as_float(v[i]);
-    mx = fmaxf(mx, fabsf(x));
-    acc[i] += drain_fast_bits(x);
+  for (int i = 0; i < 16; i += 2) {
+    const float x0 = __uint_as_float(v[i]), x1 = __uint_as_float(v[i + 1]);
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(mx) : "f"(fabsf(x0)), "f"(fabsf(x1)), "f"(mx));
+    unsigned long long y;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(y)
+        : "l"(((unsigned long long)v[i + 1] << 32) | v[i]), "l"(0x4B4000004B400000ull));
+    acc[i] += (uint32_t)y - 0x4B400000u;
+    acc[i + 1] += (uint32_t)(y >> 32) - 0x4B400000u;
   }
 }
 __device__ __forceinline__ void drain_fix16(uint32_t *acc, const uint32_t (&v)[16]) {
