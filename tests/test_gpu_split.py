@@ -251,6 +251,53 @@ def test_recombine_64_and_128_bit_paths(kind, S):
     assert np.array_equal(C.cpu().numpy(), want)
 
 
+def _own_planes(K, kind, S, d):
+    """Segment planes diagonal d fills: (d - 1) pairs of K rounded up to the
+    128-column stages, cut into segments of 127 exact fp32 chunks (bf16:
+    2^(26 - 2w) products each) or of 2^18 products (int8)."""
+    k128 = -(-(-(-K // 64) * 64) // 128) * 128
+    seg = 127 * 2 ** (26 - 2 * split.slice_bits(kind, S)) if kind == "bf16" else 2 ** 18
+    return max(1, -(-((d - 1) * k128) // seg))
+
+
+@pytest.mark.parametrize("kind,S,K,M,N", [
+    ("bf16", 3, 70000, 5, 37),     # diagonals fill 3 / 5 / 7 planes; ragged rows of C
+    ("bf16", 4, 40000, 4, 64),     # 2 / 3 / 4 / 5 planes; 16-byte rows
+    ("bf16", 6, 33000, 3, 20),     # every diagonal past one plane; 128-bit path only
+    ("int8", 3, 300000, 4, 36),    # 2 / 3 / 4 planes
+])
+def test_recombine_several_planes_per_diagonal(kind, S, K, M, N):
+    # a diagonal's exact sum spread over several int32 planes, the first
+    # diagonal's too: the recombination must add exactly its own planes (the
+    # planes past them hold garbage here, which it must not read), on the 64-
+    # and the 128-bit path
+    hs = lib_ready()
+    torch = torch_cuda()
+    planes = hs.split_planes(K, kind, S)
+    own = [_own_planes(K, kind, S, d) for d in range(2, S + 2)]
+    assert own[-1] == planes and own[0] >= 2
+    rng = np.random.default_rng(K + S)
+    D = np.full((S, planes, M, N), 0x3F3F3F3F, dtype=np.int32)
+    for i, n in enumerate(own):
+        D[i, :n] = rng.integers(-2 ** 20, 2 ** 20, size=(n, M, N))
+    # full-range planes in one row: sums past 2^31 (the 128-bit path at S = 6,
+    # where the other diagonals alone can pass 2^63)
+    D[:, :, 1, :] = rng.integers(-2 ** 31, 2 ** 31, size=(S, planes, N))
+    D[0, 0, 2, :] = 2 ** 31 - 1
+    e = rng.integers(-40, 40, M).astype(np.int32)
+    f = rng.integers(-40, 40, N).astype(np.int32)
+    dD = torch.from_numpy(D).cuda()
+    de, df = torch.from_numpy(e).cuda(), torch.from_numpy(f).cuda()
+    C = hs.split_recombine(dD, de, df, M, N, K, kind, S)
+    hs.sync()
+    sums = {d: D[d - 2, :own[d - 2]].astype(np.int64).sum(axis=0) for d in range(2, S + 2)}
+    want = split.recombine(sums, e, f, S, split.slice_bits(kind, S))
+    got = C.cpu().numpy()
+    assert np.array_equal(np.isinf(got), np.isinf(want))
+    fin = np.isfinite(want)
+    assert np.array_equal(got[fin], want[fin])
+
+
 def test_accuracy_within_bound_bf16_S5():
     hs = lib_ready()
     M, N, K = 256, 256, 4096
